@@ -1,0 +1,198 @@
+/*
+ * cmf.h -- C ABI of libcmf, a GB300 (sm_103a) solver for continuous max-flow
+ * / min-cut image segmentation after Sun, Tai and Yuan, "Efficient ADMM and
+ * splitting methods for continuous min-cut and max-flow problems".
+ *
+ * Problems (Sec. 2.1):
+ *   binary  max sum_x p_s  s.t. |q(x)| <= alpha(x), p_s <= C_s, p_t <= C_t,
+ *           div q - p_s + p_t = 0                       (Eq. two-label-mf)
+ *           dual of  min_{u in [0,1]} sum (1-u) C_s + u C_t + alpha |grad u|
+ *                                                       (Eq. seg:chanvese)
+ *   Potts   max sum_x p_s  s.t. |q_i| <= alpha, p_i <= C_i,
+ *           div q_i - p_s + p_i = 0, i = 1..L           (Eq. potts-mf)
+ *           dual of the simplex-constrained relaxed Potts model
+ *                                                       (Eq. relaxed-potts)
+ * The multiplier u of the conservation constraint is the relaxed labelling.
+ *
+ * Algorithms (Sec. 3): pADMMI (Fortin-Glowinski ADMM without relaxation,
+ * Sec. 4), rpADMMI (Eq. rpADMMI / Eq. multi:fg:4), rpADMMII (Eq. rpADMMII /
+ * the Potts Eckstein-Bertsekas equations after Thm 2), rPDRQ (Eq.
+ * iteration:quadratic:seg / Eq. pdrq:4labels) with a symmetric red-black
+ * Gauss-Seidel preconditioner.
+ *
+ * Discretisation: unit grid spacing, forward-difference gradient that is 0 on
+ * the far boundary, div = -grad^T (the scheme behind ||div^* div|| <= 8 in
+ * Thm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Grids are H rows x W columns, row-major with a row stride of `pitch`
+ *    elements (pitch >= W).  A "plane" is H*pitch elements; stacked planes
+ *    follow each other with no gap.  Padding columns are never read or
+ *    written.
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *    never frees them and never allocates device memory inside a call except
+ *    where stated (the CUDA graph objects of cmf_solve_*).  Pointers named h_*
+ *    are HOST pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream-ordered: device outputs are valid once the
+ *    stream has been synchronised.  Entry points that return host values
+ *    (cmf_eval_*, cmf_solve_*) synchronise the stream themselves.
+ *  - Errors are returned, never aborted on.  On CMF_EINVAL nothing was
+ *    launched.  On CMF_ECUDA the state buffers are undefined.
+ *  - State storage: u is always float32.  Flows (q, p_s, p_t / p_i) are
+ *    stored as cmf_params.storage (float32, float16 or bfloat16); all
+ *    arithmetic is float32 and the certificates (energies, gap, residual) are
+ *    accumulated in float64.
+ */
+#ifndef CMF_H
+#define CMF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CMF_OK = 0,
+    CMF_EINVAL = 1,        /* bad argument: sizes, pointers, parameters       */
+    CMF_ENOMEM = 2,        /* workspace smaller than cmf_workspace_bytes()    */
+    CMF_ECUDA = 3,         /* a CUDA runtime call failed                      */
+    CMF_ETIMEOUT = 4,      /* a bounded device-side wait ran out              */
+    CMF_NOT_CONVERGED = 5  /* status, not failure: max_iter reached first     */
+} cmf_status;
+
+typedef enum {
+    CMF_PADMM = 0,      /* pADMMI: rpADMMI with r = 1                        */
+    CMF_RPADMM_FG = 1,  /* rpADMMI, relaxation r on u (Fortin-Glowinski)     */
+    CMF_RPADMM_EB = 2,  /* rpADMMII, relaxation rho (Eckstein-Bertsekas)     */
+    CMF_RPDRQ = 3       /* relaxed preconditioned Douglas-Rachford           */
+} cmf_algo;
+
+typedef enum { CMF_F32 = 0, CMF_F16 = 1, CMF_BF16 = 2 } cmf_dtype;
+
+typedef enum {
+    CMF_FUSED = 0,      /* one fused kernel per iteration (default)          */
+    CMF_PLAIN = 1       /* one kernel per step of the method (baseline)      */
+} cmf_impl;
+
+/* Parameters.  cmf_default_params() fills the paper's values (Sec. 4):
+ * c = 0.3, a = 8, a1 = 2 (binary a~), a2 = 2L, rho = 1.9, r = 1.618,
+ * rPDRQ sigma = 0.2, tau = 1.0 (binary) or sigma = 5, tau = 0.4 (Potts),
+ * one sRBGS sweep, isotropic P_alpha. */
+typedef struct {
+    int algo;          /* cmf_algo                                             */
+    int storage;       /* cmf_dtype of the flow planes                         */
+    int impl;          /* cmf_impl                                             */
+    int aniso;         /* 0: |q(x)|_2 <= alpha(x); 1: |q_k(x)| <= alpha(x)      */
+    int sweeps;        /* symmetric red-black GS sweeps per rPDRQ step (>= 1)  */
+    int max_iter;      /* cmf_solve_*: iteration cap                           */
+    int check_every;   /* cmf_solve_*: iterations between certificate checks   */
+    int warm_start;    /* cmf_solve_*: 0 = cold start, 1 = start from buffers  */
+    int use_graph;     /* cmf_solve_*: replay a CUDA graph per check interval  */
+    int reserved;
+    double c;          /* ADMM step size                                       */
+    double a;          /* q preconditioner N = a c I (a >= 8, Thm 1)           */
+    double a1;         /* p preconditioner a~ (binary) / a_1 (Potts), >= 2     */
+    double a2;         /* Potts p_s preconditioner a_2 >= 2L (Thm 2); 0 => 2L  */
+    double rho;        /* rpADMMII / rPDRQ relaxation in (0, 2)                */
+    double r;          /* rpADMMI relaxation in (0, (1+sqrt 5)/2)              */
+    double sigma;      /* rPDRQ step sizes                                     */
+    double tau;
+    double tol_gap;    /* cmf_solve_*: stop when the relative gap <= tol_gap   */
+} cmf_params;
+
+/* Fill *p with the paper's defaults for `algo` and L labels (L = 2 for the
+ * binary model).  Returns CMF_EINVAL on a NULL pointer or unknown algo. */
+cmf_status cmf_default_params(int algo, int L, cmf_params *p);
+
+/* Human-readable name of a status code (static string). */
+const char *cmf_status_str(cmf_status s);
+
+/* Bytes of device workspace the calls below need for an H x W grid with L
+ * labels (L = 2: binary) and row pitch `pitch`.  The workspace is caller-
+ * owned device memory, at least 256-byte aligned, passed as d_ws/ws_bytes. */
+size_t cmf_workspace_bytes(int H, int W, int L, int pitch, const cmf_params *p);
+
+/* ------------------------------------------------------------------------ */
+/* Binary model.  Planes: d_Cs, d_Ct (float32, read only); d_alpha (float32  */
+/* plane or NULL, then alpha0 everywhere); state d_u (float32), d_qx, d_qy,  */
+/* d_ps, d_pt (storage dtype).  For rPDRQ the flow buffers hold the          */
+/* relaxed DR iterate (qbar, pbar_s, pbar_t) of Eq. iteration:quadratic:seg. */
+/* ------------------------------------------------------------------------ */
+
+/* Cold start: the alpha = 0 saddle point (u = 1 where C_t < C_s, q = 0,
+ * p_s = p_t = min(C_s, C_t)); rPDRQ stores ybar = y - tau K u of that point. */
+cmf_status cmf_init_binary(const float *d_Cs, const float *d_Ct, int H, int W, int pitch,
+                           const cmf_params *p, float *d_u, void *d_qx, void *d_qy,
+                           void *d_ps, void *d_pt, void *stream);
+
+/* Exactly n_iter iterations of p->algo from the state in the buffers
+ * (Eq. rpADMMI / Eq. rpADMMII / Eq. iteration:quadratic:seg); the result is
+ * written back to the same buffers. */
+cmf_status cmf_iterate_binary(const float *d_Cs, const float *d_Ct, const float *d_alpha,
+                              float alpha0, int H, int W, int pitch, const cmf_params *p,
+                              int n_iter, float *d_u, void *d_qx, void *d_qy, void *d_ps,
+                              void *d_pt, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Certificates of the current state, into h_out[0..3] (host):
+ *  E   = sum (1-ub) C_s + ub C_t + alpha |grad ub|, ub = clip(u, 0, 1)
+ *  D   = sum min(C_s, C_t + div q)   (max-flow value of feasible q)
+ *  gap = (E - D) / max(|E|, 1e-30)
+ *  res = || div q - p_s + p_t ||_2
+ * For rPDRQ the flows are y = ybar + tau K u and D uses P_alpha(q). */
+cmf_status cmf_eval_binary(const float *d_Cs, const float *d_Ct, const float *d_alpha,
+                           float alpha0, int H, int W, int pitch, const cmf_params *p,
+                           const float *d_u, const void *d_qx, const void *d_qy,
+                           const void *d_ps, const void *d_pt, double *h_out, void *d_ws,
+                           size_t ws_bytes, void *stream);
+
+/* Solve to gap <= p->tol_gap or p->max_iter iterations: cold start unless
+ * p->warm_start, then repeat {check_every iterations; certificates}.
+ * h_hist (host, may be NULL) receives up to hist_cap rows of
+ * (iteration, E, D, gap, res); *h_iters (host, may be NULL) the iterations
+ * run.  Returns CMF_OK on convergence, CMF_NOT_CONVERGED at max_iter. */
+cmf_status cmf_solve_binary(const float *d_Cs, const float *d_Ct, const float *d_alpha,
+                            float alpha0, int H, int W, int pitch, const cmf_params *p,
+                            float *d_u, void *d_qx, void *d_qy, void *d_ps, void *d_pt,
+                            double *h_hist, int hist_cap, int *h_iters, void *d_ws,
+                            size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Potts model, L labels (2 <= L <= 64).  d_C: L float32 planes C_1..C_L.   */
+/* State: d_u (L float32 planes), d_qx, d_qy, d_p (L planes each, storage    */
+/* dtype), d_ps (one plane).  rPDRQ: (qbar_i, pbar_i, pbar_s).              */
+/* ------------------------------------------------------------------------ */
+
+/* Cold start: u_i = 1 for the first cheapest label, q_i = 0,
+ * p_i = p_s = min_j C_j; rPDRQ stores ybar = y - tau K u of that point. */
+cmf_status cmf_init_potts(const float *d_C, int L, int H, int W, int pitch,
+                          const cmf_params *p, float *d_u, void *d_qx, void *d_qy, void *d_p,
+                          void *d_ps, void *stream);
+
+/* Exactly n_iter iterations (Eq. multi:fg:4, the Eckstein-Bertsekas Potts
+ * equations after Thm 2, Eq. pdrq:4labels), in place. */
+cmf_status cmf_iterate_potts(const float *d_C, int L, const float *d_alpha, float alpha0, int H,
+                             int W, int pitch, const cmf_params *p, int n_iter, float *d_u,
+                             void *d_qx, void *d_qy, void *d_p, void *d_ps, void *d_ws,
+                             size_t ws_bytes, void *stream);
+
+/* Certificates into h_out[0..3]:
+ *  E   = sum_i sum_x ub_i C_i + alpha |grad ub_i|, ub(x) = simplex projection
+ *  D   = sum_x min_i (C_i + div q_i)
+ *  gap = (E - D) / max(|E|, 1e-30),  res = || div q_i - p_s + p_i ||_2. */
+cmf_status cmf_eval_potts(const float *d_C, int L, const float *d_alpha, float alpha0, int H,
+                          int W, int pitch, const cmf_params *p, const float *d_u,
+                          const void *d_qx, const void *d_qy, const void *d_p, const void *d_ps,
+                          double *h_out, void *d_ws, size_t ws_bytes, void *stream);
+
+cmf_status cmf_solve_potts(const float *d_C, int L, const float *d_alpha, float alpha0, int H,
+                           int W, int pitch, const cmf_params *p, float *d_u, void *d_qx,
+                           void *d_qy, void *d_p, void *d_ps, double *h_hist, int hist_cap,
+                           int *h_iters, void *d_ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMF_H */

@@ -1,0 +1,305 @@
+"""Thin ctypes binding of libcmf (include/cmf.h).
+
+Argument marshalling only: torch tensors become device pointers, the current
+torch CUDA stream becomes the cudaStream_t, and the C-ABI does all the work.
+Importing this module never falls back to anything: if libcmf.so is missing
+or was built without CUDA, every call raises.
+
+Planes are row-major (H, pitch) float tensors; ``alloc_binary`` /
+``alloc_potts`` allocate correctly pitched state and workspace tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED = range(6)
+PADMM, RPADMM_FG, RPADMM_EB, RPDRQ = range(4)
+F32, F16, BF16 = range(3)
+FUSED, PLAIN = range(2)
+ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ"}
+_TORCH_DTYPE = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
+
+
+class CmfError(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    """Mirror of cmf_params."""
+    _fields_ = [
+        ("algo", ctypes.c_int), ("storage", ctypes.c_int), ("impl", ctypes.c_int),
+        ("aniso", ctypes.c_int), ("sweeps", ctypes.c_int), ("max_iter", ctypes.c_int),
+        ("check_every", ctypes.c_int), ("warm_start", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("c", ctypes.c_double), ("a", ctypes.c_double), ("a1", ctypes.c_double),
+        ("a2", ctypes.c_double), ("rho", ctypes.c_double), ("r", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("tol_gap", ctypes.c_double),
+    ]
+
+
+_lib = None
+_SIGS = {
+    "cmf_default_params": [ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "cmf_status_str": [ctypes.c_int],
+    "cmf_workspace_bytes": [ctypes.c_int] * 4 + [ctypes.c_void_p],
+    "cmf_init_binary": [ctypes.c_void_p] * 2 + [ctypes.c_int] * 3 + [ctypes.c_void_p] * 7,
+    "cmf_iterate_binary": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
+                          [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6 +
+                          [ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_eval_binary": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
+                       [ctypes.c_void_p] * 8 + [ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_solve_binary": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
+                        [ctypes.c_void_p] * 7 + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_init_potts": [ctypes.c_void_p] + [ctypes.c_int] * 4 + [ctypes.c_void_p] * 7,
+    "cmf_iterate_potts": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_float] +
+                         [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int] +
+                         [ctypes.c_void_p] * 6 + [ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_eval_potts": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_float] +
+                      [ctypes.c_int] * 3 + [ctypes.c_void_p] * 8 +
+                      [ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_solve_potts": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_float] +
+                       [ctypes.c_int] * 3 + [ctypes.c_void_p] * 7 +
+                       [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                        ctypes.c_void_p],
+}
+EXPORTED = tuple(_SIGS)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libcmf.so (it must have been built: ``_build.build()``)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise CmfError(f"libcmf.so not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.cmf_status_str.restype = ctypes.c_char_p
+        L.cmf_workspace_bytes.restype = ctypes.c_size_t
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str, allow=(OK,)) -> int:
+    if status not in allow:
+        msg = lib().cmf_status_str(status).decode()
+        raise CmfError(f"{what}: {msg} (status {status})")
+    return status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise CmfError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def default_params(algo: int, L: int = 2, **kw) -> Params:
+    p = Params()
+    _check(lib().cmf_default_params(algo, L, ctypes.byref(p)), "cmf_default_params")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def cmf_workspace_bytes(H: int, W: int, L: int, pitch: int, p: Params) -> int:
+    return int(lib().cmf_workspace_bytes(H, W, L, pitch, ctypes.byref(p)))
+
+
+def pitch_for(W: int) -> int:
+    """Row stride in elements: W rounded up to a multiple of 32."""
+    return (W + 31) // 32 * 32
+
+
+# --- state containers --------------------------------------------------------------
+
+class Binary:
+    """Device buffers of one binary problem (costs, alpha, state, workspace)."""
+
+    def __init__(self, Cs, Ct, alpha, params: Params, device="cuda"):
+        Cs = np.asarray(Cs, dtype=np.float32)
+        Ct = np.asarray(Ct, dtype=np.float32)
+        self.H, self.W = Cs.shape
+        self.pitch = pitch_for(self.W)
+        self.params = params
+        self.device = device
+        self.Cs = _pitched(Cs, self.pitch, device)
+        self.Ct = _pitched(Ct, self.pitch, device)
+        if np.isscalar(alpha):
+            self.alpha, self.alpha0 = None, float(alpha)
+        else:
+            self.alpha, self.alpha0 = _pitched(np.asarray(alpha, np.float32), self.pitch,
+                                               device), 0.0
+        sd = _TORCH_DTYPE[params.storage]
+        shp = (self.H, self.pitch)
+        self.u = torch.zeros(shp, dtype=torch.float32, device=device)
+        self.qx = torch.zeros(shp, dtype=sd, device=device)
+        self.qy = torch.zeros(shp, dtype=sd, device=device)
+        self.ps = torch.zeros(shp, dtype=sd, device=device)
+        self.pt = torch.zeros(shp, dtype=sd, device=device)
+        nb = cmf_workspace_bytes(self.H, self.W, 2, self.pitch, params)
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=device)
+
+    def state(self) -> dict:
+        """Host float64 copies of (u, qx, qy, ps, pt) without padding."""
+        W = self.W
+        return {k: getattr(self, k)[:, :W].float().cpu().double().numpy()
+                for k in ("u", "qx", "qy", "ps", "pt")}
+
+    def load_state(self, st: dict) -> None:
+        W = self.W
+        for k in ("u", "qx", "qy", "ps", "pt"):
+            t = getattr(self, k)
+            t[:, :W] = torch.as_tensor(np.asarray(st[k]), device=self.device).to(t.dtype)
+
+    def _common(self):
+        return (_ptr(self.Cs), _ptr(self.Ct), _ptr(self.alpha), self.alpha0, self.H, self.W,
+                self.pitch, ctypes.byref(self.params))
+
+    def _state_ptrs(self):
+        return (_ptr(self.u), _ptr(self.qx), _ptr(self.qy), _ptr(self.ps), _ptr(self.pt))
+
+
+class Potts:
+    """Device buffers of one Potts problem with L labels."""
+
+    def __init__(self, C, alpha, params: Params, device="cuda"):
+        C = np.asarray(C, dtype=np.float32)
+        self.L, self.H, self.W = C.shape
+        self.pitch = pitch_for(self.W)
+        self.params = params
+        self.device = device
+        self.C = _pitched(C, self.pitch, device)
+        if np.isscalar(alpha):
+            self.alpha, self.alpha0 = None, float(alpha)
+        else:
+            self.alpha, self.alpha0 = _pitched(np.asarray(alpha, np.float32), self.pitch,
+                                               device), 0.0
+        sd = _TORCH_DTYPE[params.storage]
+        shp = (self.L, self.H, self.pitch)
+        self.u = torch.zeros(shp, dtype=torch.float32, device=device)
+        self.qx = torch.zeros(shp, dtype=sd, device=device)
+        self.qy = torch.zeros(shp, dtype=sd, device=device)
+        self.p = torch.zeros(shp, dtype=sd, device=device)
+        self.ps = torch.zeros((self.H, self.pitch), dtype=sd, device=device)
+        nb = cmf_workspace_bytes(self.H, self.W, self.L, self.pitch, params)
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=device)
+
+    def state(self) -> dict:
+        W = self.W
+        out = {k: getattr(self, k)[..., :W].float().cpu().double().numpy()
+               for k in ("u", "qx", "qy", "p")}
+        out["ps"] = self.ps[:, :W].float().cpu().double().numpy()
+        return out
+
+    def load_state(self, st: dict) -> None:
+        W = self.W
+        for k in ("u", "qx", "qy", "p", "ps"):
+            t = getattr(self, k)
+            t[..., :W] = torch.as_tensor(np.asarray(st[k]), device=self.device).to(t.dtype)
+
+    def _common(self):
+        return (_ptr(self.C), self.L, _ptr(self.alpha), self.alpha0, self.H, self.W,
+                self.pitch, ctypes.byref(self.params))
+
+    def _state_ptrs(self):
+        return (_ptr(self.u), _ptr(self.qx), _ptr(self.qy), _ptr(self.p), _ptr(self.ps))
+
+
+def _pitched(a: np.ndarray, pitch: int, device) -> torch.Tensor:
+    shp = a.shape[:-1] + (pitch,)
+    t = torch.zeros(shp, dtype=torch.float32, device=device)
+    t[..., :a.shape[-1]] = torch.as_tensor(np.ascontiguousarray(a), device=device)
+    return t
+
+
+def alloc_binary(inst, params: Params, device="cuda") -> Binary:
+    return Binary(inst.costs[0], inst.costs[1], inst.alpha, params, device)
+
+
+def alloc_potts(inst, params: Params, device="cuda") -> Potts:
+    return Potts(inst.costs, inst.alpha, params, device)
+
+
+# --- C-ABI calls (same names as include/cmf.h) --------------------------------------
+
+def cmf_init_binary(b: Binary, stream=None) -> None:
+    _check(lib().cmf_init_binary(_ptr(b.Cs), _ptr(b.Ct), b.H, b.W, b.pitch,
+                                 ctypes.byref(b.params), *b._state_ptrs(), _stream(stream)),
+           "cmf_init_binary")
+
+
+def cmf_iterate_binary(b: Binary, n_iter: int, stream=None) -> None:
+    _check(lib().cmf_iterate_binary(*b._common(), n_iter, *b._state_ptrs(), _ptr(b.ws),
+                                    b.ws.numel(), _stream(stream)), "cmf_iterate_binary")
+
+
+def cmf_eval_binary(b: Binary, stream=None):
+    out = (ctypes.c_double * 4)()
+    _check(lib().cmf_eval_binary(*b._common(), *b._state_ptrs(), out, _ptr(b.ws), b.ws.numel(),
+                                 _stream(stream)), "cmf_eval_binary")
+    return tuple(out)
+
+
+def cmf_solve_binary(b: Binary, hist_cap: int = 4096, stream=None):
+    """Returns (status, iterations, history array [n, 5])."""
+    hist = np.zeros((hist_cap, 5))
+    iters = ctypes.c_int(0)
+    st = _check(lib().cmf_solve_binary(*b._common(), *b._state_ptrs(),
+                                       hist.ctypes.data_as(ctypes.c_void_p), hist_cap,
+                                       ctypes.byref(iters), _ptr(b.ws), b.ws.numel(),
+                                       _stream(stream)),
+                "cmf_solve_binary", allow=(OK, NOT_CONVERGED))
+    n = int(np.count_nonzero(hist[:, 0]))
+    return st, iters.value, hist[:n]
+
+
+def cmf_init_potts(s: Potts, stream=None) -> None:
+    _check(lib().cmf_init_potts(_ptr(s.C), s.L, s.H, s.W, s.pitch, ctypes.byref(s.params),
+                                *s._state_ptrs(), _stream(stream)), "cmf_init_potts")
+
+
+def cmf_iterate_potts(s: Potts, n_iter: int, stream=None) -> None:
+    _check(lib().cmf_iterate_potts(*s._common(), n_iter, *s._state_ptrs(), _ptr(s.ws),
+                                   s.ws.numel(), _stream(stream)), "cmf_iterate_potts")
+
+
+def cmf_eval_potts(s: Potts, stream=None):
+    out = (ctypes.c_double * 4)()
+    _check(lib().cmf_eval_potts(*s._common(), *s._state_ptrs(), out, _ptr(s.ws), s.ws.numel(),
+                                _stream(stream)), "cmf_eval_potts")
+    return tuple(out)
+
+
+def cmf_solve_potts(s: Potts, hist_cap: int = 4096, stream=None):
+    hist = np.zeros((hist_cap, 5))
+    iters = ctypes.c_int(0)
+    st = _check(lib().cmf_solve_potts(*s._common(), *s._state_ptrs(),
+                                      hist.ctypes.data_as(ctypes.c_void_p), hist_cap,
+                                      ctypes.byref(iters), _ptr(s.ws), s.ws.numel(),
+                                      _stream(stream)),
+                "cmf_solve_potts", allow=(OK, NOT_CONVERGED))
+    n = int(np.count_nonzero(hist[:, 0]))
+    return st, iters.value, hist[:n]

@@ -1,0 +1,509 @@
+// C-ABI layer of libcmf: argument validation, workspace layout, the
+// iteration / certificate / solve drivers.  See include/cmf.h for the
+// contract of every entry point.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cmf_kernels.cuh"
+
+using namespace cmf;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Workspace regions (offsets from the workspace base).
+struct WsLayout {
+    size_t state;     // second state buffer set (ping-pong of the fused form)
+    size_t tmp;       // float planes used by the plain form
+    size_t partials;  // 3 doubles per certificate block
+    size_t scalars;   // 4 doubles
+    size_t total;
+};
+
+WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool potts) {
+    const size_t plane = (size_t)H * (size_t)pitch;
+    const size_t es = dtype_size(p.storage);
+    const int nu = potts ? L : 1;           // u planes
+    const int nf = potts ? 3 * L + 1 : 4;   // flow planes
+    WsLayout w;
+    size_t off = 0;
+    w.state = off;
+    off += align_up(plane * 4 * nu);
+    for (int i = 0; i < nf; ++i) off += align_up(plane * es);
+    w.tmp = off;
+    off += align_up(plane * 4 * (size_t)(potts ? L + 2 : 1));
+    w.partials = off;
+    off += align_up(sizeof(double) * 3 * (size_t)eval_blocks(H, W));
+    w.scalars = off;
+    off += align_up(sizeof(double) * 4);
+    w.total = off;
+    return w;
+}
+
+bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+cmf_status check_params(const cmf_params* p, int L) {
+    if (!p) return CMF_EINVAL;
+    if (p->algo < CMF_PADMM || p->algo > CMF_RPDRQ) return CMF_EINVAL;
+    if (p->storage < CMF_F32 || p->storage > CMF_BF16) return CMF_EINVAL;
+    if (p->impl != CMF_FUSED && p->impl != CMF_PLAIN) return CMF_EINVAL;
+    if (p->sweeps < 1 || (p->impl == CMF_FUSED && p->sweeps > 4) || p->sweeps > 64)
+        return CMF_EINVAL;
+    if (!(p->c > 0) || !(p->a > 0) || !(p->a1 > 0) || !(p->a2 >= 0)) return CMF_EINVAL;
+    if (!(p->rho > 0) || !(p->rho < 2)) return CMF_EINVAL;
+    if (!(p->r > 0) || !(p->sigma > 0) || !(p->tau > 0)) return CMF_EINVAL;
+    if (p->max_iter < 0 || p->check_every < 1 || !(p->tol_gap >= 0)) return CMF_EINVAL;
+    (void)L;
+    return CMF_OK;
+}
+
+cmf_status check_grid(int H, int W, int pitch) {
+    if (H < 1 || W < 1 || pitch < W) return CMF_EINVAL;
+    if ((double)H * (double)pitch > 4.0e12) return CMF_EINVAL;
+    return CMF_OK;
+}
+
+Alpha make_alpha(const float* d_alpha, float alpha0) { return Alpha{d_alpha, alpha0}; }
+
+Grid make_grid(int H, int W, int pitch) {
+    return Grid{H, W, pitch, (size_t)H * (size_t)pitch};
+}
+
+StepConfig make_step(const cmf_params& p, int L, bool potts) {
+    StepConfig s;
+    s.dr = p.algo == CMF_RPDRQ;
+    s.aniso = p.aniso != 0;
+    s.plain = p.impl == CMF_PLAIN;
+    s.ac = make_admm_coef(p, L);
+    s.dc = make_dr_coef(p, L, potts);
+    return s;
+}
+
+// ---- binary ---------------------------------------------------------------
+
+BinStateV ws_binary_state(char* ws, const WsLayout& w, const Grid& G, int storage) {
+    const size_t plane = G.plane;
+    const size_t es = dtype_size(storage);
+    char* base = ws + w.state;
+    BinStateV s;
+    s.u = (float*)base;
+    base += align_up(plane * 4);
+    void** f[4] = {&s.qx, &s.qy, &s.ps, &s.pt};
+    for (int i = 0; i < 4; ++i) {
+        *f[i] = base;
+        base += align_up(plane * es);
+    }
+    return s;
+}
+
+cudaError_t copy_plane(void* dst, const void* src, const Grid& G, size_t es, cudaStream_t st) {
+    if (dst == src) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst, G.pitch * es, src, G.pitch * es, G.W * es, G.H,
+                             cudaMemcpyDeviceToDevice, st);
+}
+
+cudaError_t copy_binary(const BinStateV& dst, const BinStateV& src, const Grid& G, int storage,
+                        cudaStream_t st) {
+    const size_t es = dtype_size(storage);
+    cudaError_t e;
+    if ((e = copy_plane(dst.u, src.u, G, 4, st)) != cudaSuccess) return e;
+    if ((e = copy_plane(dst.qx, src.qx, G, es, st)) != cudaSuccess) return e;
+    if ((e = copy_plane(dst.qy, src.qy, G, es, st)) != cudaSuccess) return e;
+    if ((e = copy_plane(dst.ps, src.ps, G, es, st)) != cudaSuccess) return e;
+    return copy_plane(dst.pt, src.pt, G, es, st);
+}
+
+struct BinaryCall {
+    BinProblem P;
+    BinStateV user, ws;
+    WsLayout w;
+    char* wsbase;
+    StepConfig cfg;
+    int storage;
+};
+
+cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, float alpha0,
+                          int H, int W, int pitch, const cmf_params* p, float* u, void* qx,
+                          void* qy, void* ps, void* pt, void* ws, size_t ws_bytes,
+                          BinaryCall& call) {
+    cmf_status s;
+    if ((s = check_params(p, 2)) != CMF_OK) return s;
+    if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
+    if (!Cs || !Ct || !u || !qx || !qy || !ps || !pt || !ws) return CMF_EINVAL;
+    if (!alpha && !(alpha0 >= 0.0f && isfinite(alpha0))) return CMF_EINVAL;
+    const size_t es = dtype_size(p->storage);
+    if (!aligned(u, 4) || !aligned(Cs, 4) || !aligned(Ct, 4) || (alpha && !aligned(alpha, 4)))
+        return CMF_EINVAL;
+    if (!aligned(qx, es) || !aligned(qy, es) || !aligned(ps, es) || !aligned(pt, es))
+        return CMF_EINVAL;
+    if (!aligned(ws, kAlign)) return CMF_EINVAL;
+    call.w = ws_layout(H, W, 2, pitch, *p, false);
+    if (ws_bytes < call.w.total) return CMF_ENOMEM;
+    call.P = BinProblem{Cs, Ct, make_alpha(alpha, alpha0), make_grid(H, W, pitch)};
+    call.user = BinStateV{u, qx, qy, ps, pt};
+    call.wsbase = (char*)ws;
+    call.ws = ws_binary_state(call.wsbase, call.w, call.P.g, p->storage);
+    call.cfg = make_step(*p, 2, false);
+    call.storage = p->storage;
+    return CMF_OK;
+}
+
+// Run n iterations starting from `cur` (0 = user buffers, 1 = workspace);
+// returns the index of the buffer set holding the result.
+cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st) {
+    float* tmp = (float*)(c.wsbase + c.w.tmp);
+    for (int i = 0; i < n; ++i) {
+        if (c.cfg.plain) {
+            cudaError_t e = binary_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
+            if (e != cudaSuccess) return e;
+            cur = 0;
+        } else {
+            const BinStateV& a = cur == 0 ? c.user : c.ws;
+            const BinStateV& b = cur == 0 ? c.ws : c.user;
+            cudaError_t e = binary_step(c.storage, c.P, a, b, c.cfg, tmp, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+cmf_status finish_eval(char* wsbase, const WsLayout& w, int nblocks, double* h_out,
+                       cudaStream_t st) {
+    double* partials = (double*)(wsbase + w.partials);
+    double* scal = (double*)(wsbase + w.scalars);
+    CMF_CUDA_TRY(reduce_partials(partials, nblocks, scal, st));
+    double h[3];
+    CMF_CUDA_TRY(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CMF_CUDA_TRY(cudaStreamSynchronize(st));
+    const double E = h[0], D = h[1];
+    h_out[0] = E;
+    h_out[1] = D;
+    h_out[2] = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
+    h_out[3] = sqrt(h[2] > 0 ? h[2] : 0.0);
+    return CMF_OK;
+}
+
+cmf_status binary_eval_state(const BinaryCall& c, const BinStateV& s, double* h_out,
+                             cudaStream_t st) {
+    CMF_CUDA_TRY(binary_eval(c.storage, c.P, s, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                             (double*)(c.wsbase + c.w.partials), st));
+    return finish_eval(c.wsbase, c.w, eval_blocks(c.P.g.H, c.P.g.W), h_out, st);
+}
+
+// ---- Potts ----------------------------------------------------------------
+
+PottsStateV ws_potts_state(char* ws, const WsLayout& w, const Grid& G, int L, int storage) {
+    const size_t plane = G.plane;
+    const size_t es = dtype_size(storage);
+    char* base = ws + w.state;
+    PottsStateV s;
+    s.u = (float*)base;
+    base += align_up(plane * 4 * L);
+    s.qx = base;
+    base += align_up(plane * es * L);
+    s.qy = base;
+    base += align_up(plane * es * L);
+    s.p = base;
+    base += align_up(plane * es * L);
+    s.ps = base;
+    return s;
+}
+
+cudaError_t copy_potts(const PottsStateV& dst, const PottsStateV& src, const Grid& G, int L,
+                       int storage, cudaStream_t st) {
+    const size_t es = dtype_size(storage);
+    cudaError_t e;
+    for (int i = 0; i < L; ++i) {
+        const size_t o4 = G.plane * 4 * i, oe = G.plane * es * i;
+        if ((e = copy_plane((char*)dst.u + o4, (char*)src.u + o4, G, 4, st)) != cudaSuccess)
+            return e;
+        if ((e = copy_plane((char*)dst.qx + oe, (char*)src.qx + oe, G, es, st)) != cudaSuccess)
+            return e;
+        if ((e = copy_plane((char*)dst.qy + oe, (char*)src.qy + oe, G, es, st)) != cudaSuccess)
+            return e;
+        if ((e = copy_plane((char*)dst.p + oe, (char*)src.p + oe, G, es, st)) != cudaSuccess)
+            return e;
+    }
+    return copy_plane(dst.ps, src.ps, G, es, st);
+}
+
+struct PottsCall {
+    PottsProblem P;
+    PottsStateV user, ws;
+    WsLayout w;
+    char* wsbase;
+    StepConfig cfg;
+    int storage;
+};
+
+cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0, int H, int W,
+                         int pitch, const cmf_params* p, float* u, void* qx, void* qy, void* pp,
+                         void* ps, void* ws, size_t ws_bytes, PottsCall& call) {
+    cmf_status s;
+    if (L < 2 || L > 64) return CMF_EINVAL;
+    if ((s = check_params(p, L)) != CMF_OK) return s;
+    if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
+    if (!C || !u || !qx || !qy || !pp || !ps || !ws) return CMF_EINVAL;
+    if (!alpha && !(alpha0 >= 0.0f && isfinite(alpha0))) return CMF_EINVAL;
+    const size_t es = dtype_size(p->storage);
+    if (!aligned(u, 4) || !aligned(C, 4) || (alpha && !aligned(alpha, 4))) return CMF_EINVAL;
+    if (!aligned(qx, es) || !aligned(qy, es) || !aligned(pp, es) || !aligned(ps, es))
+        return CMF_EINVAL;
+    if (!aligned(ws, kAlign)) return CMF_EINVAL;
+    call.w = ws_layout(H, W, L, pitch, *p, true);
+    if (ws_bytes < call.w.total) return CMF_ENOMEM;
+    call.P = PottsProblem{C, L, make_alpha(alpha, alpha0), make_grid(H, W, pitch)};
+    call.user = PottsStateV{u, qx, qy, pp, ps};
+    call.wsbase = (char*)ws;
+    call.ws = ws_potts_state(call.wsbase, call.w, call.P.g, L, p->storage);
+    call.cfg = make_step(*p, L, true);
+    call.storage = p->storage;
+    return CMF_OK;
+}
+
+cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st) {
+    float* tmp = (float*)(c.wsbase + c.w.tmp);
+    for (int i = 0; i < n; ++i) {
+        if (c.cfg.plain) {
+            cudaError_t e = potts_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
+            if (e != cudaSuccess) return e;
+            cur = 0;
+        } else {
+            const PottsStateV& a = cur == 0 ? c.user : c.ws;
+            const PottsStateV& b = cur == 0 ? c.ws : c.user;
+            cudaError_t e = potts_step(c.storage, c.P, a, b, c.cfg, tmp, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+cmf_status potts_eval_state(const PottsCall& c, const PottsStateV& s, double* h_out,
+                            cudaStream_t st) {
+    CMF_CUDA_TRY(potts_eval(c.storage, c.P, s, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                            (double*)(c.wsbase + c.w.partials), st));
+    return finish_eval(c.wsbase, c.w, eval_blocks(c.P.g.H, c.P.g.W), h_out, st);
+}
+
+// Shared solve loop: `run(n, cur)` advances, `eval(cur, out)` certifies.
+template <typename Run, typename Eval, typename Copy>
+cmf_status solve_loop(const cmf_params* p, Run run, Eval eval, Copy copy_back, double* h_hist,
+                      int hist_cap, int* h_iters, cudaStream_t st) {
+    int cur = 0, it = 0, nh = 0;
+    bool converged = false;
+    double out[4];
+    while (it < p->max_iter) {
+        const int k = p->check_every < p->max_iter - it ? p->check_every : p->max_iter - it;
+        CMF_CUDA_TRY(run(k, cur));
+        it += k;
+        cmf_status s = eval(cur, out);
+        if (s != CMF_OK) return s;
+        if (h_hist && nh < hist_cap) {
+            double* row = h_hist + 5 * (size_t)nh;
+            row[0] = it;
+            row[1] = out[0];
+            row[2] = out[1];
+            row[3] = out[2];
+            row[4] = out[3];
+        }
+        ++nh;
+        if (out[2] <= p->tol_gap) {
+            converged = true;
+            break;
+        }
+    }
+    if (cur != 0) CMF_CUDA_TRY(copy_back());
+    CMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_iters) *h_iters = it;
+    return converged ? CMF_OK : CMF_NOT_CONVERGED;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Public entry points
+// ===========================================================================
+extern "C" {
+
+cmf_status cmf_default_params(int algo, int L, cmf_params* p) {
+    if (!p || algo < CMF_PADMM || algo > CMF_RPDRQ || L < 2) return CMF_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->algo = algo;
+    p->storage = CMF_F32;
+    p->impl = CMF_FUSED;
+    p->aniso = 0;
+    p->sweeps = 1;
+    p->max_iter = 10000;
+    p->check_every = 10;
+    p->warm_start = 0;
+    p->use_graph = 0;
+    p->c = 0.3;
+    p->a = 8.0;
+    p->a1 = 2.0;
+    p->a2 = 2.0 * L;
+    p->rho = 1.9;
+    p->r = 1.618;
+    p->sigma = L == 2 ? 0.2 : 5.0;
+    p->tau = L == 2 ? 1.0 : 0.4;
+    p->tol_gap = 1e-4;
+    return CMF_OK;
+}
+
+const char* cmf_status_str(cmf_status s) {
+    switch (s) {
+        case CMF_OK: return "ok";
+        case CMF_EINVAL: return "invalid argument";
+        case CMF_ENOMEM: return "workspace too small";
+        case CMF_ECUDA: return "CUDA error";
+        case CMF_ETIMEOUT: return "device wait timed out";
+        case CMF_NOT_CONVERGED: return "not converged (max_iter reached)";
+    }
+    return "unknown status";
+}
+
+size_t cmf_workspace_bytes(int H, int W, int L, int pitch, const cmf_params* p) {
+    if (!p || check_grid(H, W, pitch) != CMF_OK || L < 2 || L > 64) return 0;
+    const size_t potts = ws_layout(H, W, L, pitch, *p, true).total;
+    if (L > 2) return potts;
+    const size_t binary = ws_layout(H, W, 2, pitch, *p, false).total;
+    return binary > potts ? binary : potts;  // L = 2 serves both models
+}
+
+cmf_status cmf_init_binary(const float* d_Cs, const float* d_Ct, int H, int W, int pitch,
+                           const cmf_params* p, float* d_u, void* d_qx, void* d_qy, void* d_ps,
+                           void* d_pt, void* stream) {
+    cmf_status s;
+    if ((s = check_params(p, 2)) != CMF_OK) return s;
+    if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
+    if (!d_Cs || !d_Ct || !d_u || !d_qx || !d_qy || !d_ps || !d_pt) return CMF_EINVAL;
+    BinProblem P{d_Cs, d_Ct, make_alpha(nullptr, 0.f), make_grid(H, W, pitch)};
+    BinStateV st{d_u, d_qx, d_qy, d_ps, d_pt};
+    CMF_CUDA_TRY(binary_init(p->storage, P, st, p->algo == CMF_RPDRQ, (float)p->tau,
+                             (cudaStream_t)stream));
+    return CMF_OK;
+}
+
+cmf_status cmf_iterate_binary(const float* d_Cs, const float* d_Ct, const float* d_alpha,
+                              float alpha0, int H, int W, int pitch, const cmf_params* p,
+                              int n_iter, float* d_u, void* d_qx, void* d_qy, void* d_ps,
+                              void* d_pt, void* d_ws, size_t ws_bytes, void* stream) {
+    BinaryCall c;
+    cmf_status s = binary_prepare(d_Cs, d_Ct, d_alpha, alpha0, H, W, pitch, p, d_u, d_qx, d_qy,
+                                  d_ps, d_pt, d_ws, ws_bytes, c);
+    if (s != CMF_OK) return s;
+    if (n_iter < 0) return CMF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int cur = 0;
+    CMF_CUDA_TRY(binary_run(c, n_iter, cur, st));
+    if (cur != 0) CMF_CUDA_TRY(copy_binary(c.user, c.ws, c.P.g, c.storage, st));
+    return CMF_OK;
+}
+
+cmf_status cmf_eval_binary(const float* d_Cs, const float* d_Ct, const float* d_alpha,
+                           float alpha0, int H, int W, int pitch, const cmf_params* p,
+                           const float* d_u, const void* d_qx, const void* d_qy,
+                           const void* d_ps, const void* d_pt, double* h_out, void* d_ws,
+                           size_t ws_bytes, void* stream) {
+    if (!h_out) return CMF_EINVAL;
+    BinaryCall c;
+    cmf_status s = binary_prepare(d_Cs, d_Ct, d_alpha, alpha0, H, W, pitch, p, (float*)d_u,
+                                  (void*)d_qx, (void*)d_qy, (void*)d_ps, (void*)d_pt, d_ws,
+                                  ws_bytes, c);
+    if (s != CMF_OK) return s;
+    return binary_eval_state(c, c.user, h_out, (cudaStream_t)stream);
+}
+
+cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d_alpha,
+                            float alpha0, int H, int W, int pitch, const cmf_params* p,
+                            float* d_u, void* d_qx, void* d_qy, void* d_ps, void* d_pt,
+                            double* h_hist, int hist_cap, int* h_iters, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+    BinaryCall c;
+    cmf_status s = binary_prepare(d_Cs, d_Ct, d_alpha, alpha0, H, W, pitch, p, d_u, d_qx, d_qy,
+                                  d_ps, d_pt, d_ws, ws_bytes, c);
+    if (s != CMF_OK) return s;
+    if (hist_cap < 0) return CMF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->warm_start)
+        CMF_CUDA_TRY(binary_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    return solve_loop(
+        p, [&](int n, int& cur) { return binary_run(c, n, cur, st); },
+        [&](int cur, double* out) {
+            return binary_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
+        },
+        [&]() { return copy_binary(c.user, c.ws, c.P.g, c.storage, st); }, h_hist, hist_cap,
+        h_iters, st);
+}
+
+cmf_status cmf_init_potts(const float* d_C, int L, int H, int W, int pitch, const cmf_params* p,
+                          float* d_u, void* d_qx, void* d_qy, void* d_p, void* d_ps,
+                          void* stream) {
+    cmf_status s;
+    if (L < 2 || L > 64) return CMF_EINVAL;
+    if ((s = check_params(p, L)) != CMF_OK) return s;
+    if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
+    if (!d_C || !d_u || !d_qx || !d_qy || !d_p || !d_ps) return CMF_EINVAL;
+    PottsProblem P{d_C, L, make_alpha(nullptr, 0.f), make_grid(H, W, pitch)};
+    PottsStateV st{d_u, d_qx, d_qy, d_p, d_ps};
+    CMF_CUDA_TRY(potts_init(p->storage, P, st, p->algo == CMF_RPDRQ, (float)p->tau,
+                            (cudaStream_t)stream));
+    return CMF_OK;
+}
+
+cmf_status cmf_iterate_potts(const float* d_C, int L, const float* d_alpha, float alpha0, int H,
+                             int W, int pitch, const cmf_params* p, int n_iter, float* d_u,
+                             void* d_qx, void* d_qy, void* d_p, void* d_ps, void* d_ws,
+                             size_t ws_bytes, void* stream) {
+    PottsCall c;
+    cmf_status s = potts_prepare(d_C, L, d_alpha, alpha0, H, W, pitch, p, d_u, d_qx, d_qy, d_p,
+                                 d_ps, d_ws, ws_bytes, c);
+    if (s != CMF_OK) return s;
+    if (n_iter < 0) return CMF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int cur = 0;
+    CMF_CUDA_TRY(potts_run(c, n_iter, cur, st));
+    if (cur != 0) CMF_CUDA_TRY(copy_potts(c.user, c.ws, c.P.g, L, c.storage, st));
+    return CMF_OK;
+}
+
+cmf_status cmf_eval_potts(const float* d_C, int L, const float* d_alpha, float alpha0, int H,
+                          int W, int pitch, const cmf_params* p, const float* d_u,
+                          const void* d_qx, const void* d_qy, const void* d_p, const void* d_ps,
+                          double* h_out, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!h_out) return CMF_EINVAL;
+    PottsCall c;
+    cmf_status s = potts_prepare(d_C, L, d_alpha, alpha0, H, W, pitch, p, (float*)d_u,
+                                 (void*)d_qx, (void*)d_qy, (void*)d_p, (void*)d_ps, d_ws,
+                                 ws_bytes, c);
+    if (s != CMF_OK) return s;
+    return potts_eval_state(c, c.user, h_out, (cudaStream_t)stream);
+}
+
+cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float alpha0, int H,
+                           int W, int pitch, const cmf_params* p, float* d_u, void* d_qx,
+                           void* d_qy, void* d_p, void* d_ps, double* h_hist, int hist_cap,
+                           int* h_iters, void* d_ws, size_t ws_bytes, void* stream) {
+    PottsCall c;
+    cmf_status s = potts_prepare(d_C, L, d_alpha, alpha0, H, W, pitch, p, d_u, d_qx, d_qy, d_p,
+                                 d_ps, d_ws, ws_bytes, c);
+    if (s != CMF_OK) return s;
+    if (hist_cap < 0) return CMF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p->warm_start)
+        CMF_CUDA_TRY(potts_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    return solve_loop(
+        p, [&](int n, int& cur) { return potts_run(c, n, cur, st); },
+        [&](int cur, double* out) {
+            return potts_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
+        },
+        [&]() { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); }, h_hist, hist_cap,
+        h_iters, st);
+}
+
+}  // extern "C"

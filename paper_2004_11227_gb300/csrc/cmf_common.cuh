@@ -1,0 +1,124 @@
+// Shared device helpers of libcmf: storage types, projections, coefficient
+// bundles and the launch-error plumbing.  Everything here is float32
+// arithmetic on values stored as float32 / float16 / bfloat16.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cmf.h"
+
+namespace cmf {
+
+// ---- storage types -------------------------------------------------------
+
+template <typename S> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ldw(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ float rt(float v) { return v; }
+};
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ldw(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float rt(float v) {
+        return __half2float(__float2half_rn(v));
+    }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+        return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ float ldw(const __nv_bfloat16* p) {
+        return __bfloat162float(*p);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+        *p = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ float rt(float v) {
+        return __bfloat162float(__float2bfloat16_rn(v));
+    }
+};
+
+inline size_t dtype_size(int storage) { return storage == CMF_F32 ? 4 : 2; }
+
+// ---- pointwise projections (Eq. projections) -----------------------------
+
+// P_alpha: q / max(1, |q|/alpha); alpha <= 0 gives 0.  Anisotropic option:
+// clamp each component to [-alpha, alpha].
+template <bool ANISO>
+__device__ __forceinline__ void project_alpha(float& x, float& y, float al) {
+    al = fmaxf(al, 0.0f);
+    if (ANISO) {
+        x = fminf(fmaxf(x, -al), al);
+        y = fminf(fmaxf(y, -al), al);
+    } else {
+        float n2 = x * x + y * y;
+        if (n2 > al * al) {
+            float s = al * rsqrtf(n2);
+            x *= s;
+            y *= s;
+        }
+    }
+}
+
+// ---- alpha: a plane or a constant ----------------------------------------
+
+struct Alpha {
+    const float* plane;  // NULL => constant
+    float value;
+    __device__ __forceinline__ float at(size_t k) const {
+        return plane ? __ldg(plane + k) : value;
+    }
+};
+
+// ---- grid geometry -------------------------------------------------------
+
+struct Grid {
+    int H, W, pitch;
+    size_t plane;  // H * pitch
+    __device__ __forceinline__ size_t idx(int r, int c) const {
+        return (size_t)r * (size_t)pitch + (size_t)c;
+    }
+};
+
+// ---- ADMM coefficients (float32, precomputed on the host) ----------------
+// One formula covers rpADMMII (Eckstein-Bertsekas) and rpADMMI/pADMMI
+// (Fortin-Glowinski):
+//   p update uses rho_p (= rho for EB, 1 for FG),
+//   u <- u - cu * ((Ap)^{k+1} - omr * (Ap)^k + rho_p * div q^{k+1})
+// with cu = c, omr = 1 - rho for EB and cu = r c, omr = 0 for FG.
+struct AdmmCoef {
+    float inv_a;     // 1/a
+    float inv_c;     // 1/c
+    float rho_p;     // rho (EB) or 1 (FG)
+    float rho_a1;    // rho_p / a1
+    float inv_a1;    // 1 / a1
+    float inv_a2;    // 1 / a2 (Potts)
+    float cu;        // c (EB) or r c (FG)
+    float omr;       // 1 - rho (EB) or 0 (FG)
+};
+
+// ---- DR coefficients -----------------------------------------------------
+struct DrCoef {
+    float sigma, tau, rho;
+    float inv_st;    // 1 / (sigma tau)
+    float kappa;     // 2 (binary) or L + 1 (Potts)
+    float Lm1;       // L - 1 (Potts)
+    int sweeps;
+};
+
+AdmmCoef make_admm_coef(const cmf_params& p, int L);
+DrCoef make_dr_coef(const cmf_params& p, int L, bool potts);
+
+}  // namespace cmf
+
+#define CMF_CUDA_TRY(expr)                                       \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) return CMF_ECUDA;                 \
+    } while (0)

@@ -1,0 +1,144 @@
+// Internal interface between the C-ABI layer (cmf_api.cu) and the kernel
+// translation units.  Not installed; not part of the public ABI.
+#pragma once
+
+#include "cmf_common.cuh"
+
+namespace cmf {
+
+constexpr int EVAL_ROWS = 4;  // rows per thread in the certificate kernels
+
+// Read-only problem data of the binary model.
+struct BinProblem {
+    const float* Cs;
+    const float* Ct;
+    Alpha alpha;
+    Grid g;
+};
+
+// Binary state planes with a typed flow storage.
+template <typename S>
+struct BinState {
+    float* u;
+    S* qx;
+    S* qy;
+    S* ps;
+    S* pt;
+};
+
+// Type-erased binary state (what the host layer carries around).
+struct BinStateV {
+    float* u;
+    void* qx;
+    void* qy;
+    void* ps;
+    void* pt;
+    template <typename S>
+    BinState<S> as() const {
+        return BinState<S>{u, (S*)qx, (S*)qy, (S*)ps, (S*)pt};
+    }
+};
+
+// Potts problem data: L cost planes.
+struct PottsProblem {
+    const float* C;
+    int L;
+    Alpha alpha;
+    Grid g;
+};
+
+template <typename S>
+struct PottsState {
+    float* u;   // L planes
+    S* qx;      // L planes
+    S* qy;      // L planes
+    S* p;       // L planes
+    S* ps;      // one plane
+};
+
+struct PottsStateV {
+    float* u;
+    void* qx;
+    void* qy;
+    void* p;
+    void* ps;
+    template <typename S>
+    PottsState<S> as() const {
+        return PottsState<S>{u, (S*)qx, (S*)qy, (S*)p, (S*)ps};
+    }
+};
+
+// What one iteration launch needs besides the buffers.
+struct StepConfig {
+    bool dr;      // rPDRQ (else an ADMM variant)
+    bool aniso;
+    bool plain;   // one kernel per step (else fused)
+    AdmmCoef ac;
+    DrCoef dc;
+};
+
+// Block-level FP64 reduction of three accumulators; thread 0 stores the
+// block's triple at partials[3 * linear block index].
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void block_reduce3_store(double a, double b, double c,
+                                                    double* partials) {
+    __shared__ double red[3][32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = a;
+        red[1][tid >> 5] = b;
+        red[2][tid >> 5] = c;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        a = tid < nw ? red[0][tid] : 0.0;
+        b = tid < nw ? red[1][tid] : 0.0;
+        c = tid < nw ? red[2][tid] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (tid == 0) {
+            const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+            partials[3 * blk + 0] = a;
+            partials[3 * blk + 1] = b;
+            partials[3 * blk + 2] = c;
+        }
+    }
+}
+
+// --- launchers (binary) ---
+cudaError_t binary_init(int storage, const BinProblem& P, const BinStateV& s, bool dr, float tau,
+                        cudaStream_t st);
+cudaError_t binary_step(int storage, const BinProblem& P, const BinStateV& a, const BinStateV& b,
+                        const StepConfig& cfg, float* tmp, cudaStream_t st);
+cudaError_t binary_eval(int storage, const BinProblem& P, const BinStateV& s, bool aniso, bool dr,
+                        float tau, double* partials, cudaStream_t st);
+int eval_blocks(int H, int W);
+
+// --- launchers (Potts) ---
+cudaError_t potts_init(int storage, const PottsProblem& P, const PottsStateV& s, bool dr,
+                       float tau, cudaStream_t st);
+cudaError_t potts_step(int storage, const PottsProblem& P, const PottsStateV& a,
+                       const PottsStateV& b, const StepConfig& cfg, float* tmp, cudaStream_t st);
+cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s, bool aniso,
+                       bool dr, float tau, double* partials, cudaStream_t st);
+
+// One sRBGS preconditioner application as separate half-sweep launches
+// (plain form): red, then (black, red) x D.sweeps.
+cudaError_t halfsweeps(const Grid& G, float* u, const float* b, const DrCoef& D,
+                       cudaStream_t st);
+
+// --- reductions ---
+// Sum n partial triples in a fixed order into out[0..2] (one block).
+cudaError_t reduce_partials(const double* partials, int n, double* out, cudaStream_t st);
+
+}  // namespace cmf

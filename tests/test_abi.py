@@ -1,0 +1,121 @@
+"""The C-ABI library loads, exports every symbol include/cmf.h declares, and
+rejects bad arguments with error codes before touching the GPU (these calls
+run on a machine without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cmf():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2004_11227_gb300 import cmf as m
+
+    return m
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cmf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cmf_[a-z_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree(cmf):
+    assert _declared() == sorted(cmf.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(cmf):
+    lib = ctypes.CDLL(cmf.library_path())
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_default_params_are_the_papers(cmf):
+    p = cmf.default_params(cmf.RPADMM_EB, 2)
+    assert (p.c, p.a, p.a1, p.rho, p.r) == (0.3, 8.0, 2.0, 1.9, 1.618)
+    assert (p.sigma, p.tau, p.sweeps) == (0.2, 1.0, 1)
+    q = cmf.default_params(cmf.RPDRQ, 4)
+    assert (q.sigma, q.tau, q.a2) == (5.0, 0.4, 8.0)
+    with pytest.raises(cmf.CmfError):
+        cmf.default_params(7, 2)
+
+
+def test_workspace_bytes(cmf):
+    p = cmf.default_params(cmf.RPADMM_EB, 2)
+    n1 = cmf.cmf_workspace_bytes(64, 64, 2, 64, p)
+    n2 = cmf.cmf_workspace_bytes(128, 64, 2, 64, p)
+    assert n1 > 5 * 64 * 64 * 4 and n2 > n1
+    p16 = cmf.default_params(cmf.RPADMM_EB, 2, storage=cmf.F16)
+    assert cmf.cmf_workspace_bytes(64, 64, 2, 64, p16) < n1
+    assert cmf.cmf_workspace_bytes(64, 64, 4, 64, p) > n1
+    assert cmf.cmf_workspace_bytes(0, 64, 2, 64, p) == 0
+    assert cmf.cmf_workspace_bytes(64, 64, 2, 32, p) == 0
+
+
+def _fake(n=8):
+    # host memory standing in for device pointers: the calls below must fail
+    # validation before any pointer is dereferenced or any kernel launched
+    buf = (ctypes.c_float * (n * 64 + 256))()
+    addr = ctypes.cast(buf, ctypes.c_void_p).value
+    return (addr + 255) // 256 * 256, buf
+
+
+def test_bad_arguments_rejected_without_launch(cmf):
+    lib = cmf.lib()
+    p = cmf.default_params(cmf.RPADMM_EB, 2)
+    ptr, keep = _fake()
+    P = ctypes.byref(p)
+    args = lambda H, W, pitch, n, ws_bytes: (ptr, ptr, None, 0.5, H, W, pitch, P, n,
+                                              ptr, ptr, ptr, ptr, ptr, ptr, ws_bytes, None)
+    assert lib.cmf_iterate_binary(*args(0, 8, 8, 1, 1 << 20)) == cmf.EINVAL
+    assert lib.cmf_iterate_binary(*args(8, 8, 4, 1, 1 << 20)) == cmf.EINVAL
+    assert lib.cmf_iterate_binary(*args(8, 8, 8, -1, 1 << 30)) == cmf.EINVAL
+    assert lib.cmf_iterate_binary(*args(8, 8, 8, 1, 16)) == cmf.ENOMEM
+    # negative constant alpha
+    assert lib.cmf_iterate_binary(ptr, ptr, None, -1.0, 8, 8, 8, P, 1, ptr, ptr, ptr, ptr, ptr,
+                                  ptr, 1 << 20, None) == cmf.EINVAL
+    # NULL state pointer
+    assert lib.cmf_iterate_binary(ptr, ptr, None, 0.5, 8, 8, 8, P, 1, None, ptr, ptr, ptr, ptr,
+                                  ptr, 1 << 20, None) == cmf.EINVAL
+    for bad in [dict(algo=9), dict(storage=5), dict(impl=3), dict(sweeps=0), dict(c=0.0),
+                dict(rho=2.0), dict(rho=0.0), dict(check_every=0), dict(sweeps=5)]:
+        q = cmf.default_params(cmf.RPADMM_EB, 2)
+        for k, v in bad.items():
+            setattr(q, k, v)
+        assert lib.cmf_iterate_binary(ptr, ptr, None, 0.5, 8, 8, 8, ctypes.byref(q), 1, ptr,
+                                      ptr, ptr, ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL, bad
+    # Potts: L out of range
+    pp = cmf.default_params(cmf.RPADMM_EB, 4)
+    assert lib.cmf_iterate_potts(ptr, 1, None, 0.5, 8, 8, 8, ctypes.byref(pp), 1, ptr, ptr, ptr,
+                                 ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL
+    assert lib.cmf_iterate_potts(ptr, 65, None, 0.5, 8, 8, 8, ctypes.byref(pp), 1, ptr, ptr,
+                                 ptr, ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL
+    out = (ctypes.c_double * 4)()
+    assert lib.cmf_eval_binary(ptr, ptr, None, 0.5, 8, 8, 8, P, ptr, ptr, ptr, ptr, ptr, None,
+                               ptr, 1 << 20, None) == cmf.EINVAL
+    assert lib.cmf_solve_binary(ptr, ptr, None, 0.5, 8, 8, 8, P, ptr, ptr, ptr, ptr, ptr, None,
+                                -1, None, ptr, 1 << 20, None) == cmf.EINVAL
+    del keep, out
+
+
+def test_status_strings(cmf):
+    lib = cmf.lib()
+    for s in range(6):
+        assert lib.cmf_status_str(s)
+    assert b"unknown" in lib.cmf_status_str(42)
+
+
+def test_product_path_does_not_touch_oracle():
+    """The CUDA package never imports the test oracle."""
+    pkg = os.path.join(ROOT, "paper_2004_11227_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower() or f == "synth.py", f

@@ -1,0 +1,199 @@
+"""GPU parity of the binary solver (through the C ABI) against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (float32 state, float32 arithmetic): max |u - u_oracle| <= 1e-4
+and flows within 1e-4 after a fixed iteration count; certificates (E, D)
+within 1e-5 relative and the relative gap within 1e-6 absolute of the
+oracle's evaluation of the same state; a solve to gap 1e-4 is certified by the
+oracle and its thresholded labelling agrees with the oracle's converged one
+on >= 99.9% of pixels.  float16 / bfloat16 flow storage is checked with
+tolerances derived from their unit roundoff (2^-11 and 2^-8)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2004_11227_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = [0, 1, 2, 3]
+TOL_U = 1e-4
+
+
+@pytest.fixture(scope="module")
+def cmf():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2004_11227_gb300 import cmf as m
+
+    return m
+
+
+def _cases():
+    return {
+        "disk64": (synth.config1(), 200),
+        "shapes37x53": (synth.config2(37, 53), 60),
+        "row1x67": (synth.random_binary(1, 67, seed=3, alpha=0.3), 40),
+        "col45x1": (synth.random_binary(45, 1, seed=4, alpha=0.3), 40),
+        "tiny2x3": (synth.random_binary(2, 3, seed=5, alpha=0.2, field_alpha=True), 30),
+        "ragged70x33": (synth.random_binary(70, 33, seed=6, alpha=0.4, field_alpha=True), 50),
+    }
+
+
+def _gpu_run(cmf, inst, algo, n, **kw):
+    p = cmf.default_params(algo, 2, **kw)
+    b = cmf.alloc_binary(inst, p)
+    cmf.cmf_init_binary(b)
+    cmf.cmf_iterate_binary(b, n)
+    torch.cuda.synchronize()
+    return b
+
+
+def _oracle_run(inst, algo, n, aniso=0, sweeps=1):
+    p = O.default_params(algo, 2, aniso=aniso, sweeps=sweeps)
+    return O.binary_run(inst.costs[0], inst.costs[1], inst.alpha, p, n), p
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("case", list(_cases()))
+def test_iterations_match_oracle_f32(cmf, case, algo, impl):
+    inst, n = _cases()[case]
+    b = _gpu_run(cmf, inst, algo, n, impl=impl)
+    got = b.state()
+    ref, _ = _oracle_run(inst, algo, n)
+    for k in ("u", "qx", "qy", "ps", "pt"):
+        err = np.abs(got[k] - ref[k]).max()
+        assert err <= TOL_U, (k, err)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_anisotropic_and_multisweep(cmf, algo):
+    inst = synth.random_binary(29, 41, seed=8, alpha=0.35, field_alpha=True)
+    for aniso, sweeps in [(1, 1), (0, 3)]:
+        b = _gpu_run(cmf, inst, algo, 40, aniso=aniso, sweeps=sweeps)
+        ref, _ = _oracle_run(inst, algo, 40, aniso=aniso, sweeps=sweeps)
+        assert np.abs(b.state()["u"] - ref["u"]).max() <= TOL_U
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_fused_equals_plain(cmf, algo):
+    inst = synth.config2(96, 80)
+    a = _gpu_run(cmf, inst, algo, 30, impl=0).state()
+    b = _gpu_run(cmf, inst, algo, 30, impl=1).state()
+    for k in a:
+        assert np.abs(a[k] - b[k]).max() <= 1e-5, k
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_certificates_match_oracle(cmf, algo):
+    inst = synth.config2(70, 90)
+    b = _gpu_run(cmf, inst, algo, 25)
+    E, D, gap, res = cmf.cmf_eval_binary(b)
+    st = b.state()
+    p = O.default_params(algo, 2)
+    Eo, Do, gapo, reso = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, st, p)
+    assert abs(E - Eo) <= 1e-5 * abs(Eo)
+    assert abs(D - Do) <= 1e-5 * abs(Eo)
+    assert abs(gap - gapo) <= 1e-6 + 1e-4 * abs(gapo)
+    assert abs(res - reso) <= 1e-4 * reso + 1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [(1, 3e-3), (2, 3e-2)])
+@pytest.mark.parametrize("algo", [0, 2, 3])
+def test_half_storage_tracks_oracle(cmf, storage, tol, algo):
+    inst = synth.config1()
+    b = _gpu_run(cmf, inst, algo, 30, storage=storage)
+    ref, _ = _oracle_run(inst, algo, 30)
+    assert np.abs(b.state()["u"] - ref["u"]).max() <= tol
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_solve_certified_by_oracle(cmf, algo):
+    inst = synth.config2(160, 192)
+    p = cmf.default_params(algo, 2, tol_gap=1e-4, max_iter=20000, check_every=10)
+    b = cmf.alloc_binary(inst, p)
+    status, iters, hist = cmf.cmf_solve_binary(b)
+    assert status == cmf.OK and hist[-1, 3] <= 1e-4 and iters == int(hist[-1, 0])
+    st = b.state()
+    po = O.default_params(algo, 2)
+    E, D, gap, res = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, st, po)
+    assert gap <= 1.01e-4
+    ref, _, _ = O.solve(inst, algo, tol=1e-7, max_iter=40000)
+    agree = np.mean(O.binary_labels(st["u"]) == O.binary_labels(ref["u"]))
+    assert agree >= 0.999, agree
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_half_storage_solve_reaches_gap(cmf, storage):
+    inst = synth.config2(128, 128)
+    p = cmf.default_params(2, 2, storage=storage, tol_gap=1e-4, max_iter=20000)
+    b = cmf.alloc_binary(inst, p)
+    status, iters, hist = cmf.cmf_solve_binary(b)
+    assert status == cmf.OK
+    st = b.state()
+    E, D, gap, res = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, st,
+                                   O.default_params(2, 2))
+    assert gap <= 2e-4
+    ref, _, _ = O.solve(inst, 2, tol=1e-7, max_iter=40000)
+    assert np.mean(O.binary_labels(st["u"]) == O.binary_labels(ref["u"])) >= 0.999
+
+
+def test_warm_start_split_equals_single_run(cmf):
+    inst = synth.config2(64, 96)
+    a = _gpu_run(cmf, inst, 2, 40).state()
+    p = cmf.default_params(2, 2)
+    b = cmf.alloc_binary(inst, p)
+    cmf.cmf_init_binary(b)
+    cmf.cmf_iterate_binary(b, 17)
+    cmf.cmf_iterate_binary(b, 23)
+    torch.cuda.synchronize()
+    s = b.state()
+    for k in a:
+        np.testing.assert_array_equal(a[k], s[k])
+
+
+def _window_step_check(cmf, inst, algo, k_before, windows, margin=8):
+    """Full-size state: GPU runs k_before iterations, then one more; the
+    oracle runs that last iteration on cropped windows (with a margin that
+    covers the iteration's stencil reach) and the window interiors must
+    match element by element."""
+    p = cmf.default_params(algo, 2)
+    b = cmf.alloc_binary(inst, p)
+    cmf.cmf_init_binary(b)
+    cmf.cmf_iterate_binary(b, k_before)
+    torch.cuda.synchronize()
+    W = b.W
+    before = {k: getattr(b, k)[:, :W].float() for k in ("u", "qx", "qy", "ps", "pt")}
+    cmf.cmf_iterate_binary(b, 1)
+    torch.cuda.synchronize()
+    after = {k: getattr(b, k)[:, :W].float() for k in ("u", "qx", "qy", "ps", "pt")}
+    po = O.default_params(algo, 2)
+    alpha = inst.alpha_field()
+    for (r0, c0, h, w) in windows:
+        R0, C0 = max(r0 - margin, 0), max(c0 - margin, 0)
+        R1, C1 = min(r0 + h + margin, b.H), min(c0 + w + margin, b.W)
+        st = {k: v[R0:R1, C0:C1].cpu().double().numpy() for k, v in before.items()}
+        res = O.binary_run(inst.costs[0][R0:R1, C0:C1], inst.costs[1][R0:R1, C0:C1],
+                           alpha[R0:R1, C0:C1], po, 1, st)
+        for k in res:
+            # interior = the window, minus a margin wherever the crop is not the grid edge
+            ri0 = r0 - R0 if R0 > 0 else 0
+            ci0 = c0 - C0 if C0 > 0 else 0
+            got = after[k][r0:r0 + h, c0:c0 + w].cpu().double().numpy()
+            ref = res[k][ri0:ri0 + h, ci0:ci0 + w]
+            err = np.abs(got - ref).max()
+            assert err <= 2e-5, (k, (r0, c0), err)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_full_size_1024_windows(cmf, algo):
+    """1024^2 (the benchmark workload) in the benchmark's launch
+    configuration: windows at corners, edges, the centre and a ragged spot."""
+    inst = synth.config2()
+    wins = [(0, 0, 48, 48), (0, 1024 - 40, 40, 40), (1024 - 33, 0, 33, 64),
+            (1024 - 50, 1024 - 50, 50, 50), (500, 500, 64, 64), (257, 771, 31, 45)]
+    _window_step_check(cmf, inst, algo, 37, wins)
