@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: continuous max-flow segmentation on GB300.
+
+Workload: the binary model on a 1024 x 1024 image of eight random disks /
+rectangles (0.8 on 0.2, noise sigma 0.15), edge-weighted alpha(x) =
+0.5 exp(-10 |grad I|), costs C_s = |I - 0.2|, C_t = |I - 0.8|.  One step = one
+solve from a cold start to a relative primal-dual gap <= 1e-4 (certificates
+every 10 iterations) with the fused float32 rPDRQ solver.
+
+Metric: pixel*label*iterations per second (binary counts as L = 2), plus the
+time to the 1e-4 gap of the fused solver and of the plain one-kernel-per-step
+form.  The L2 cache (129 MB) is flushed before every timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank solves its own instance (seed 2 + rank): weak scaling,
+no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 1024
+L = 2
+TOL = 1e-4
+CHECK_EVERY = 10
+FLAGSHIP = 3          # rPDRQ
+BYTES_PER_PX = 52     # 10 state floats r+w, C_s, C_t, alpha: algorithmic bytes / pixel / iteration
+WORKLOAD = "binary 1024x1024 shapes, edge-weighted alpha, solve to gap 1e-4"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[2 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _traffic(kernel_src: str, kernel_name: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d[kernel_name]
+        sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()
+        if ent.get("src_sha256") != sha:
+            return None
+        return float(ent["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_oracle_rate(inst, n_iter: int):
+    """The FP64 oracle (single-threaded C) on a bounded sample: n_iter
+    rPDRQ iterations of the full workload; returns px*label*it/s."""
+    import oracle
+
+    oracle.build()
+    p = oracle.default_params(oracle.RPDRQ, 2)
+    t0 = time.perf_counter()
+    oracle.binary_run(inst.costs[0], inst.costs[1], inst.alpha, p, n_iter)
+    dt = time.perf_counter() - t0
+    return H * W * L * n_iter / dt, dt
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from paper_2004_11227_gb300 import synth
+
+    inst = synth.config2(H, W, seed=2)
+    n_iter = 40
+    cpu_oracle_rate(inst, 2)  # build + warm the page cache
+    for _ in range(args.warmup):
+        cpu_oracle_rate(inst, 2)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(inst, n_iter)
+        rates.append(r)
+        times.append(dt)
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": "pixel*label*iterations/s", "value": value,
+        "unit": "px*label*it/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L,
+                                        "algo": "rPDRQ"},
+        "cpu_baseline": {"value": value, "unit": "px*label*it/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_iter} rPDRQ iterations of the full 1024x1024 workload "
+                                   "per step, FP64 C oracle, one thread"},
+        "e2e": {"value": value, "unit": "px*label*it/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    from paper_2004_11227_gb300 import cmf, synth
+
+    world, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    inst = synth.config2(H, W, seed=2 + rank)
+    p = cmf.default_params(FLAGSHIP, L, tol_gap=TOL, max_iter=20000, check_every=CHECK_EVERY)
+    b = cmf.alloc_binary(inst, p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(buf):
+        st, iters, hist = cmf.cmf_solve_binary(buf)
+        assert st == cmf.OK, "solve did not reach the gap"
+        return iters, hist
+
+    for _ in range(max(args.warmup, 3)):
+        step(b)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    times, iters_all = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        iters, hist = step(b)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        iters_all.append(iters)
+    barrier()
+    clocks = sampler.stop()
+
+    total_ms = float(np.sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        it_t = torch.tensor([float(np.sum(iters_all))], device=dev)
+        dist.all_reduce(it_t)
+        total_units = H * W * L * float(it_t.item())
+    else:
+        total_units = H * W * L * float(np.sum(iters_all))
+    value = total_units / (total_ms / 1000.0)
+    iters = int(np.median(iters_all))
+    n_checks = int(np.ceil(iters / CHECK_EVERY))
+    launches = args.steps * (1 + iters + 2 * n_checks)  # init + fused iterations + eval/reduce
+
+    # --- end to end through the C ABI with host buffers -------------------------------
+    costs_h = [torch.from_numpy(np.ascontiguousarray(np.pad(
+        inst.costs[i], ((0, 0), (0, b.pitch - W))))).pin_memory() for i in range(2)]
+    alpha_h = torch.from_numpy(np.ascontiguousarray(np.pad(
+        inst.alpha, ((0, 0), (0, b.pitch - W))))).pin_memory()
+    u_h = torch.empty((H, b.pitch), dtype=torch.float32).pin_memory()
+    e2e_times = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.Cs.copy_(costs_h[0], non_blocking=True)
+        b.Ct.copy_(costs_h[1], non_blocking=True)
+        b.alpha.copy_(alpha_h, non_blocking=True)
+        step(b)
+        u_h.copy_(b.u, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_ms = float(np.sum(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = total_units / (e2e_ms / 1000.0)
+    h2d = 3 * H * b.pitch * 4
+    d2h = H * b.pitch * 4
+
+    # --- dominant kernel: fused iteration, back-to-back launches -----------------------
+    cmf.cmf_init_binary(b)
+    cmf.cmf_iterate_binary(b, 20)
+    flush.zero_()
+    torch.cuda.synchronize()
+    n_rf = 200
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    cmf.cmf_iterate_binary(b, n_rf)
+    e1.record()
+    e1.synchronize()
+    kern_ms = e0.elapsed_time(e1) / n_rf
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_PX * H * W / (kern_ms / 1000.0) / 1e9
+    traffic = _traffic("paper_2004_11227_gb300/csrc/cmf_binary.cu", "k_binary_dr_fused")
+
+    # --- plain one-kernel-per-step form and the other algorithms: time to gap ---------
+    def time_to_gap(algo, impl):
+        q = cmf.default_params(algo, L, tol_gap=TOL, max_iter=20000, check_every=CHECK_EVERY,
+                               impl=impl)
+        bb = cmf.alloc_binary(inst, q)
+        cmf.cmf_solve_binary(bb)  # warm
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            st, it, _ = cmf.cmf_solve_binary(bb)
+            a1.record()
+            a1.synchronize()
+            ts.append(a0.elapsed_time(a1))
+        return float(np.median(ts)), it
+
+    ttg = {}
+    for algo in (0, 1, 2, 3):
+        for impl in (0, 1):
+            ms, it = time_to_gap(algo, impl)
+            ttg[f"{cmf.ALGO_NAMES[algo]}_{'fused' if impl == 0 else 'plain'}"] = {
+                "ms": round(ms, 3), "iters": it}
+    fused_ms = ttg["rPDRQ_fused"]["ms"]
+    plain_ms = ttg["rPDRQ_plain"]["ms"]
+
+    if rank == 0:
+        rate, dt = cpu_oracle_rate(inst, 150)
+        line = {
+            "metric": "pixel*label*iterations/s", "value": value, "unit": "px*label*it/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "algo": "rPDRQ fused",
+                       "check_every": CHECK_EVERY, "tol_gap": TOL,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_gap_ms": {"fused": fused_ms, "plain": plain_ms,
+                               "speedup_fused_vs_plain": round(plain_ms / fused_ms, 3),
+                               "iterations": iters, "all": ttg},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_binary_dr_fused", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": BYTES_PER_PX * H * W,
+                         "launch_ms": kern_ms},
+            "cpu_baseline": {"value": rate, "unit": "px*label*it/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "150 rPDRQ iterations of the full 1024x1024 workload, "
+                                       f"FP64 C oracle, one thread ({dt:.1f} s)"},
+            "e2e": {"value": e2e_value, "unit": "px*label*it/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

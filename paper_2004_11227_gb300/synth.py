@@ -220,9 +220,9 @@ def config1() -> Instance:
     return binary_disk(64, 64, seed=1)
 
 
-def config2(H: int = 1024, W: int = 1024) -> Instance:
+def config2(H: int = 1024, W: int = 1024, seed: int = 2) -> Instance:
     """Binary 1024^2 shapes, edge-weighted alpha (run to gap 1e-4)."""
-    return binary_shapes(H, W, seed=2)
+    return binary_shapes(H, W, seed=seed)
 
 
 def config3(H: int = 2048, W: int = 2048) -> Instance:
