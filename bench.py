@@ -5,7 +5,7 @@ Workload: the binary model on a 1024 x 1024 image of eight random disks /
 rectangles (0.8 on 0.2, noise sigma 0.15), edge-weighted alpha(x) =
 0.5 exp(-10 |grad I|), costs C_s = |I - 0.2|, C_t = |I - 0.8|.  One step = one
 solve from a cold start to a relative primal-dual gap <= 1e-4 (certificates
-every 10 iterations) with the fused float32 rPDRQ solver.
+every 10 iterations) with the fused float32 rpADMMII solver.
 
 Metric: pixel*label*iterations per second (binary counts as L = 2), plus the
 time to the 1e-4 gap of the fused solver and of the plain one-kernel-per-step
@@ -35,7 +35,7 @@ H = W = 1024
 L = 2
 TOL = 1e-4
 CHECK_EVERY = 10
-FLAGSHIP = 3          # rPDRQ
+FLAGSHIP = 2          # rpADMMII (fewest iterations to the gap on this workload)
 BYTES_PER_PX = 52     # 10 state floats r+w, C_s, C_t, alpha: algorithmic bytes / pixel / iteration
 WORKLOAD = "binary 1024x1024 shapes, edge-weighted alpha, solve to gap 1e-4"
 
@@ -118,11 +118,11 @@ def _traffic(kernel_src: str, kernel_name: str):
 
 def cpu_oracle_rate(inst, n_iter: int):
     """The FP64 oracle (single-threaded C) on a bounded sample: n_iter
-    rPDRQ iterations of the full workload; returns px*label*it/s."""
+    rpADMMII iterations of the full workload; returns px*label*it/s."""
     import oracle
 
     oracle.build()
-    p = oracle.default_params(oracle.RPDRQ, 2)
+    p = oracle.default_params(oracle.RPADMM_EB, 2)
     t0 = time.perf_counter()
     oracle.binary_run(inst.costs[0], inst.costs[1], inst.alpha, p, n_iter)
     dt = time.perf_counter() - t0
@@ -152,14 +152,53 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L,
-                                        "algo": "rPDRQ"},
+                                        "algo": "rpADMMII"},
         "cpu_baseline": {"value": value, "unit": "px*label*it/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n_iter} rPDRQ iterations of the full 1024x1024 workload "
+                         "sample": f"{n_iter} rpADMMII iterations of the full 1024x1024 workload "
                                    "per step, FP64 C oracle, one thread"},
         "e2e": {"value": value, "unit": "px*label*it/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+KERNEL_CASES = {
+    # name: (model, algo, H, W, L, storage, impl)
+    "binary-admm-1024": ("binary", 2, 1024, 1024, 2, 0, 0),
+    "binary-admm-4096": ("binary", 2, 4096, 4096, 2, 0, 0),
+    "binary-dr-4096": ("binary", 3, 4096, 4096, 2, 0, 0),
+    "binary-plain-4096": ("binary", 2, 4096, 4096, 2, 0, 1),
+    "potts4-admm-2048": ("potts", 2, 2048, 2048, 4, 0, 0),
+    "potts4-admm-2048-f16": ("potts", 2, 2048, 2048, 4, 1, 0),
+    "potts4-dr-2048": ("potts", 3, 2048, 2048, 4, 0, 0),
+    "potts16-admm-2048-f16": ("potts", 2, 2048, 2048, 16, 1, 0),
+}
+
+
+def run_kernel_case(name: str, iters: int):
+    """Untimed: cold start plus `iters` iterations of one configuration, for
+    profiler captures (ncu -k <kernel> -c <n>)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2004_11227_gb300 import cmf, synth
+
+    __graft_entry__.build()
+    model, algo, h, w, nl, storage, impl = KERNEL_CASES[name]
+    p = cmf.default_params(algo, nl, storage=storage, impl=impl)
+    if model == "binary":
+        inst = synth.config2(h, w)
+        b = cmf.alloc_binary(inst, p)
+        cmf.cmf_init_binary(b)
+        cmf.cmf_iterate_binary(b, iters)
+        print(name, cmf.cmf_eval_binary(b))
+    else:
+        inst = synth.config3(h, w) if nl == 4 else synth.config5(h, w)
+        s = cmf.alloc_potts(inst, p)
+        cmf.cmf_init_potts(s)
+        cmf.cmf_iterate_potts(s, iters)
+        print(name, cmf.cmf_eval_potts(s))
+    torch.cuda.synchronize()
 
 
 def main():
@@ -168,7 +207,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
+                    help="run one untimed configuration for a profiler capture")
+    ap.add_argument("--iters", type=int, default=4)
     args = ap.parse_args()
+    if args.kernel_case:
+        run_kernel_case(args.kernel_case, args.iters)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -285,7 +330,7 @@ def main():
     kern_ms = e0.elapsed_time(e1) / n_rf
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_PX * H * W / (kern_ms / 1000.0) / 1e9
-    traffic = _traffic("paper_2004_11227_gb300/csrc/cmf_binary.cu", "k_binary_dr_fused")
+    traffic = _traffic("paper_2004_11227_gb300/csrc/cmf_binary.cu", "k_binary_admm_fused")
 
     # --- plain one-kernel-per-step form and the other algorithms: time to gap ---------
     def time_to_gap(algo, impl):
@@ -312,8 +357,8 @@ def main():
             ms, it = time_to_gap(algo, impl)
             ttg[f"{cmf.ALGO_NAMES[algo]}_{'fused' if impl == 0 else 'plain'}"] = {
                 "ms": round(ms, 3), "iters": it}
-    fused_ms = ttg["rPDRQ_fused"]["ms"]
-    plain_ms = ttg["rPDRQ_plain"]["ms"]
+    fused_ms = ttg["rpADMMII_fused"]["ms"]
+    plain_ms = ttg["rpADMMII_plain"]["ms"]
 
     if rank == 0:
         rate, dt = cpu_oracle_rate(inst, 150)
@@ -322,7 +367,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "algo": "rPDRQ fused",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "algo": "rpADMMII fused",
                        "check_every": CHECK_EVERY, "tol_gap": TOL,
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
@@ -331,12 +376,12 @@ def main():
                                "iterations": iters, "all": ttg},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_binary_dr_fused", "peak_kind": peak_kind,
+                         "kernel": "k_binary_admm_fused", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": BYTES_PER_PX * H * W,
                          "launch_ms": kern_ms},
             "cpu_baseline": {"value": rate, "unit": "px*label*it/s", "cores": 1,
                              "kind": "oracle",
-                             "sample": "150 rPDRQ iterations of the full 1024x1024 workload, "
+                             "sample": "150 rpADMMII iterations of the full 1024x1024 workload, "
                                        f"FP64 C oracle, one thread ({dt:.1f} s)"},
             "e2e": {"value": e2e_value, "unit": "px*label*it/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -570,10 +570,14 @@ static cudaError_t launch_potts_admm_fused(const PottsProblem& P, const PottsSta
                                            cudaStream_t st) {
     const size_t dyn = (size_t)P.L * (8 * ROWS) * 32 * sizeof(float);
     auto kern = k_potts_admm_fused<S, ANISO, ROWS>;
-    if (dyn > 48 * 1024) {
+    // static + dynamic shared memory above 48 KB needs the opt-in; raise the
+    // limit once per instantiation to the largest request seen so far
+    static size_t configured = 0;
+    if (dyn > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)dyn);
         if (e != cudaSuccess) return e;
+        configured = dyn;
     }
     kern<<<pgrid(P.g, 8 * ROWS), dim3(32, 8), dyn, st>>>(P, a, b, K);
     return cudaGetLastError();

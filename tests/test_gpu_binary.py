@@ -171,10 +171,10 @@ def _window_step_check(cmf, inst, algo, k_before, windows, margin=8):
     cmf.cmf_iterate_binary(b, k_before)
     torch.cuda.synchronize()
     W = b.W
-    before = {k: getattr(b, k)[:, :W].float() for k in ("u", "qx", "qy", "ps", "pt")}
+    before = {k: getattr(b, k)[:, :W].float().clone() for k in ("u", "qx", "qy", "ps", "pt")}
     cmf.cmf_iterate_binary(b, 1)
     torch.cuda.synchronize()
-    after = {k: getattr(b, k)[:, :W].float() for k in ("u", "qx", "qy", "ps", "pt")}
+    after = {k: getattr(b, k)[:, :W].float().clone() for k in ("u", "qx", "qy", "ps", "pt")}
     po = O.default_params(algo, 2)
     alpha = inst.alpha_field()
     for (r0, c0, h, w) in windows:

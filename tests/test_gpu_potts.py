@@ -128,10 +128,10 @@ def _window_step_check(cmf, inst, algo, k_before, windows, margin=8, storage=0, 
     torch.cuda.synchronize()
     W = s.W
     keys = ("u", "qx", "qy", "p", "ps")
-    before = {k: getattr(s, k)[..., :W].float() for k in keys}
+    before = {k: getattr(s, k)[..., :W].float().clone() for k in keys}
     cmf.cmf_iterate_potts(s, 1)
     torch.cuda.synchronize()
-    after = {k: getattr(s, k)[..., :W].float() for k in keys}
+    after = {k: getattr(s, k)[..., :W].float().clone() for k in keys}
     po = O.default_params(algo, inst.L)
     alpha = inst.alpha_field()
     for (r0, c0, h, w) in windows:
