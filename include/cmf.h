@@ -89,8 +89,15 @@ typedef struct {
     int max_iter;      /* cmf_solve_*: iteration cap                           */
     int check_every;   /* cmf_solve_*: iterations between certificate checks   */
     int warm_start;    /* cmf_solve_*: 0 = cold start, 1 = start from buffers  */
-    int use_graph;     /* cmf_solve_*: replay a CUDA graph per check interval  */
-    int reserved;
+    int use_graph;     /* cmf_solve_*: 1 = device-driven loop (a CUDA graph whose
+                          conditional WHILE node repeats {check_every iterations,
+                          certificates, stop test} with no host round trip; used
+                          when max_iter % check_every == 0 and, for CMF_FUSED,
+                          check_every is even), else a host-driven loop        */
+    int variant;       /* kernel variant: 0 = automatic (TMA-staged tiles where the
+                          layout allows: rows and planes 16-byte aligned), 1 = the
+                          shared-memory tile kernels, 16 / 32 = TMA tiles of that
+                          many rows (Potts ADMM)                               */
     double c;          /* ADMM step size                                       */
     double a;          /* q preconditioner N = a c I (a >= 8, Thm 1)           */
     double a1;         /* p preconditioner a~ (binary) / a_1 (Potts), >= 2     */

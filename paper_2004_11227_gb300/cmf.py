@@ -36,7 +36,7 @@ class Params(ctypes.Structure):
         ("algo", ctypes.c_int), ("storage", ctypes.c_int), ("impl", ctypes.c_int),
         ("aniso", ctypes.c_int), ("sweeps", ctypes.c_int), ("max_iter", ctypes.c_int),
         ("check_every", ctypes.c_int), ("warm_start", ctypes.c_int),
-        ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("variant", ctypes.c_int),
         ("c", ctypes.c_double), ("a", ctypes.c_double), ("a1", ctypes.c_double),
         ("a2", ctypes.c_double), ("rho", ctypes.c_double), ("r", ctypes.c_double),
         ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("tol_gap", ctypes.c_double),

@@ -21,7 +21,20 @@ struct WsLayout {
     size_t tmp;       // float planes used by the plain form
     size_t partials;  // 3 doubles per certificate block
     size_t scalars;   // 4 doubles
+    size_t ctl;       // solve-loop control block (graph path)
+    size_t hist;      // device history rows (graph path)
     size_t total;
+};
+
+size_t hist_rows_for(const cmf_params& p);
+
+// Control block in the workspace: the device-driven solve loop's counters and
+// the sticky error word that kernels with bounded waits set on a timeout.
+struct SolveCtl {
+    int it;      // iterations done
+    int checks;  // certificate evaluations done
+    int stop;    // 0 running, 1 converged, 2 iteration cap, 3 device wait timed out
+    int err;     // nonzero: a bounded device-side wait ran out
 };
 
 WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool potts) {
@@ -40,6 +53,10 @@ WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool pot
     off += align_up(sizeof(double) * 3 * (size_t)eval_blocks(H, W));
     w.scalars = off;
     off += align_up(sizeof(double) * 4);
+    w.ctl = off;
+    off += align_up(64);
+    w.hist = off;
+    off += align_up(sizeof(double) * 5 * hist_rows_for(p));
     w.total = off;
     return w;
 }
@@ -57,6 +74,8 @@ cmf_status check_params(const cmf_params* p, int L) {
     if (!(p->rho > 0) || !(p->rho < 2)) return CMF_EINVAL;
     if (!(p->r > 0) || !(p->sigma > 0) || !(p->tau > 0)) return CMF_EINVAL;
     if (p->max_iter < 0 || p->check_every < 1 || !(p->tol_gap >= 0)) return CMF_EINVAL;
+    if (p->variant != 0 && p->variant != 1 && p->variant != 16 && p->variant != 32)
+        return CMF_EINVAL;
     (void)L;
     return CMF_OK;
 }
@@ -179,7 +198,14 @@ cmf_status finish_eval(char* wsbase, const WsLayout& w, int nblocks, double* h_o
     CMF_CUDA_TRY(reduce_partials(partials, nblocks, scal, st));
     double h[3];
     CMF_CUDA_TRY(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+    int* err = &((SolveCtl*)(wsbase + w.ctl))->err;
+    int herr = 0;
+    CMF_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CMF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        CMF_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        return CMF_ETIMEOUT;
+    }
     const double E = h[0], D = h[1];
     h_out[0] = E;
     h_out[1] = D;
@@ -239,6 +265,9 @@ struct PottsCall {
     char* wsbase;
     StepConfig cfg;
     int storage;
+    bool tma;                    // fused ADMM through TMA-staged tiles
+    PottsTmaMaps maps[2];        // tensor maps of the user / workspace state sets
+    int* err;                    // sticky device error word
 };
 
 cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0, int H, int W,
@@ -263,6 +292,19 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.ws = ws_potts_state(call.wsbase, call.w, call.P.g, L, p->storage);
     call.cfg = make_step(*p, L, true);
     call.storage = p->storage;
+    call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
+    call.tma = false;
+    const bool want_tma = !call.cfg.dr && !call.cfg.plain && p->variant != 1;
+    if (want_tma && potts_tma_eligible(call.P.g, p->storage, call.user) &&
+        potts_tma_eligible(call.P.g, p->storage, call.ws)) {
+        const int ty = p->variant == 32 ? 32 : 16;
+        call.tma = potts_tma_maps(call.P.g, L, p->storage, call.user, ty, call.maps[0]) ==
+                       cudaSuccess &&
+                   potts_tma_maps(call.P.g, L, p->storage, call.ws, ty, call.maps[1]) ==
+                       cudaSuccess;
+    }
+    if (!call.tma && !call.cfg.dr && !call.cfg.plain && (p->variant == 16 || p->variant == 32))
+        return CMF_EINVAL;  // TMA tiles requested but the layout does not allow them
     return CMF_OK;
 }
 
@@ -273,6 +315,12 @@ cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st) {
             cudaError_t e = potts_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur = 0;
+        } else if (c.tma) {
+            const PottsStateV& b = cur == 0 ? c.ws : c.user;
+            cudaError_t e = potts_admm_tma_step(c.storage, c.P, b, c.cfg.aniso, c.cfg.ac,
+                                                c.maps[cur], c.err, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
         } else {
             const PottsStateV& a = cur == 0 ? c.user : c.ws;
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
@@ -289,6 +337,124 @@ cmf_status potts_eval_state(const PottsCall& c, const PottsStateV& s, double* h_
     CMF_CUDA_TRY(potts_eval(c.storage, c.P, s, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
                             (double*)(c.wsbase + c.w.partials), st));
     return finish_eval(c.wsbase, c.w, eval_blocks(c.P.g.H, c.P.g.W), h_out, st);
+}
+
+// ---- device-driven solve loop (CUDA graph with a conditional WHILE node) ----
+
+__global__ void k_solve_reset(SolveCtl* ctl) {
+    ctl->it = 0;
+    ctl->checks = 0;
+    ctl->stop = 0;
+}
+
+// One thread: turn the reduced (E, D, res^2) into a history row and decide
+// whether the loop body runs again.
+__global__ void k_solve_decide(const double* scal, SolveCtl* ctl, double* hist, int hist_rows,
+                               int K, int max_iter, double tol, cudaGraphConditionalHandle h) {
+    const double E = scal[0], D = scal[1], R = scal[2];
+    const double gap = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
+    const int it = ctl->it + K;
+    const int n = ctl->checks;
+    ctl->it = it;
+    if (n < hist_rows) {
+        double* row = hist + 5 * (size_t)n;
+        row[0] = it;
+        row[1] = E;
+        row[2] = D;
+        row[3] = gap;
+        row[4] = sqrt(R > 0.0 ? R : 0.0);
+    }
+    ctl->checks = n + 1;
+    const bool converged = gap <= tol;
+    const bool failed = ctl->err != 0;
+    const bool go = !converged && !failed && it + K <= max_iter;
+    ctl->stop = go ? 0 : (failed ? 3 : (converged ? 1 : 2));
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+size_t hist_rows_for(const cmf_params& p) {
+    const size_t r = (size_t)(p.max_iter / (p.check_every > 0 ? p.check_every : 1)) + 1;
+    return r < 65536 ? r : 65536;  // later checks are decided but not recorded
+}
+
+// Whether the graph path can reproduce the host loop exactly: whole chunks
+// only, and an even chunk for the fused ping-pong so every chunk ends in the
+// caller's buffers.
+bool graph_eligible(const cmf_params& p) {
+    if (!p.use_graph || p.max_iter < p.check_every) return false;
+    if (p.max_iter % p.check_every != 0) return false;
+    if (p.impl == CMF_FUSED && (p.check_every & 1)) return false;
+    return true;
+}
+
+// `chunk(stream)` launches check_every iterations that start and end in the
+// caller's buffers; `certify(stream)` launches the certificate kernel into
+// the partials.
+template <typename Chunk, typename Certify>
+cmf_status solve_graph(const cmf_params* p, char* wsbase, const WsLayout& w, int nblocks,
+                       Chunk chunk, Certify certify, double* h_hist, int hist_cap, int* h_iters,
+                       cudaStream_t st) {
+    SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
+    double* dhist = (double*)(wsbase + w.hist);
+    const int rows = (int)hist_rows_for(*p);
+    double* partials = (double*)(wsbase + w.partials);
+    double* scal = (double*)(wsbase + w.scalars);
+    k_solve_reset<<<1, 1, 0, st>>>(ctl);
+    CMF_CUDA_TRY(cudaGetLastError());
+
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cmf_status status = CMF_ECUDA;
+    do {
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) break;
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) !=
+            cudaSuccess)
+            break;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) break;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            break;
+        cudaError_t e1 = chunk(cs);
+        cudaError_t e2 = e1 == cudaSuccess ? certify(cs) : e1;
+        cudaError_t e3 = e2 == cudaSuccess ? reduce_partials(partials, nblocks, scal, cs) : e2;
+        if (e3 == cudaSuccess) {
+            k_solve_decide<<<1, 1, 0, cs>>>(scal, ctl, dhist, rows, p->check_every,
+                                            p->max_iter, p->tol_gap, h);
+            e3 = cudaGetLastError();
+        }
+        cudaGraph_t captured = nullptr;
+        cudaError_t e4 = cudaStreamEndCapture(cs, &captured);
+        if (e3 != cudaSuccess || e4 != cudaSuccess) break;
+        if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) break;
+        if (cudaGraphLaunch(ge, st) != cudaSuccess) break;
+        SolveCtl hc;
+        if (cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) break;
+        const int n = hc.checks < rows ? hc.checks : rows;
+        const int ncopy = n < hist_cap ? n : hist_cap;
+        if (h_hist && ncopy > 0) {
+            if (cudaMemcpy(h_hist, dhist, sizeof(double) * 5 * (size_t)ncopy,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+                break;
+        }
+        if (h_iters) *h_iters = hc.it;
+        status = hc.stop == 1 ? CMF_OK : (hc.stop == 3 ? CMF_ETIMEOUT : CMF_NOT_CONVERGED);
+    } while (0);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    return status;
 }
 
 // Shared solve loop: `run(n, cur)` advances, `eval(cur, out)` certifies.
@@ -342,7 +508,7 @@ cmf_status cmf_default_params(int algo, int L, cmf_params* p) {
     p->max_iter = 10000;
     p->check_every = 10;
     p->warm_start = 0;
-    p->use_graph = 0;
+    p->use_graph = 1;
     p->c = 0.3;
     p->a = 8.0;
     p->a1 = 2.0;
@@ -430,8 +596,22 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
     if (s != CMF_OK) return s;
     if (hist_cap < 0) return CMF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    CMF_CUDA_TRY(cudaMemsetAsync(&((SolveCtl*)(c.wsbase + c.w.ctl))->err, 0, sizeof(int), st));
     if (!p->warm_start)
         CMF_CUDA_TRY(binary_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    if (graph_eligible(*p)) {
+        return solve_graph(
+            p, c.wsbase, c.w, eval_blocks(H, W),
+            [&](cudaStream_t s) {
+                int cur = 0;
+                return binary_run(c, p->check_every, cur, s);
+            },
+            [&](cudaStream_t s) {
+                return binary_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                                   (double*)(c.wsbase + c.w.partials), s);
+            },
+            h_hist, hist_cap, h_iters, st);
+    }
     return solve_loop(
         p, [&](int n, int& cur) { return binary_run(c, n, cur, st); },
         [&](int cur, double* out) {
@@ -466,6 +646,7 @@ cmf_status cmf_iterate_potts(const float* d_C, int L, const float* d_alpha, floa
     if (s != CMF_OK) return s;
     if (n_iter < 0) return CMF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    CMF_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), st));
     int cur = 0;
     CMF_CUDA_TRY(potts_run(c, n_iter, cur, st));
     if (cur != 0) CMF_CUDA_TRY(copy_potts(c.user, c.ws, c.P.g, L, c.storage, st));
@@ -495,8 +676,22 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
     if (s != CMF_OK) return s;
     if (hist_cap < 0) return CMF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    CMF_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), st));
     if (!p->warm_start)
         CMF_CUDA_TRY(potts_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    if (graph_eligible(*p)) {
+        return solve_graph(
+            p, c.wsbase, c.w, eval_blocks(H, W),
+            [&](cudaStream_t s) {
+                int cur = 0;
+                return potts_run(c, p->check_every, cur, s);
+            },
+            [&](cudaStream_t s) {
+                return potts_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                                  (double*)(c.wsbase + c.w.partials), s);
+            },
+            h_hist, hist_cap, h_iters, st);
+    }
     return solve_loop(
         p, [&](int n, int& cur) { return potts_run(c, n, cur, st); },
         [&](int cur, double* out) {

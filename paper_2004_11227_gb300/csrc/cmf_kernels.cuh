@@ -2,6 +2,8 @@
 // translation units.  Not installed; not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
+
 #include "cmf_common.cuh"
 
 namespace cmf {
@@ -136,6 +138,20 @@ cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s,
 // (plain form): red, then (black, red) x D.sweeps.
 cudaError_t halfsweeps(const Grid& G, float* u, const float* b, const DrCoef& D,
                        cudaStream_t st);
+
+// --- TMA-staged Potts ADMM (cmf_potts_tma.cu) ---
+struct PottsTmaMaps {
+    CUtensorMap qx, qy, p, u, ps;
+    int ty;  // output rows per tile (16 or 32)
+};
+bool potts_tma_eligible(const Grid& G, int storage, const PottsStateV& s);
+cudaError_t potts_tma_maps(const Grid& G, int L, int storage, const PottsStateV& s, int ty,
+                           PottsTmaMaps& m);
+// One iteration reading the state described by src_maps, writing b; a
+// bounded TMA wait that runs out sets *err.
+cudaError_t potts_admm_tma_step(int storage, const PottsProblem& P, const PottsStateV& b,
+                                bool aniso, const AdmmCoef& K, const PottsTmaMaps& src_maps,
+                                int* err, cudaStream_t st);
 
 // --- reductions ---
 // Sum n partial triples in a fixed order into out[0..2] (one block).

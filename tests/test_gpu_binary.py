@@ -180,6 +180,11 @@ def _window_step_check(cmf, inst, algo, k_before, windows, margin=8):
     for (r0, c0, h, w) in windows:
         R0, C0 = max(r0 - margin, 0), max(c0 - margin, 0)
         R1, C1 = min(r0 + h + margin, b.H), min(c0 + w + margin, b.W)
+        if (R0 + C0) % 2:  # keep the crop's red/black colouring that of the grid
+            if R0 > 0:
+                R0 -= 1
+            else:
+                C0 -= 1
         st = {k: v[R0:R1, C0:C1].cpu().double().numpy() for k, v in before.items()}
         res = O.binary_run(inst.costs[0][R0:R1, C0:C1], inst.costs[1][R0:R1, C0:C1],
                            alpha[R0:R1, C0:C1], po, 1, st)
@@ -201,3 +206,30 @@ def test_full_size_1024_windows(cmf, algo):
     wins = [(0, 0, 48, 48), (0, 1024 - 40, 40, 40), (1024 - 33, 0, 33, 64),
             (1024 - 50, 1024 - 50, 50, 50), (500, 500, 64, 64), (257, 771, 31, 45)]
     _window_step_check(cmf, inst, algo, 37, wins)
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("algo", [0, 3])
+def test_graph_solve_equals_host_loop(cmf, algo, impl):
+    """The device-driven solve loop (graph with a conditional node) runs the
+    same kernels in the same order as the host loop: identical state, history
+    and iteration count; a max_iter cap yields NOT_CONVERGED on both paths."""
+    inst = synth.config2(80, 112)
+    out = []
+    for use_graph in (1, 0):
+        p = cmf.default_params(algo, 2, impl=impl, use_graph=use_graph, tol_gap=1e-4,
+                               max_iter=4000, check_every=10)
+        b = cmf.alloc_binary(inst, p)
+        out.append((cmf.cmf_solve_binary(b), b.state()))
+    (s1, i1, h1), st1 = out[0]
+    (s0, i0, h0), st0 = out[1]
+    assert s1 == s0 == cmf.OK and i1 == i0
+    np.testing.assert_array_equal(h1, h0)
+    for k in st0:
+        np.testing.assert_array_equal(st1[k], st0[k])
+    for use_graph in (1, 0):
+        p = cmf.default_params(algo, 2, impl=impl, use_graph=use_graph, tol_gap=1e-12,
+                               max_iter=40, check_every=10)
+        b = cmf.alloc_binary(inst, p)
+        st, it, hist = cmf.cmf_solve_binary(b)
+        assert st == cmf.NOT_CONVERGED and it == 40 and len(hist) == 4
