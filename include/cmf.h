@@ -154,6 +154,33 @@ cmf_status cmf_eval_binary(const float *d_Cs, const float *d_Ct, const float *d_
                            const void *d_ps, const void *d_pt, double *h_out, void *d_ws,
                            size_t ws_bytes, void *stream);
 
+/* Certificates of a binary state exactly as cmf_eval_binary computes them,
+ * for callers that cannot allocate device memory when they need them (code
+ * running while a stream is captured in global mode, where cudaMalloc is
+ * prohibited; plug-ins that only receive a stream and the solver's buffers;
+ * loops with a memory budget fixed up front).  It takes no workspace and
+ * allocates nothing: its scratch is a static device array inside libcmf of
+ * 393,248 bytes (per-block partial sums for up to 16384 blocks of 32 x 32
+ * pixels, i.e. grids up to 4096 x 4096 pixels, plus the reduced scalars),
+ * present on every GPU that loads the library until the process exits.
+ *  - Larger grids (more than 16384 blocks of 32 x 32) return CMF_EINVAL.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress for the current device; make that first call
+ *    before any stream capture.
+ *  - All calls share the array: calls whose GPU work overlaps (different
+ *    streams, or different host threads on one device) race and give wrong
+ *    results.  Nothing in the array has to start at zero; each call
+ *    overwrites what it reads.
+ *  - Like cmf_eval_binary it synchronises `stream` and writes h_out[0..3]
+ *    = (E, D, gap, res) on the host.
+ * The paper has no counterpart: this is a deployment variant of
+ * cmf_eval_binary. */
+cmf_status cmf_eval_binary_noalloc(const float *d_Cs, const float *d_Ct, const float *d_alpha,
+                                   float alpha0, int H, int W, int pitch, const cmf_params *p,
+                                   const float *d_u, const void *d_qx, const void *d_qy,
+                                   const void *d_ps, const void *d_pt, double *h_out,
+                                   void *stream);
+
 /* Solve to gap <= p->tol_gap or p->max_iter iterations: cold start unless
  * p->warm_start, then repeat {check_every iterations; certificates}.
  * h_hist (host, may be NULL) receives up to hist_cap rows of

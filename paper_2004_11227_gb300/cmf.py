@@ -54,6 +54,8 @@ _SIGS = {
                           [ctypes.c_size_t, ctypes.c_void_p],
     "cmf_eval_binary": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
                        [ctypes.c_void_p] * 8 + [ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_eval_binary_noalloc": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
+                               [ctypes.c_void_p] * 8,
     "cmf_solve_binary": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
                         [ctypes.c_void_p] * 7 + [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_size_t, ctypes.c_void_p],
@@ -260,6 +262,15 @@ def cmf_eval_binary(b: Binary, stream=None):
     out = (ctypes.c_double * 4)()
     _check(lib().cmf_eval_binary(*b._common(), *b._state_ptrs(), out, _ptr(b.ws), b.ws.numel(),
                                  _stream(stream)), "cmf_eval_binary")
+    return tuple(out)
+
+
+def cmf_eval_binary_noalloc(b: Binary, stream=None):
+    """Certificates of the binary state without a workspace (the library's
+    static scratch; grids up to 4096 x 4096)."""
+    out = (ctypes.c_double * 4)()
+    _check(lib().cmf_eval_binary_noalloc(*b._common(), *b._state_ptrs(), out,
+                                         _stream(stream)), "cmf_eval_binary_noalloc")
     return tuple(out)
 
 
