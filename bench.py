@@ -172,12 +172,22 @@ KERNEL_CASES = {
     "potts4-admm-2048-f16": ("potts", 2, 2048, 2048, 4, 1, 0),
     "potts4-dr-2048": ("potts", 3, 2048, 2048, 4, 0, 0),
     "potts16-admm-2048-f16": ("potts", 2, 2048, 2048, 16, 1, 0),
+    "potts16-admm-4096-f16": ("potts", 2, 4096, 4096, 16, 1, 0),
+    "potts4-plain-2048": ("potts", 2, 2048, 2048, 4, 0, 1),
 }
 
 
-def run_kernel_case(name: str, iters: int):
-    """Untimed: cold start plus `iters` iterations of one configuration, for
-    profiler captures (ncu -k <kernel> -c <n>)."""
+def algorithmic_bytes_per_px(model: str, L: int, storage: int, alpha_field: bool) -> int:
+    """State read + written once, costs and alpha read once (halos excluded)."""
+    s = 4 if storage == 0 else 2
+    if model == "binary":
+        return 4 * 2 + 4 * s * 2 + 8 + (4 if alpha_field else 0)
+    return L * (4 * 2 + 3 * s * 2 + 4) + 2 * s + (4 if alpha_field else 0)
+
+
+def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int = 0):
+    """Cold start plus `iters` iterations of one configuration: untimed for
+    profiler captures (ncu -k <kernel> -c <n>), or timed with CUDA events."""
     import torch
 
     import __graft_entry__
@@ -185,19 +195,33 @@ def run_kernel_case(name: str, iters: int):
 
     __graft_entry__.build()
     model, algo, h, w, nl, storage, impl = KERNEL_CASES[name]
-    p = cmf.default_params(algo, nl, storage=storage, impl=impl)
+    p = cmf.default_params(algo, nl, storage=storage, impl=impl, variant=variant)
     if model == "binary":
         inst = synth.config2(h, w)
-        b = cmf.alloc_binary(inst, p)
-        cmf.cmf_init_binary(b)
-        cmf.cmf_iterate_binary(b, iters)
-        print(name, cmf.cmf_eval_binary(b))
+        st = cmf.alloc_binary(inst, p)
+        init, step, ev = cmf.cmf_init_binary, cmf.cmf_iterate_binary, cmf.cmf_eval_binary
     else:
         inst = synth.config3(h, w) if nl == 4 else synth.config5(h, w)
-        s = cmf.alloc_potts(inst, p)
-        cmf.cmf_init_potts(s)
-        cmf.cmf_iterate_potts(s, iters)
-        print(name, cmf.cmf_eval_potts(s))
+        st = cmf.alloc_potts(inst, p)
+        init, step, ev = cmf.cmf_init_potts, cmf.cmf_iterate_potts, cmf.cmf_eval_potts
+    init(st)
+    step(st, iters)
+    if time_it:
+        n = max(iters, 20)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        step(st, n)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        nb = algorithmic_bytes_per_px(model, nl, storage,
+                                      isinstance(inst.alpha, np.ndarray)) * h * w
+        print(json.dumps({"case": name, "variant": variant, "ms_per_iter": ms,
+                          "algorithmic_GBps": nb / ms / 1e6,
+                          "px_label_it_per_s": h * w * nl / ms * 1e3}))
+    print(name, ev(st))
     torch.cuda.synchronize()
 
 
@@ -210,9 +234,11 @@ def main():
     ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
                     help="run one untimed configuration for a profiler capture")
     ap.add_argument("--iters", type=int, default=4)
+    ap.add_argument("--time", action="store_true", help="time the kernel case")
+    ap.add_argument("--variant", type=int, default=0, help="cmf_params.variant")
     args = ap.parse_args()
     if args.kernel_case:
-        run_kernel_case(args.kernel_case, args.iters)
+        run_kernel_case(args.kernel_case, args.iters, args.time, args.variant)
         return
     if args.impl == "reference":
         run_reference(args)

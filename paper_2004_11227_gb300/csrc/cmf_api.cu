@@ -295,9 +295,10 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
     const bool want_tma = !call.cfg.dr && !call.cfg.plain && p->variant != 1;
-    if (want_tma && potts_tma_eligible(call.P.g, p->storage, call.user) &&
+    const int ty = p->variant == 32 ? 32 : 16;
+    if (want_tma && potts_tma_fits(p->storage, L, ty) &&
+        potts_tma_eligible(call.P.g, p->storage, call.user) &&
         potts_tma_eligible(call.P.g, p->storage, call.ws)) {
-        const int ty = p->variant == 32 ? 32 : 16;
         call.tma = potts_tma_maps(call.P.g, L, p->storage, call.user, ty, call.maps[0]) ==
                        cudaSuccess &&
                    potts_tma_maps(call.P.g, L, p->storage, call.ws, ty, call.maps[1]) ==

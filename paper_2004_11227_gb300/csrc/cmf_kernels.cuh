@@ -145,6 +145,7 @@ struct PottsTmaMaps {
     int ty;  // output rows per tile (16 or 32)
 };
 bool potts_tma_eligible(const Grid& G, int storage, const PottsStateV& s);
+bool potts_tma_fits(int storage, int L, int ty);  // shared memory within the block limit
 cudaError_t potts_tma_maps(const Grid& G, int L, int storage, const PottsStateV& s, int ty,
                            PottsTmaMaps& m);
 // One iteration reading the state described by src_maps, writing b; a

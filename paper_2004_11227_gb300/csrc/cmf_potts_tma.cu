@@ -31,7 +31,8 @@ struct PottsTmaLayout {
     static constexpr int STAGE = 3 * FS + FU;
     static constexpr uint32_t TX_BYTES = 3u * BY * BXS * sizeof(S) + (uint32_t)BY * BXU * 4u;
     static constexpr uint32_t PS_BYTES = (uint32_t)BY * BXS * sizeof(S);
-    static size_t dyn_bytes(int L) { return 2 * STAGE + FS + (size_t)L * TY * 32 * 4; }
+    // + 128: the kernel rounds the dynamic shared-memory base up to 128 bytes
+    static size_t dyn_bytes(int L) { return 2 * STAGE + FS + (size_t)L * TY * 32 * 4 + 128; }
 };
 
 template <typename S>
@@ -57,7 +58,9 @@ __global__ void __launch_bounds__(256)
     __shared__ float g_s[TY + 2][TX + 2];
     __shared__ float qnx[TY + 1][TX + 1];
     __shared__ float qny[TY + 1][TX + 1];
-    extern __shared__ __align__(128) unsigned char dsm[];
+    extern __shared__ __align__(128) unsigned char dsm_raw[];
+    unsigned char* dsm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~static_cast<uintptr_t>(127));
     unsigned char* stage[2] = {dsm, dsm + Lay::STAGE};
     S* ps_s = reinterpret_cast<S*>(dsm + 2 * Lay::STAGE);
     float* v_s = reinterpret_cast<float*>(dsm + 2 * Lay::STAGE + Lay::FS);
@@ -120,9 +123,12 @@ __global__ void __launch_bounds__(256)
             const int gy = i / (TX + 2), gx = i - gy * (TX + 2);
             const int r = y0 - 1 + gy, c = x0 - 1 + gx;
             const int sy = gy + 1, sx = gx - 1 + XO, su_x = gx - 1 + XU;
-            float dv = -sload(sqx + sy * BXS + sx - 1) - sload(sqy + (sy - 1) * BXS + sx);
+            // neighbours outside the grid were zero-filled by the TMA unit
+            float dv = 0.f;
             if (c < G.W - 1) dv += sload(sqx + sy * BXS + sx);
+            dv -= sload(sqx + sy * BXS + sx - 1);
             if (r < G.H - 1) dv += sload(sqy + sy * BXS + sx);
+            dv -= sload(sqy + (sy - 1) * BXS + sx);
             g_s[gy][gx] = dv + sload(sp + sy * BXS + sx) - sload(ps_s + sy * BXS + sx) -
                           su[sy * BXU + su_x] * K.inv_c;
         }
@@ -162,10 +168,11 @@ __global__ void __launch_bounds__(256)
             float v = 0.f;
             if (r < G.H && c < G.W) {
                 const size_t k = G.idx(r, c);
-                float d = qnx[ly + 1][lx + 1] - qnx[ly + 1][lx] + qny[ly + 1][lx + 1] -
-                          qny[ly][lx + 1];
-                if (c == G.W - 1) d -= qnx[ly + 1][lx + 1];
-                if (r == G.H - 1) d -= qny[ly + 1][lx + 1];
+                float d = 0.f;  // out-of-grid neighbours of the q tile hold 0
+                if (c < G.W - 1) d += qnx[ly + 1][lx + 1];
+                d -= qnx[ly + 1][lx];
+                if (r < G.H - 1) d += qny[ly + 1][lx + 1];
+                d -= qny[ly][lx + 1];
                 const int sy = ly + 2;
                 const float ps0 = sload(ps_s + sy * BXS + lx + XO);
                 const float p0 = sload(sp + sy * BXS + lx + XO);
@@ -210,6 +217,23 @@ __global__ void __launch_bounds__(256)
                     v_s[(l * TY + ly) * TX + lx] + K.cu * ps1[j];
         }
     }
+}
+
+// Shared memory one block of the TMA kernel needs (static + dynamic).
+static size_t tma_smem_bytes(int storage, int L, int ty) {
+    const size_t stat = (size_t)(ty + 2) * 34 * 4 + 2 * (size_t)(ty + 1) * 33 * 4 + 64;
+    size_t dyn;
+    if (storage == CMF_F32)
+        dyn = ty == 32 ? PottsTmaLayout<float, 32>::dyn_bytes(L)
+                       : PottsTmaLayout<float, 16>::dyn_bytes(L);
+    else
+        dyn = ty == 32 ? PottsTmaLayout<__half, 32>::dyn_bytes(L)
+                       : PottsTmaLayout<__half, 16>::dyn_bytes(L);
+    return stat + dyn;
+}
+
+bool potts_tma_fits(int storage, int L, int ty) {
+    return tma_smem_bytes(storage, L, ty) <= 220 * 1024;
 }
 
 // Whether a Potts state set can be staged by TMA: 16-byte aligned plane
