@@ -39,6 +39,12 @@
  *    (cmf_eval_*, cmf_solve_*) synchronise the stream themselves.
  *  - Errors are returned, never aborted on.  On CMF_EINVAL nothing was
  *    launched.  On CMF_ECUDA the state buffers are undefined.
+ *  - Kernels that stage data with TMA wait on shared-memory barriers with a
+ *    bound of about one second; a wait that runs out makes the kernel record
+ *    the event in the workspace and return (the state is then undefined).
+ *    cmf_solve_* report it as CMF_ETIMEOUT; after cmf_iterate_* (which does
+ *    not synchronise) the next cmf_eval_* on the same workspace reports it.
+ *    cmf_iterate_* and cmf_solve_* clear the record when they start.
  *  - State storage: u is always float32.  Flows (q, p_s, p_t / p_i) are
  *    stored as cmf_params.storage (float32, float16 or bfloat16); all
  *    arithmetic is float32 and the certificates (energies, gap, residual) are
@@ -96,7 +102,7 @@ typedef struct {
                           check_every is even), else a host-driven loop        */
     int variant;       /* kernel variant: 0 = automatic (TMA-staged tiles where the
                           layout allows: rows and planes 16-byte aligned), 1 = the
-                          shared-memory tile kernels, 16 / 32 = TMA tiles of that
+                          shared-memory tile kernels, 8 / 16 / 32 = TMA tiles of that
                           many rows (Potts ADMM)                               */
     double c;          /* ADMM step size                                       */
     double a;          /* q preconditioner N = a c I (a >= 8, Thm 1)           */

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "cmf_kernels.cuh"
+#include "cmf_tma.cuh"
 
 using namespace cmf;
 
@@ -34,7 +35,7 @@ struct SolveCtl {
     int it;      // iterations done
     int checks;  // certificate evaluations done
     int stop;    // 0 running, 1 converged, 2 iteration cap, 3 device wait timed out
-    int err;     // nonzero: a bounded device-side wait ran out
+    int err;     // kErrWaitTimeout: a bounded device-side wait ran out
 };
 
 WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool potts) {
@@ -74,7 +75,8 @@ cmf_status check_params(const cmf_params* p, int L) {
     if (!(p->rho > 0) || !(p->rho < 2)) return CMF_EINVAL;
     if (!(p->r > 0) || !(p->sigma > 0) || !(p->tau > 0)) return CMF_EINVAL;
     if (p->max_iter < 0 || p->check_every < 1 || !(p->tol_gap >= 0)) return CMF_EINVAL;
-    if (p->variant != 0 && p->variant != 1 && p->variant != 16 && p->variant != 32)
+    if (p->variant != 0 && p->variant != 1 && p->variant != 8 && p->variant != 16 &&
+        p->variant != 32)
         return CMF_EINVAL;
     (void)L;
     return CMF_OK;
@@ -143,6 +145,9 @@ struct BinaryCall {
     char* wsbase;
     StepConfig cfg;
     int storage;
+    bool tma;               // fused ADMM through the persistent TMA kernel
+    BinTmaMaps maps[2];     // tensor maps of the user / workspace state sets
+    int* err;               // sticky device error word
 };
 
 cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, float alpha0,
@@ -168,6 +173,19 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     call.ws = ws_binary_state(call.wsbase, call.w, call.P.g, p->storage);
     call.cfg = make_step(*p, 2, false);
     call.storage = p->storage;
+    call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
+    call.tma = false;
+    const int ty = p->variant >= 8 ? p->variant : 16;
+    if (!call.cfg.dr && !call.cfg.plain && p->variant != 1 &&
+        binary_tma_eligible(call.P.g, p->storage, call.user) &&
+        binary_tma_eligible(call.P.g, p->storage, call.ws)) {
+        call.tma = binary_tma_maps(call.P.g, p->storage, call.user, ty, call.maps[0]) ==
+                       cudaSuccess &&
+                   binary_tma_maps(call.P.g, p->storage, call.ws, ty, call.maps[1]) ==
+                       cudaSuccess;
+    }
+    if (!call.tma && !call.cfg.dr && !call.cfg.plain && p->variant >= 8)
+        return CMF_EINVAL;  // TMA tiles requested but the layout does not allow them
     return CMF_OK;
 }
 
@@ -180,6 +198,12 @@ cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st) {
             cudaError_t e = binary_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur = 0;
+        } else if (c.tma) {
+            const BinStateV& b = cur == 0 ? c.ws : c.user;
+            cudaError_t e = binary_admm_tma_step(c.storage, c.P, b, c.cfg.aniso, c.cfg.ac,
+                                                 c.maps[cur], c.err, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
         } else {
             const BinStateV& a = cur == 0 ? c.user : c.ws;
             const BinStateV& b = cur == 0 ? c.ws : c.user;
@@ -202,7 +226,7 @@ cmf_status finish_eval(char* wsbase, const WsLayout& w, int nblocks, double* h_o
     int herr = 0;
     CMF_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CMF_CUDA_TRY(cudaStreamSynchronize(st));
-    if (herr) {
+    if (herr == kErrWaitTimeout) {
         CMF_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
         return CMF_ETIMEOUT;
     }
@@ -295,7 +319,7 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
     const bool want_tma = !call.cfg.dr && !call.cfg.plain && p->variant != 1;
-    const int ty = p->variant == 32 ? 32 : 16;
+    const int ty = p->variant >= 8 ? p->variant : 16;
     if (want_tma && potts_tma_fits(p->storage, L, ty) &&
         potts_tma_eligible(call.P.g, p->storage, call.user) &&
         potts_tma_eligible(call.P.g, p->storage, call.ws)) {
@@ -304,7 +328,7 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
                    potts_tma_maps(call.P.g, L, p->storage, call.ws, ty, call.maps[1]) ==
                        cudaSuccess;
     }
-    if (!call.tma && !call.cfg.dr && !call.cfg.plain && (p->variant == 16 || p->variant == 32))
+    if (!call.tma && !call.cfg.dr && !call.cfg.plain && p->variant >= 8)
         return CMF_EINVAL;  // TMA tiles requested but the layout does not allow them
     return CMF_OK;
 }
@@ -367,7 +391,7 @@ __global__ void k_solve_decide(const double* scal, SolveCtl* ctl, double* hist, 
     }
     ctl->checks = n + 1;
     const bool converged = gap <= tol;
-    const bool failed = ctl->err != 0;
+    const bool failed = ctl->err == kErrWaitTimeout;
     const bool go = !converged && !failed && it + K <= max_iter;
     ctl->stop = go ? 0 : (failed ? 3 : (converged ? 1 : 2));
     cudaGraphSetConditional(h, go ? 1u : 0u);
@@ -566,6 +590,7 @@ cmf_status cmf_iterate_binary(const float* d_Cs, const float* d_Ct, const float*
     if (s != CMF_OK) return s;
     if (n_iter < 0) return CMF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    CMF_CUDA_TRY(cudaMemsetAsync(&((SolveCtl*)(c.wsbase + c.w.ctl))->err, 0, sizeof(int), st));
     int cur = 0;
     CMF_CUDA_TRY(binary_run(c, n_iter, cur, st));
     if (cur != 0) CMF_CUDA_TRY(copy_binary(c.user, c.ws, c.P.g, c.storage, st));

@@ -378,62 +378,86 @@ __global__ void k_binary_plain_dr_flows(BinProblem P, BinState<S> s, DrCoef D) {
 }
 
 // ---------------------------------------------------------------------------
-// Certificates (FP64 accumulation).  Each thread handles ROWS pixels of one
-// column; per-pixel terms are float32, sums are float64; one partial triple
-// (E, D, res^2) per block, reduced in a fixed order by k_reduce_partials.
+// Certificates (FP64 accumulation).  A block owns a 32 x TY tile (TY = 8 x
+// EVAL_ROWS): u is staged on the tile grown by one row / column on each side,
+// the flows y and their projections P_alpha(y) on the tile grown by one on
+// the low side, all in shared memory; per-pixel terms are float32, sums are
+// float64; one partial triple (E, D, res^2) per block, reduced in a fixed
+// order by k_reduce_partials.  For rPDRQ y = ybar + tau K u.
 // ---------------------------------------------------------------------------
-template <typename S, bool DR>
-__device__ __forceinline__ void binary_flow_at(const BinProblem& P, const BinState<S>& s,
-                                               float tau, int r, int c, float& fx, float& fy) {
-    using St = Store<S>;
-    const Grid& G = P.g;
-    const size_t k = G.idx(r, c);
-    fx = St::ldw(s.qx + k);
-    fy = St::ldw(s.qy + k);
-    if (DR) {
-        const float uc = s.u[k];
-        if (c < G.W - 1) fx -= tau * (s.u[k + 1] - uc);
-        if (r < G.H - 1) fy -= tau * (s.u[k + G.pitch] - uc);
-    }
-}
-
 template <typename S, bool ANISO, bool DR>
 __global__ void __launch_bounds__(256)
     k_binary_eval(BinProblem P, BinState<S> s, float tau, double* partials) {
+    constexpr int TX = 32, TY = 8 * EVAL_ROWS;
+    __shared__ float u_s[TY + 2][TX + 2];   // grid (y0-1+i, x0-1+j)
+    __shared__ float fx_s[TY + 1][TX + 1];  // grid (y0-1+i, x0-1+j)
+    __shared__ float fy_s[TY + 1][TX + 1];
+    __shared__ float px_s[TY + 1][TX + 1];
+    __shared__ float py_s[TY + 1][TX + 1];
     using St = Store<S>;
     const Grid G = P.g;
-    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+
+    for (int i = tid; i < (TY + 2) * (TX + 2); i += 256) {
+        const int a = i / (TX + 2), b = i - a * (TX + 2);
+        const int r = y0 - 1 + a, c = x0 - 1 + b;
+        u_s[a][b] = (r >= 0 && r < G.H && c >= 0 && c < G.W) ? s.u[G.idx(r, c)] : 0.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < (TY + 1) * (TX + 1); i += 256) {
+        const int a = i / (TX + 1), b = i - a * (TX + 1);
+        const int r = y0 - 1 + a, c = x0 - 1 + b;
+        float fx = 0.f, fy = 0.f, px = 0.f, py = 0.f;
+        if (r >= 0 && r < G.H && c >= 0 && c < G.W) {
+            const size_t k = G.idx(r, c);
+            fx = St::ldw(s.qx + k);
+            fy = St::ldw(s.qy + k);
+            if (DR) {
+                const float uc = u_s[a][b];
+                if (c < G.W - 1) fx -= tau * (u_s[a][b + 1] - uc);
+                if (r < G.H - 1) fy -= tau * (u_s[a + 1][b] - uc);
+            }
+            px = fx;
+            py = fy;
+            project_alpha<ANISO>(px, py, P.alpha.at(k));
+        }
+        fx_s[a][b] = fx;
+        fy_s[a][b] = fy;
+        px_s[a][b] = px;
+        py_s[a][b] = py;
+    }
+    __syncthreads();
+
     double accE = 0.0, accD = 0.0, accR = 0.0;
+#pragma unroll
     for (int j = 0; j < EVAL_ROWS; ++j) {
-        const int r = (blockIdx.y * 8 + threadIdx.y) * EVAL_ROWS + j;
+        const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
+        const int r = y0 + ly, c = x0 + lx;
         if (r >= G.H || c >= G.W) continue;
         const size_t k = G.idx(r, c);
         const float cs = __ldg(P.Cs + k), ct = __ldg(P.Ct + k);
         const float al = P.alpha.at(k);
         // primal energy at ub = clip(u, 0, 1)
-        const float ub = fminf(fmaxf(s.u[k], 0.f), 1.f);
-        const float gx = c < G.W - 1 ? fminf(fmaxf(s.u[k + 1], 0.f), 1.f) - ub : 0.f;
-        const float gy = r < G.H - 1 ? fminf(fmaxf(s.u[k + G.pitch], 0.f), 1.f) - ub : 0.f;
+        const float uc = u_s[ly + 1][lx + 1];
+        const float ub = fminf(fmaxf(uc, 0.f), 1.f);
+        const float gx = c < G.W - 1 ? fminf(fmaxf(u_s[ly + 1][lx + 2], 0.f), 1.f) - ub : 0.f;
+        const float gy = r < G.H - 1 ? fminf(fmaxf(u_s[ly + 2][lx + 1], 0.f), 1.f) - ub : 0.f;
         const float tv = ANISO ? fabsf(gx) + fabsf(gy) : sqrtf(gx * gx + gy * gy);
         accE += (double)((1.f - ub) * cs + ub * ct + al * tv);
-        // flows y and their divergence
-        float fx, fy, fxl = 0.f, fyl = 0.f, fxu = 0.f, fyu = 0.f;
-        binary_flow_at<S, DR>(P, s, tau, r, c, fx, fy);
-        if (c > 0) binary_flow_at<S, DR>(P, s, tau, r, c - 1, fxl, fyl);
-        if (r > 0) binary_flow_at<S, DR>(P, s, tau, r - 1, c, fxu, fyu);
+        // conservation residual of y, and the max-flow value of P_alpha(y);
+        // out-of-grid neighbours of the tile hold 0
         float ps = St::ldw(s.ps + k), pt = St::ldw(s.pt + k);
         if (DR) {
-            pt += tau * s.u[k];
-            ps -= tau * s.u[k];
+            pt += tau * uc;
+            ps -= tau * uc;
         }
-        const float dv = (c < G.W - 1 ? fx : 0.f) - fxl + (r < G.H - 1 ? fy : 0.f) - fyu;
+        const float dv = (c < G.W - 1 ? fx_s[ly + 1][lx + 1] : 0.f) - fx_s[ly + 1][lx] +
+                         (r < G.H - 1 ? fy_s[ly + 1][lx + 1] : 0.f) - fy_s[ly][lx + 1];
         const float rr = dv - ps + pt;
         accR += (double)(rr * rr);
-        // max-flow value of the projected (feasible) flow
-        project_alpha<ANISO>(fx, fy, al);
-        if (c > 0) project_alpha<ANISO>(fxl, fyl, P.alpha.at(k - 1));
-        if (r > 0) project_alpha<ANISO>(fxu, fyu, P.alpha.at(k - G.pitch));
-        const float dp = (c < G.W - 1 ? fx : 0.f) - fxl + (r < G.H - 1 ? fy : 0.f) - fyu;
+        const float dp = (c < G.W - 1 ? px_s[ly + 1][lx + 1] : 0.f) - px_s[ly + 1][lx] +
+                         (r < G.H - 1 ? py_s[ly + 1][lx + 1] : 0.f) - py_s[ly][lx + 1];
         accD += (double)fminf(cs, ct + dp);
     }
     block_reduce3_store(accE, accD, accR, partials);

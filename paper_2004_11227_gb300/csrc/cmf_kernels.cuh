@@ -154,6 +154,18 @@ cudaError_t potts_admm_tma_step(int storage, const PottsProblem& P, const PottsS
                                 bool aniso, const AdmmCoef& K, const PottsTmaMaps& src_maps,
                                 int* err, cudaStream_t st);
 
+// --- TMA-staged persistent binary ADMM (cmf_binary_tma.cu) ---
+struct BinTmaMaps {
+    CUtensorMap qx, qy, ps, pt, u;
+    int ty;  // output rows per tile (8, 16 or 32)
+};
+bool binary_tma_eligible(const Grid& G, int storage, const BinStateV& s);
+cudaError_t binary_tma_maps(const Grid& G, int storage, const BinStateV& s, int ty,
+                            BinTmaMaps& m);
+cudaError_t binary_admm_tma_step(int storage, const BinProblem& P, const BinStateV& b,
+                                 bool aniso, const AdmmCoef& K, const BinTmaMaps& src_maps,
+                                 int* err, cudaStream_t st);
+
 // --- reductions ---
 // Sum n partial triples in a fixed order into out[0..2] (one block).
 cudaError_t reduce_partials(const double* partials, int n, double* out, cudaStream_t st);

@@ -43,7 +43,7 @@ __device__ __forceinline__ float sload(const S* p) {
 }  // namespace
 
 template <typename S, bool ANISO, int TY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     k_potts_admm_tma(PottsProblem P, PottsState<S> s1, AdmmCoef K,
                      const __grid_constant__ CUtensorMap mqx,
                      const __grid_constant__ CUtensorMap mqy,
@@ -54,10 +54,14 @@ __global__ void __launch_bounds__(256)
     using St = Store<S>;
     constexpr int TX = 32, ROWS = TY / 8;
     constexpr int BXS = Lay::BXS, BXU = Lay::BXU, XO = Lay::XO, XU = Lay::XU;
+    constexpr int GW = TX + 2, GH = TY + 2;  // g cells: rows y0-1.., cols x0-1..
+    constexpr int QW = TX + 1, QH = TY + 1;  // q cells: rows y0-1.., cols x0-1..
+    constexpr int NG = (GW * GH + 255) / 256;
+    constexpr int NQ = (QW * QH + 255) / 256;
     __shared__ __align__(8) uint64_t bar[3];
-    __shared__ float g_s[TY + 2][TX + 2];
-    __shared__ float qnx[TY + 1][TX + 1];
-    __shared__ float qny[TY + 1][TX + 1];
+    __shared__ float g_s[GH * GW];
+    __shared__ float qnx[QH * QW];
+    __shared__ float qny[QH * QW];
     extern __shared__ __align__(128) unsigned char dsm_raw[];
     unsigned char* dsm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -92,8 +96,58 @@ __global__ void __launch_bounds__(256)
         issue(0, 0);
         if (L > 1) issue(1, 1);
     }
-    bool ok = mbar_wait_bounded(&bar[2], 0, kWaitLimitCycles);
 
+    // ---- per-thread cell data, the same for every label ----------------------
+    // g cells: staged offset (S arrays; the u array is offset by XU - XO) and
+    // the 0/1 weights of the far-boundary terms of div q
+    int g_off[NG], g_uoff[NG];
+    float g_mx[NG], g_my[NG];
+#pragma unroll
+    for (int n = 0; n < NG; ++n) {
+        const int i = tid + 256 * n;
+        const int gy = i / GW, gx = i - gy * GW;
+        const int r = y0 - 1 + gy, c = x0 - 1 + gx;
+        g_off[n] = i < GW * GH ? (gy + 1) * BXS + gx - 1 + XO : -1;
+        g_uoff[n] = (gy + 1) * BXU + gx - 1 + XO;
+        g_mx[n] = c < G.W - 1 ? 1.f : 0.f;
+        g_my[n] = r < G.H - 1 ? 1.f : 0.f;
+    }
+    // q cells: staged offset, g offset, weights, alpha, global offset of the
+    // tile part (-1: halo or outside the grid)
+    int q_off[NQ], q_goff[NQ];
+    long long q_k[NQ];
+    float q_mx[NQ], q_my[NQ], q_al[NQ];
+    bool q_in[NQ];
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) {
+        const int i = tid + 256 * n;
+        const int qy_ = i / QW, qx_ = i - qy_ * QW;
+        const int r = y0 - 1 + qy_, c = x0 - 1 + qx_;
+        const bool in = i < QW * QH && r >= 0 && r < G.H && c >= 0 && c < G.W;
+        q_in[n] = in;
+        q_off[n] = (qy_ + 1) * BXS + qx_ - 1 + XO;
+        q_goff[n] = qy_ * GW + qx_;
+        q_mx[n] = c < G.W - 1 ? K.inv_a : 0.f;
+        q_my[n] = r < G.H - 1 ? K.inv_a : 0.f;
+        q_al[n] = in ? P.alpha.at(G.idx(r, c)) : 0.f;
+        q_k[n] = (in && qy_ >= 1 && qx_ >= 1) ? (long long)G.idx(r, c) : -1;
+        if (i < QW * QH) {  // cells outside the grid keep q = 0 for every label
+            qnx[i] = 0.f;
+            qny[i] = 0.f;
+        }
+    }
+    // own pixels
+    long long o_k[ROWS];
+    float o_mx[ROWS], o_my[ROWS];
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+        const int r = y0 + threadIdx.y + 8 * j, c = x0 + threadIdx.x;
+        o_k[j] = (r < G.H && c < G.W) ? (long long)G.idx(r, c) : -1;
+        o_mx[j] = c < G.W - 1 ? 1.f : 0.f;
+        o_my[j] = r < G.H - 1 ? 1.f : 0.f;
+    }
+
+    bool ok = mbar_wait_bounded(&bar[2], 0, kWaitLimitCycles);
     float accd[ROWS], accp[ROWS];
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) accd[j] = accp[j] = 0.f;
@@ -104,13 +158,14 @@ __global__ void __launch_bounds__(256)
         const S* sqx = reinterpret_cast<const S*>(stage[s]);
         const S* sqy = reinterpret_cast<const S*>(stage[s] + Lay::FS);
         const S* sp = reinterpret_cast<const S*>(stage[s] + 2 * Lay::FS);
-        const float* su = reinterpret_cast<const float*>(stage[s] + 3 * Lay::FS);
+        // the u box starts XO - XU columns later than the S boxes
+        const float* su = reinterpret_cast<const float*>(stage[s] + 3 * Lay::FS) - (XO - XU);
         ok = ok && mbar_wait_bounded(&bar[s], (l >> 1) & 1, kWaitLimitCycles);
         if (__syncthreads_or(!ok)) {
             // a TMA stage never arrived: flag it, give in-flight copies a
             // bounded chance to land in this block's shared memory, return
             if (tid == 0) {
-                atomicExch(err, 1);
+                atomicExch(err, kErrWaitTimeout);
                 mbar_wait_bounded(&bar[0], (l >> 1) & 1, kWaitLimitCycles);
                 if (L > 1) mbar_wait_bounded(&bar[1], (l >> 1) & 1, kWaitLimitCycles);
             }
@@ -118,45 +173,40 @@ __global__ void __launch_bounds__(256)
         }
         const size_t lo = (size_t)l * G.plane;
 
-        // g_l on rows y0-1..y0+TY, cols x0-1..x0+TX
-        for (int i = tid; i < (TY + 2) * (TX + 2); i += 256) {
-            const int gy = i / (TX + 2), gx = i - gy * (TX + 2);
-            const int r = y0 - 1 + gy, c = x0 - 1 + gx;
-            const int sy = gy + 1, sx = gx - 1 + XO, su_x = gx - 1 + XU;
-            // neighbours outside the grid were zero-filled by the TMA unit
-            float dv = 0.f;
-            if (c < G.W - 1) dv += sload(sqx + sy * BXS + sx);
-            dv -= sload(sqx + sy * BXS + sx - 1);
-            if (r < G.H - 1) dv += sload(sqy + sy * BXS + sx);
-            dv -= sload(sqy + (sy - 1) * BXS + sx);
-            g_s[gy][gx] = dv + sload(sp + sy * BXS + sx) - sload(ps_s + sy * BXS + sx) -
-                          su[sy * BXU + su_x] * K.inv_c;
+        // g_l = div q_l + p_l - p_s - u_l / c (zero-filled outside the grid)
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            const int o = g_off[n];
+            if (o >= 0) {
+                float dv = g_mx[n] * sload(sqx + o);
+                dv -= sload(sqx + o - 1);
+                dv += g_my[n] * sload(sqy + o);
+                dv -= sload(sqy + o - BXS);
+                g_s[tid + 256 * n] =
+                    dv + sload(sp + o) - sload(ps_s + o) - su[g_uoff[n]] * K.inv_c;
+            }
         }
         __syncthreads();
 
-        // q_l^{k+1} on rows y0-1..y0+TY-1, cols x0-1..x0+TX-1
-        for (int i = tid; i < (TY + 1) * (TX + 1); i += 256) {
-            const int qy_ = i / (TX + 1), qx_ = i - qy_ * (TX + 1);
-            const int r = y0 - 1 + qy_, c = x0 - 1 + qx_;
-            float tx = 0.f, ty = 0.f;
-            if (r >= 0 && r < G.H && c >= 0 && c < G.W) {
-                const int sy = qy_ + 1, sx = qx_ - 1 + XO;
-                const size_t k = G.idx(r, c);
-                const float gc = g_s[qy_][qx_];
-                tx = sload(sqx + sy * BXS + sx) +
-                     (c < G.W - 1 ? (g_s[qy_][qx_ + 1] - gc) * K.inv_a : 0.f);
-                ty = sload(sqy + sy * BXS + sx) +
-                     (r < G.H - 1 ? (g_s[qy_ + 1][qx_] - gc) * K.inv_a : 0.f);
-                project_alpha<ANISO>(tx, ty, P.alpha.at(k));
+        // q_l^{k+1} = P_alpha(q_l + grad g_l / a)
+#pragma unroll
+        for (int n = 0; n < NQ; ++n) {
+            if (q_in[n]) {
+                const int o = q_off[n], go = q_goff[n];
+                const float gc = g_s[go];
+                float tx = sload(sqx + o) + (g_s[go + 1] - gc) * q_mx[n];
+                float ty = sload(sqy + o) + (g_s[go + GW] - gc) * q_my[n];
+                project_alpha<ANISO>(tx, ty, q_al[n]);
                 tx = St::rt(tx);
                 ty = St::rt(ty);
-                if (qy_ >= 1 && qx_ >= 1) {
-                    St::st(s1.qx + lo + k, tx);
-                    St::st(s1.qy + lo + k, ty);
+                if (q_k[n] >= 0) {
+                    St::st(s1.qx + lo + q_k[n], tx);
+                    St::st(s1.qy + lo + q_k[n], ty);
                 }
+                const int i = tid + 256 * n;
+                qnx[i] = tx;
+                qny[i] = ty;
             }
-            qnx[qy_][qx_] = tx;
-            qny[qy_][qx_] = ty;
         }
         __syncthreads();
 
@@ -164,23 +214,21 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-            const int r = y0 + ly, c = x0 + lx;
             float v = 0.f;
-            if (r < G.H && c < G.W) {
-                const size_t k = G.idx(r, c);
-                float d = 0.f;  // out-of-grid neighbours of the q tile hold 0
-                if (c < G.W - 1) d += qnx[ly + 1][lx + 1];
-                d -= qnx[ly + 1][lx];
-                if (r < G.H - 1) d += qny[ly + 1][lx + 1];
-                d -= qny[ly][lx + 1];
-                const int sy = ly + 2;
-                const float ps0 = sload(ps_s + sy * BXS + lx + XO);
-                const float p0 = sload(sp + sy * BXS + lx + XO);
-                const float u0 = su[sy * BXU + lx + XU];
+            if (o_k[j] >= 0) {
+                const int qi = (ly + 1) * QW + lx + 1;
+                float d = o_mx[j] * qnx[qi];
+                d -= qnx[qi - 1];
+                d += o_my[j] * qny[qi];
+                d -= qny[qi - QW];
+                const int so = (ly + 2) * BXS + lx + XO;
+                const float ps0 = sload(ps_s + so);
+                const float p0 = sload(sp + so);
+                const float u0 = su[(ly + 2) * BXU + lx + XO];
                 float p1 = fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * d) * K.inv_a1,
-                                 __ldg(P.C + lo + k));
+                                 __ldg(P.C + lo + o_k[j]));
                 p1 = St::rt(p1);
-                St::st(s1.p + lo + k, p1);
+                St::st(s1.p + lo + o_k[j], p1);
                 accd[j] += K.rho_p * d;
                 accp[j] += K.rho_p * (p0 - ps0) - u0 * K.inv_c;
                 v = u0 - K.cu * (p1 - K.omr * (p0 - ps0) + K.rho_p * d);
@@ -198,23 +246,20 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
         const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-        const int r = y0 + ly, c = x0 + lx;
         ps1[j] = 0.f;
-        if (r < G.H && c < G.W) {
+        if (o_k[j] >= 0) {
             const float ps0 = sload(ps_s + (ly + 2) * BXS + lx + XO);
             ps1[j] = St::rt(ps0 + (accd[j] + accp[j] + K.inv_c) * K.inv_a2);
-            St::st(s1.ps + G.idx(r, c), ps1[j]);
+            St::st(s1.ps + o_k[j], ps1[j]);
         }
     }
 #pragma unroll 1
     for (int l = 0; l < L; ++l) {
+        const size_t lo = (size_t)l * G.plane;
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-            const int r = y0 + ly, c = x0 + lx;
-            if (r < G.H && c < G.W)
-                s1.u[(size_t)l * G.plane + G.idx(r, c)] =
-                    v_s[(l * TY + ly) * TX + lx] + K.cu * ps1[j];
+            if (o_k[j] >= 0) s1.u[lo + o_k[j]] = v_s[(l * TY + ly) * TX + lx] + K.cu * ps1[j];
         }
     }
 }
@@ -225,10 +270,12 @@ static size_t tma_smem_bytes(int storage, int L, int ty) {
     size_t dyn;
     if (storage == CMF_F32)
         dyn = ty == 32 ? PottsTmaLayout<float, 32>::dyn_bytes(L)
-                       : PottsTmaLayout<float, 16>::dyn_bytes(L);
+                       : (ty == 8 ? PottsTmaLayout<float, 8>::dyn_bytes(L)
+                                  : PottsTmaLayout<float, 16>::dyn_bytes(L));
     else
         dyn = ty == 32 ? PottsTmaLayout<__half, 32>::dyn_bytes(L)
-                       : PottsTmaLayout<__half, 16>::dyn_bytes(L);
+                       : (ty == 8 ? PottsTmaLayout<__half, 8>::dyn_bytes(L)
+                                  : PottsTmaLayout<__half, 16>::dyn_bytes(L));
     return stat + dyn;
 }
 
@@ -290,6 +337,9 @@ static cudaError_t potts_admm_tma_s(const PottsProblem& P, const PottsStateV& b,
     if (m.ty == 32)
         return aniso ? launch_tma<S, true, 32>(P, B, K, m, err, st)
                      : launch_tma<S, false, 32>(P, B, K, m, err, st);
+    if (m.ty == 8)
+        return aniso ? launch_tma<S, true, 8>(P, B, K, m, err, st)
+                     : launch_tma<S, false, 8>(P, B, K, m, err, st);
     return aniso ? launch_tma<S, true, 16>(P, B, K, m, err, st)
                  : launch_tma<S, false, 16>(P, B, K, m, err, st);
 }

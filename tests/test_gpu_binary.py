@@ -233,3 +233,18 @@ def test_graph_solve_equals_host_loop(cmf, algo, impl):
         b = cmf.alloc_binary(inst, p)
         st, it, hist = cmf.cmf_solve_binary(b)
         assert st == cmf.NOT_CONVERGED and it == 40 and len(hist) == 4
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("variant", [8, 16, 32])
+@pytest.mark.parametrize("shape", [(70, 97), (5, 130), (131, 33)])
+def test_tma_tiles_match_smem_tiles(cmf, storage, variant, shape):
+    """The persistent TMA-staged fused ADMM kernel computes what the
+    shared-memory tile kernel computes (only the staging differs)."""
+    inst = synth.random_binary(*shape, seed=90, alpha=0.3, field_alpha=True)
+    for algo in (0, 2):
+        a = _gpu_run(cmf, inst, algo, 9, storage=storage, variant=1).state()
+        b = _gpu_run(cmf, inst, algo, 9, storage=storage, variant=variant).state()
+        tol = 1e-6 if storage == 0 else 1e-2
+        for k in a:
+            assert np.abs(a[k] - b[k]).max() <= tol, k

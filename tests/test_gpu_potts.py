@@ -193,7 +193,7 @@ def test_full_size_4096_L16_f16_windows(cmf):
 
 
 @pytest.mark.parametrize("storage", [0, 1, 2])
-@pytest.mark.parametrize("variant", [16, 32])
+@pytest.mark.parametrize("variant", [8, 16, 32])
 @pytest.mark.parametrize("L,shape", [(4, (70, 97)), (16, (33, 40)), (3, (5, 130))])
 def test_tma_tiles_match_smem_tiles(cmf, storage, variant, L, shape):
     """The TMA-staged fused ADMM kernel computes what the shared-memory tile
