@@ -56,13 +56,14 @@ __global__ void __launch_bounds__(256, 4)
     constexpr int NG = (GW * GH + 255) / 256;
     constexpr int NQ = (QW * QH + 255) / 256;
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float g_s[GH * GW];
-    __shared__ float qnx[QH * QW];
-    __shared__ float qny[QH * QW];
+    // cell arrays padded to whole multiples of the block; padding slots are
+    // computed and never read
+    __shared__ float g_s[NG * 256];
+    __shared__ float qnx[NQ * 256];
+    __shared__ float qny[NQ * 256];
     extern __shared__ __align__(128) unsigned char dsm_raw[];
-    unsigned char* dsm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~static_cast<uintptr_t>(127));
-    unsigned char* stage[2] = {dsm, dsm + Lay::STAGE};
+    // round up to 128 bytes by pointer arithmetic (keeps the shared space)
+    unsigned char* dsm = dsm_raw + ((128u - (smem_u32(dsm_raw) & 127u)) & 127u);
 
     const Grid G = P.g;
     const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256, 4)
 
     auto issue = [&](int t, int s) {
         const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-        unsigned char* d = stage[s];
+        unsigned char* d = dsm + s * Lay::STAGE;
         mbar_arrive_expect_tx(&bar[s], Lay::TX_BYTES);
         tma_load_3d(d, &mqx, &bar[s], x0 - XO, y0 - 2, 0);
         tma_load_3d(d + Lay::FS, &mqy, &bar[s], x0 - XO, y0 - 2, 0);
@@ -97,18 +98,20 @@ __global__ void __launch_bounds__(256, 4)
 #pragma unroll
     for (int n = 0; n < NG; ++n) {
         const int i = tid + 256 * n;
-        const int gy = i / GW, gx = i - gy * GW;
-        g_off[n] = i < GW * GH ? (gy + 1) * BXS + gx - 1 + XO : -1;
+        const int gy = i < GW * GH ? i / GW : 0, gx = i < GW * GH ? i - gy * GW : 1;
+        g_off[n] = (gy + 1) * BXS + gx - 1 + XO;
         g_uoff[n] = (gy + 1) * BXU + gx - 1 + XO;
         g_r[n] = gy - 1;
         g_c[n] = gx - 1;
     }
     int q_off[NQ], q_goff[NQ], q_r[NQ], q_c[NQ];
+    bool q_cell[NQ];
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
         const int i = tid + 256 * n;
-        const int qy_ = i / QW, qx_ = i - qy_ * QW;
-        q_off[n] = i < QW * QH ? (qy_ + 1) * BXS + qx_ - 1 + XO : -1;
+        q_cell[n] = i < QW * QH;
+        const int qy_ = q_cell[n] ? i / QW : 1, qx_ = q_cell[n] ? i - qy_ * QW : 1;
+        q_off[n] = (qy_ + 1) * BXS + qx_ - 1 + XO;
         q_goff[n] = qy_ * GW + qx_;
         q_r[n] = qy_ - 1;
         q_c[n] = qx_ - 1;
@@ -118,11 +121,12 @@ __global__ void __launch_bounds__(256, 4)
     for (int t = t0, k = 0; t < ntiles; t += dt, ++k) {
         const int s = k & 1;
         const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-        const S* sqx = reinterpret_cast<const S*>(stage[s]);
-        const S* sqy = reinterpret_cast<const S*>(stage[s] + Lay::FS);
-        const S* sps = reinterpret_cast<const S*>(stage[s] + 2 * Lay::FS);
-        const S* spt = reinterpret_cast<const S*>(stage[s] + 3 * Lay::FS);
-        const float* su = reinterpret_cast<const float*>(stage[s] + 4 * Lay::FS) - (XO - XU);
+        const unsigned char* stg = dsm + s * Lay::STAGE;
+        const S* sqx = reinterpret_cast<const S*>(stg);
+        const S* sqy = reinterpret_cast<const S*>(stg + Lay::FS);
+        const S* sps = reinterpret_cast<const S*>(stg + 2 * Lay::FS);
+        const S* spt = reinterpret_cast<const S*>(stg + 3 * Lay::FS);
+        const float* su = reinterpret_cast<const float*>(stg + 4 * Lay::FS) - (XO - XU);
         const bool ok = mbar_wait_bounded(&bar[s], (k >> 1) & 1, kWaitLimitCycles);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -136,42 +140,34 @@ __global__ void __launch_bounds__(256, 4)
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
             const int o = g_off[n];
-            if (o >= 0) {
-                const int r = y0 + g_r[n], c = x0 + g_c[n];
-                float dv = 0.f;
-                if (c < G.W - 1) dv += bload(sqx + o);
-                dv -= bload(sqx + o - 1);
-                if (r < G.H - 1) dv += bload(sqy + o);
-                dv -= bload(sqy + o - BXS);
-                g_s[tid + 256 * n] = dv + bload(spt + o) - bload(sps + o) - su[g_uoff[n]] * K.inv_c;
-            }
+            const int r = y0 + g_r[n], c = x0 + g_c[n];
+            float dv = c < G.W - 1 ? bload(sqx + o) : 0.f;
+            dv -= bload(sqx + o - 1);
+            dv += r < G.H - 1 ? bload(sqy + o) : 0.f;
+            dv -= bload(sqy + o - BXS);
+            g_s[tid + 256 * n] = dv + bload(spt + o) - bload(sps + o) - su[g_uoff[n]] * K.inv_c;
         }
         __syncthreads();
 
         // q^{k+1} = P_alpha(q + grad g / a) on rows y0-1.., cols x0-1..
 #pragma unroll
         for (int n = 0; n < NQ; ++n) {
-            const int o = q_off[n];
-            if (o >= 0) {
-                const int r = y0 + q_r[n], c = x0 + q_c[n];
-                float tx = 0.f, ty = 0.f;
-                if (r >= 0 && r < G.H && c >= 0 && c < G.W) {
-                    const int go = q_goff[n];
-                    const size_t kk = G.idx(r, c);
-                    const float gc = g_s[go];
-                    tx = bload(sqx + o) + (c < G.W - 1 ? (g_s[go + 1] - gc) * K.inv_a : 0.f);
-                    ty = bload(sqy + o) + (r < G.H - 1 ? (g_s[go + GW] - gc) * K.inv_a : 0.f);
-                    project_alpha<ANISO>(tx, ty, P.alpha.at(kk));
-                    tx = St::rt(tx);
-                    ty = St::rt(ty);
-                    if (q_r[n] >= 0 && q_c[n] >= 0) {
-                        St::st(s1.qx + kk, tx);
-                        St::st(s1.qy + kk, ty);
-                    }
-                }
-                qnx[tid + 256 * n] = tx;
-                qny[tid + 256 * n] = ty;
+            const int o = q_off[n], go = q_goff[n];
+            const int r = y0 + q_r[n], c = x0 + q_c[n];
+            const bool in = q_cell[n] && r >= 0 && r < G.H && c >= 0 && c < G.W;
+            const size_t kk = in ? G.idx(r, c) : 0;
+            const float gc = g_s[go];
+            float tx = bload(sqx + o) + (c < G.W - 1 ? (g_s[go + 1] - gc) * K.inv_a : 0.f);
+            float ty = bload(sqy + o) + (r < G.H - 1 ? (g_s[go + GW] - gc) * K.inv_a : 0.f);
+            project_alpha<ANISO>(tx, ty, P.alpha.at(kk));
+            tx = in ? St::rt(tx) : 0.f;
+            ty = in ? St::rt(ty) : 0.f;
+            if (in && q_r[n] >= 0 && q_c[n] >= 0) {
+                St::st(s1.qx + kk, tx);
+                St::st(s1.qy + kk, ty);
             }
+            qnx[tid + 256 * n] = tx;
+            qny[tid + 256 * n] = ty;
         }
         __syncthreads();
 
@@ -242,7 +238,7 @@ template <typename S, bool ANISO, int TY>
 static cudaError_t launch_bin_tma(const BinProblem& P, const BinState<S>& b, const AdmmCoef& K,
                                   const BinTmaMaps& m, int* err, cudaStream_t st) {
     using Lay = BinTmaLayout<S, TY>;
-    auto kern = k_binary_admm_tma<S, ANISO, TY>;
+    auto kern = k_binary_admm_tma<S, ANISO, TY>;  // static smem: (NG + 2 NQ) x 256 floats
     static int blocks_per_sm = 0;
     static int sms = 0;
     if (!blocks_per_sm) {

@@ -59,13 +59,14 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     constexpr int NG = (GW * GH + 255) / 256;
     constexpr int NQ = (QW * QH + 255) / 256;
     __shared__ __align__(8) uint64_t bar[3];
-    __shared__ float g_s[GH * GW];
-    __shared__ float qnx[QH * QW];
-    __shared__ float qny[QH * QW];
+    // cell arrays padded to whole multiples of the block so every thread owns
+    // NG / NQ slots; the padding slots are computed and never read
+    __shared__ float g_s[NG * 256];
+    __shared__ float qnx[NQ * 256];
+    __shared__ float qny[NQ * 256];
     extern __shared__ __align__(128) unsigned char dsm_raw[];
-    unsigned char* dsm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~static_cast<uintptr_t>(127));
-    unsigned char* stage[2] = {dsm, dsm + Lay::STAGE};
+    // round up to 128 bytes by pointer arithmetic (keeps the shared space)
+    unsigned char* dsm = dsm_raw + ((128u - (smem_u32(dsm_raw) & 127u)) & 127u);
     S* ps_s = reinterpret_cast<S*>(dsm + 2 * Lay::STAGE);
     float* v_s = reinterpret_cast<float*>(dsm + 2 * Lay::STAGE + Lay::FS);
 
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
 
     auto issue = [&](int l, int s) {
-        unsigned char* d = stage[s];
+        unsigned char* d = dsm + s * Lay::STAGE;
         mbar_arrive_expect_tx(&bar[s], Lay::TX_BYTES);
         tma_load_3d(d, &mqx, &bar[s], x0 - XO, y0 - 2, l);
         tma_load_3d(d + Lay::FS, &mqy, &bar[s], x0 - XO, y0 - 2, l);
@@ -98,32 +99,33 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     }
 
     // ---- per-thread cell data, the same for every label ----------------------
-    // g cells: staged offset (S arrays; the u array is offset by XU - XO) and
-    // the 0/1 weights of the far-boundary terms of div q
+    // g cells: staged offset (the u box is addressed through a pointer shifted
+    // by XO - XU columns) and the 0/1 weights of the far-boundary terms
     int g_off[NG], g_uoff[NG];
     float g_mx[NG], g_my[NG];
 #pragma unroll
     for (int n = 0; n < NG; ++n) {
         const int i = tid + 256 * n;
-        const int gy = i / GW, gx = i - gy * GW;
+        const int gy = i < GW * GH ? i / GW : 0, gx = i < GW * GH ? i - gy * GW : 1;
         const int r = y0 - 1 + gy, c = x0 - 1 + gx;
-        g_off[n] = i < GW * GH ? (gy + 1) * BXS + gx - 1 + XO : -1;
+        g_off[n] = (gy + 1) * BXS + gx - 1 + XO;
         g_uoff[n] = (gy + 1) * BXU + gx - 1 + XO;
         g_mx[n] = c < G.W - 1 ? 1.f : 0.f;
         g_my[n] = r < G.H - 1 ? 1.f : 0.f;
     }
-    // q cells: staged offset, g offset, weights, alpha, global offset of the
-    // tile part (-1: halo or outside the grid)
+    // q cells: staged offset, g offset, weights (times 1/a), alpha, in-grid
+    // flag, output pointers of the tile part (null: halo or outside)
     int q_off[NQ], q_goff[NQ];
-    long long q_k[NQ];
     float q_mx[NQ], q_my[NQ], q_al[NQ];
     bool q_in[NQ];
+    long long q_k[NQ];
 #pragma unroll
     for (int n = 0; n < NQ; ++n) {
         const int i = tid + 256 * n;
-        const int qy_ = i / QW, qx_ = i - qy_ * QW;
+        const bool cell = i < QW * QH;
+        const int qy_ = cell ? i / QW : 1, qx_ = cell ? i - qy_ * QW : 1;
         const int r = y0 - 1 + qy_, c = x0 - 1 + qx_;
-        const bool in = i < QW * QH && r >= 0 && r < G.H && c >= 0 && c < G.W;
+        const bool in = cell && r >= 0 && r < G.H && c >= 0 && c < G.W;
         q_in[n] = in;
         q_off[n] = (qy_ + 1) * BXS + qx_ - 1 + XO;
         q_goff[n] = qy_ * GW + qx_;
@@ -131,10 +133,6 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
         q_my[n] = r < G.H - 1 ? K.inv_a : 0.f;
         q_al[n] = in ? P.alpha.at(G.idx(r, c)) : 0.f;
         q_k[n] = (in && qy_ >= 1 && qx_ >= 1) ? (long long)G.idx(r, c) : -1;
-        if (i < QW * QH) {  // cells outside the grid keep q = 0 for every label
-            qnx[i] = 0.f;
-            qny[i] = 0.f;
-        }
     }
     // own pixels
     long long o_k[ROWS];
@@ -155,11 +153,12 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
 #pragma unroll 1
     for (int l = 0; l < L; ++l) {
         const int s = l & 1;
-        const S* sqx = reinterpret_cast<const S*>(stage[s]);
-        const S* sqy = reinterpret_cast<const S*>(stage[s] + Lay::FS);
-        const S* sp = reinterpret_cast<const S*>(stage[s] + 2 * Lay::FS);
+        const unsigned char* stg = dsm + s * Lay::STAGE;
+        const S* sqx = reinterpret_cast<const S*>(stg);
+        const S* sqy = reinterpret_cast<const S*>(stg + Lay::FS);
+        const S* sp = reinterpret_cast<const S*>(stg + 2 * Lay::FS);
         // the u box starts XO - XU columns later than the S boxes
-        const float* su = reinterpret_cast<const float*>(stage[s] + 3 * Lay::FS) - (XO - XU);
+        const float* su = reinterpret_cast<const float*>(stg + 3 * Lay::FS) - (XO - XU);
         ok = ok && mbar_wait_bounded(&bar[s], (l >> 1) & 1, kWaitLimitCycles);
         if (__syncthreads_or(!ok)) {
             // a TMA stage never arrived: flag it, give in-flight copies a
@@ -172,41 +171,40 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
             return;
         }
         const size_t lo = (size_t)l * G.plane;
+        S* qx_out = s1.qx + lo;
+        S* qy_out = s1.qy + lo;
+        S* p_out = s1.p + lo;
+        const float* C_l = P.C + lo;
 
         // g_l = div q_l + p_l - p_s - u_l / c (zero-filled outside the grid)
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
             const int o = g_off[n];
-            if (o >= 0) {
-                float dv = g_mx[n] * sload(sqx + o);
-                dv -= sload(sqx + o - 1);
-                dv += g_my[n] * sload(sqy + o);
-                dv -= sload(sqy + o - BXS);
-                g_s[tid + 256 * n] =
-                    dv + sload(sp + o) - sload(ps_s + o) - su[g_uoff[n]] * K.inv_c;
-            }
+            float dv = g_mx[n] * sload(sqx + o);
+            dv -= sload(sqx + o - 1);
+            dv += g_my[n] * sload(sqy + o);
+            dv -= sload(sqy + o - BXS);
+            g_s[tid + 256 * n] =
+                dv + sload(sp + o) - sload(ps_s + o) - su[g_uoff[n]] * K.inv_c;
         }
         __syncthreads();
 
-        // q_l^{k+1} = P_alpha(q_l + grad g_l / a)
+        // q_l^{k+1} = P_alpha(q_l + grad g_l / a); 0 outside the grid
 #pragma unroll
         for (int n = 0; n < NQ; ++n) {
-            if (q_in[n]) {
-                const int o = q_off[n], go = q_goff[n];
-                const float gc = g_s[go];
-                float tx = sload(sqx + o) + (g_s[go + 1] - gc) * q_mx[n];
-                float ty = sload(sqy + o) + (g_s[go + GW] - gc) * q_my[n];
-                project_alpha<ANISO>(tx, ty, q_al[n]);
-                tx = St::rt(tx);
-                ty = St::rt(ty);
-                if (q_k[n] >= 0) {
-                    St::st(s1.qx + lo + q_k[n], tx);
-                    St::st(s1.qy + lo + q_k[n], ty);
-                }
-                const int i = tid + 256 * n;
-                qnx[i] = tx;
-                qny[i] = ty;
+            const int o = q_off[n], go = q_goff[n];
+            const float gc = g_s[go];
+            float tx = sload(sqx + o) + (g_s[go + 1] - gc) * q_mx[n];
+            float ty = sload(sqy + o) + (g_s[go + GW] - gc) * q_my[n];
+            project_alpha<ANISO>(tx, ty, q_al[n]);
+            tx = q_in[n] ? St::rt(tx) : 0.f;
+            ty = q_in[n] ? St::rt(ty) : 0.f;
+            if (q_k[n] >= 0) {
+                St::st(qx_out + q_k[n], tx);
+                St::st(qy_out + q_k[n], ty);
             }
+            qnx[tid + 256 * n] = tx;
+            qny[tid + 256 * n] = ty;
         }
         __syncthreads();
 
@@ -214,26 +212,23 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-            float v = 0.f;
-            if (o_k[j] >= 0) {
-                const int qi = (ly + 1) * QW + lx + 1;
-                float d = o_mx[j] * qnx[qi];
-                d -= qnx[qi - 1];
-                d += o_my[j] * qny[qi];
-                d -= qny[qi - QW];
-                const int so = (ly + 2) * BXS + lx + XO;
-                const float ps0 = sload(ps_s + so);
-                const float p0 = sload(sp + so);
-                const float u0 = su[(ly + 2) * BXU + lx + XO];
-                float p1 = fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * d) * K.inv_a1,
-                                 __ldg(P.C + lo + o_k[j]));
-                p1 = St::rt(p1);
-                St::st(s1.p + lo + o_k[j], p1);
-                accd[j] += K.rho_p * d;
-                accp[j] += K.rho_p * (p0 - ps0) - u0 * K.inv_c;
-                v = u0 - K.cu * (p1 - K.omr * (p0 - ps0) + K.rho_p * d);
-            }
-            v_s[(l * TY + ly) * TX + lx] = v;
+            const int qi = (ly + 1) * QW + lx + 1;
+            float d = o_mx[j] * qnx[qi];
+            d -= qnx[qi - 1];
+            d += o_my[j] * qny[qi];
+            d -= qny[qi - QW];
+            const int so = (ly + 2) * BXS + lx + XO;
+            const float ps0 = sload(ps_s + so);
+            const float p0 = sload(sp + so);
+            const float u0 = su[(ly + 2) * BXU + lx + XO];
+            const bool own = o_k[j] >= 0;
+            const float cl = __ldg(C_l + (own ? o_k[j] : 0));
+            float p1 = fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * d) * K.inv_a1, cl);
+            p1 = St::rt(p1);
+            if (own) St::st(p_out + o_k[j], p1);
+            accd[j] += K.rho_p * d;
+            accp[j] += K.rho_p * (p0 - ps0) - u0 * K.inv_c;
+            v_s[(l * TY + ly) * TX + lx] = u0 - K.cu * (p1 - K.omr * (p0 - ps0) + K.rho_p * d);
         }
         __syncthreads();
         if (tid == 0 && l + 2 < L) {
@@ -246,27 +241,25 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
         const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-        ps1[j] = 0.f;
-        if (o_k[j] >= 0) {
-            const float ps0 = sload(ps_s + (ly + 2) * BXS + lx + XO);
-            ps1[j] = St::rt(ps0 + (accd[j] + accp[j] + K.inv_c) * K.inv_a2);
-            St::st(s1.ps + o_k[j], ps1[j]);
-        }
+        const float ps0 = sload(ps_s + (ly + 2) * BXS + lx + XO);
+        ps1[j] = St::rt(ps0 + (accd[j] + accp[j] + K.inv_c) * K.inv_a2);
+        if (o_k[j] >= 0) St::st(s1.ps + o_k[j], ps1[j]);
     }
 #pragma unroll 1
     for (int l = 0; l < L; ++l) {
-        const size_t lo = (size_t)l * G.plane;
+        float* u_out = s1.u + (size_t)l * G.plane;
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-            if (o_k[j] >= 0) s1.u[lo + o_k[j]] = v_s[(l * TY + ly) * TX + lx] + K.cu * ps1[j];
+            if (o_k[j] >= 0) u_out[o_k[j]] = v_s[(l * TY + ly) * TX + lx] + K.cu * ps1[j];
         }
     }
 }
 
 // Shared memory one block of the TMA kernel needs (static + dynamic).
 static size_t tma_smem_bytes(int storage, int L, int ty) {
-    const size_t stat = (size_t)(ty + 2) * 34 * 4 + 2 * (size_t)(ty + 1) * 33 * 4 + 64;
+    const size_t ng = ((size_t)(ty + 2) * 34 + 255) / 256, nq = ((size_t)(ty + 1) * 33 + 255) / 256;
+    const size_t stat = (ng + 2 * nq) * 256 * 4 + 64;
     size_t dyn;
     if (storage == CMF_F32)
         dyn = ty == 32 ? PottsTmaLayout<float, 32>::dyn_bytes(L)
