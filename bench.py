@@ -185,6 +185,98 @@ def algorithmic_bytes_per_px(model: str, L: int, storage: int, alpha_field: bool
     return L * (4 * 2 + 3 * s * 2 + 4) + 2 * s + (4 if alpha_field else 0)
 
 
+def potts_workloads(cmf, synth, flush) -> dict:
+    """The HBM-bound Potts workloads, measured on the side: 2048^2 with 4
+    labels in float32 and 4096^2 with 16 labels and float16 flow storage
+    (rpADMMII).  Per workload: the fused iteration's time and algorithmic
+    bandwidth over 50 back-to-back launches (inputs far larger than L2), and
+    the time to a 1e-4 gap from a cold start."""
+    import torch
+
+    peak, _ = _peaks()
+    out = {}
+    # (the 4096^2 solve is capped at 1000 iterations; see --precision-study
+    # for its convergence in float32 / float16 / bfloat16 storage)
+    cases = [("potts L=4 2048x2048 float32, alpha 0.3", lambda: synth.config3(), 0, 20000),
+             ("potts L=16 4096x4096 float16 flows, edge-weighted alpha", lambda: synth.config5(),
+              1, 1000)]
+    for name, make, storage, max_iter in cases:
+        inst = make()
+        p = cmf.default_params(2, inst.L, storage=storage, tol_gap=1e-4, max_iter=max_iter,
+                               check_every=10)
+        s = cmf.alloc_potts(inst, p)
+        cmf.cmf_init_potts(s)
+        cmf.cmf_iterate_potts(s, 10)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n = 50
+        e0.record()
+        cmf.cmf_iterate_potts(s, n)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        nb = algorithmic_bytes_per_px("potts", inst.L, storage,
+                                      isinstance(inst.alpha, np.ndarray)) * inst.H * inst.W
+        cmf.cmf_solve_potts(s)  # warm
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        st, iters, hist = cmf.cmf_solve_potts(s)
+        e1.record()
+        e1.synchronize()
+        out[name] = {
+            "ms_per_iter": round(ms, 4),
+            "px_label_it_per_s": inst.H * inst.W * inst.L / ms * 1e3,
+            "algorithmic_GBps": nb / ms / 1e6, "hbm_frac_of_measured": nb / ms / 1e6 / peak,
+            "bytes_per_px": nb // (inst.H * inst.W),
+            "time_to_gap_ms": round(e0.elapsed_time(e1), 2), "iterations": iters,
+            "converged": st == cmf.OK, "final_gap": float(hist[-1, 3]),
+        }
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+def precision_study(size: int, max_iter: int):
+    """Convergence of the 16-label Voronoi workload (edge-weighted alpha) at
+    size x size under float32, float16 and bfloat16 flow storage: one JSON
+    line per certificate check (iteration, E, D, gap) and per storage the
+    relative primal-energy error against the float32 run's final energy."""
+    import torch
+
+    import __graft_entry__
+    from paper_2004_11227_gb300 import cmf, synth
+
+    __graft_entry__.build()
+    inst = synth.config5(size, size)
+    runs = {}
+    for storage, name in ((0, "float32"), (1, "float16"), (2, "bfloat16")):
+        p = cmf.default_params(2, 16, storage=storage, tol_gap=0.0, max_iter=max_iter,
+                               check_every=50)
+        s = cmf.alloc_potts(inst, p)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, iters, hist = cmf.cmf_solve_potts(s, hist_cap=max_iter // 50 + 2)
+        e1.record()
+        e1.synchronize()
+        runs[name] = (hist, e0.elapsed_time(e1) / iters)
+        del s
+        torch.cuda.empty_cache()
+    e_ref = runs["float32"][0][-1, 1]
+    for name, (hist, ms) in runs.items():
+        rel = np.abs(hist[:, 1] - e_ref) / abs(e_ref)
+        hit_gap = [int(h[0]) for h in hist if h[3] <= 1e-4]
+        hit_rel = [int(hist[i, 0]) for i in range(len(hist)) if rel[i] <= 1e-4]
+        print(json.dumps({"storage": name, "size": size, "ms_per_iter": ms,
+                          "final_gap": float(hist[-1, 3]), "min_gap": float(hist[:, 3].min()),
+                          "iters_to_gap_1e-4": hit_gap[0] if hit_gap else None,
+                          "iters_to_primal_rel_1e-4_vs_f32_final": hit_rel[0] if hit_rel else None,
+                          "trajectory": [[int(h[0]), float(h[3]), float(r)]
+                                         for h, r in zip(hist[::4], rel[::4])]}))
+
+
 def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int = 0):
     """Cold start plus `iters` iterations of one configuration: untimed for
     profiler captures (ncu -k <kernel> -c <n>), or timed with CUDA events."""
@@ -236,7 +328,15 @@ def main():
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--time", action="store_true", help="time the kernel case")
     ap.add_argument("--variant", type=int, default=0, help="cmf_params.variant")
+    ap.add_argument("--skip-potts", action="store_true",
+                    help="skip the side measurements of the Potts workloads")
+    ap.add_argument("--precision-study", type=int, default=0, metavar="SIZE",
+                    help="convergence of the 16-label workload at SIZE^2 per storage type")
+    ap.add_argument("--study-iters", type=int, default=6000)
     args = ap.parse_args()
+    if args.precision_study:
+        precision_study(args.precision_study, args.study_iters)
+        return
     if args.kernel_case:
         run_kernel_case(args.kernel_case, args.iters, args.time, args.variant)
         return
@@ -386,6 +486,8 @@ def main():
     fused_ms = ttg["rpADMMII_fused"]["ms"]
     plain_ms = ttg["rpADMMII_plain"]["ms"]
 
+    potts = potts_workloads(cmf, synth, flush) if rank == 0 and not args.skip_potts else {}
+
     if rank == 0:
         rate, dt = cpu_oracle_rate(inst, 150)
         line = {
@@ -411,6 +513,7 @@ def main():
                                        f"FP64 C oracle, one thread ({dt:.1f} s)"},
             "e2e": {"value": e2e_value, "unit": "px*label*it/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
+            "potts_workloads": potts,
             "gpu_launches": launches,
             "clocks": clocks,
         }

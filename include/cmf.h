@@ -72,7 +72,11 @@ typedef enum {
     CMF_PADMM = 0,      /* pADMMI: rpADMMI with r = 1                        */
     CMF_RPADMM_FG = 1,  /* rpADMMI, relaxation r on u (Fortin-Glowinski)     */
     CMF_RPADMM_EB = 2,  /* rpADMMII, relaxation rho (Eckstein-Bertsekas)     */
-    CMF_RPDRQ = 3       /* relaxed preconditioned Douglas-Rachford           */
+    CMF_RPDRQ = 3,      /* relaxed preconditioned Douglas-Rachford           */
+    CMF_TY = 4          /* pADMM-TY: the classical multi-block ADMM the paper
+                           compares against (Eq. ADMM:Tai_yuan / Eq.
+                           mADMM:Tai_yuan), sequential p-steps, no relaxation,
+                           no convergence guarantee                           */
 } cmf_algo;
 
 typedef enum { CMF_F32 = 0, CMF_F16 = 1, CMF_BF16 = 2 } cmf_dtype;
@@ -230,6 +234,70 @@ cmf_status cmf_solve_potts(const float *d_C, int L, const float *d_alpha, float 
                            int W, int pitch, const cmf_params *p, float *d_u, void *d_qx,
                            void *d_qy, void *d_p, void *d_ps, double *h_hist, int hist_cap,
                            int *h_iters, void *d_ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuning (no counterpart in the paper: a launch-configuration search).  */
+/* Solves the problem from a cold start once per candidate configuration --  */
+/* the kernel variant (1, 8, 16, 32) of the fused ADMM algorithms, or the    */
+/* sRBGS sweep count (1, 2, 3) of fused rPDRQ -- with everything else taken  */
+/* from *p, and writes the candidate with the shortest time to p->tol_gap    */
+/* (CUDA events on `stream`, best of two runs after a warm-up) to *best and  */
+/* its time in milliseconds to *h_best_ms (host, may be NULL).  The state    */
+/* buffers are overwritten (they hold the last trial's solution).  Returns  */
+/* CMF_NOT_CONVERGED when no candidate reached the gap within max_iter.     */
+/* ------------------------------------------------------------------------ */
+cmf_status cmf_autotune_binary(const float *d_Cs, const float *d_Ct, const float *d_alpha,
+                               float alpha0, int H, int W, int pitch, const cmf_params *p,
+                               float *d_u, void *d_qx, void *d_qy, void *d_ps, void *d_pt,
+                               void *d_ws, size_t ws_bytes, cmf_params *best,
+                               double *h_best_ms, void *stream);
+
+cmf_status cmf_autotune_potts(const float *d_C, int L, const float *d_alpha, float alpha0,
+                              int H, int W, int pitch, const cmf_params *p, float *d_u,
+                              void *d_qx, void *d_qy, void *d_p, void *d_ps, void *d_ws,
+                              size_t ws_bytes, cmf_params *best, double *h_best_ms,
+                              void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batches: many binary and Potts instances of uneven size and label count  */
+/* solved together in one device-driven loop (a CUDA graph whose            */
+/* conditional WHILE node repeats {check_every iterations of every active   */
+/* instance, certificates, per-instance stop test}).  Converged instances   */
+/* stop iterating (per-instance convergence masks); the loop ends when all  */
+/* have converged or reached max_iter.                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    /* problem (inputs) */
+    int model;              /* 0 = binary (L must be 2), 1 = Potts              */
+    int L, H, W, pitch;     /* labels, grid, row stride in elements             */
+    const float *d_cost;    /* binary: C_s then C_t (2 planes); Potts: L planes */
+    const float *d_alpha;   /* alpha plane or NULL (then alpha0)                */
+    float alpha0;
+    /* state (in/out, caller-owned device buffers, as in the single solvers)   */
+    float *d_u;             /* binary: 1 plane; Potts: L planes (float32)       */
+    void *d_qx, *d_qy;      /* 1 / L planes each, storage dtype                 */
+    void *d_p;              /* binary: p_t (1 plane); Potts: p_i (L planes)     */
+    void *d_ps;             /* p_s (1 plane)                                    */
+    /* results (outputs) */
+    int iters;              /* iterations run for this instance                 */
+    int status;             /* CMF_OK or CMF_NOT_CONVERGED                      */
+    double energy, dual, gap, res;  /* last certificates (as cmf_eval_*)       */
+} cmf_instance;
+
+/* Workspace bytes for a batch (0 when an instance or the parameters are
+ * invalid).  The batch runs the fused kernels (p->impl = CMF_FUSED), needs an
+ * even p->check_every that divides p->max_iter, and for rPDRQ one sweep. */
+size_t cmf_batch_workspace_bytes(const cmf_instance *inst, int n, const cmf_params *p);
+
+/* Solve all n instances (host array; device pointers inside) with the same
+ * algorithm and parameters (rPDRQ: the same sigma and tau for every
+ * instance; Potts instances use a2 = max(p->a2, 2L), the bound of Thm 2);
+ * cold start unless p->warm_start.  Fills the
+ * result fields of every instance.  Returns CMF_OK when every instance
+ * reached p->tol_gap, CMF_NOT_CONVERGED when some stopped at max_iter. */
+cmf_status cmf_solve_batch(cmf_instance *inst, int n, const cmf_params *p, void *d_ws,
+                           size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,8 @@ this module compiles it with gcc and wraps it with ctypes.
 Algorithm codes: 0 pADMMI (Fortin-Glowinski with r = 1), 1 rpADMMI
 (Fortin-Glowinski, Eq. rpADMMI), 2 rpADMMII (Eckstein-Bertsekas, Eq. rpADMMII),
 3 rPDRQ (preconditioned Douglas-Rachford, Eq. iteration:quadratic:seg /
-Eq. pdrq:4labels).
+Eq. pdrq:4labels), 4 pADMM-TY (the classical multi-block ADMM, Eq. ADMM:Tai_yuan /
+Eq. mADMM:Tai_yuan).
 """
 from __future__ import annotations
 
@@ -18,8 +19,9 @@ import subprocess
 
 import numpy as np
 
-PADMM, RPADMM_FG, RPADMM_EB, RPDRQ = 0, 1, 2, 3
-ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ"}
+PADMM, RPADMM_FG, RPADMM_EB, RPDRQ, TY = 0, 1, 2, 3, 4
+ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ",
+              TY: "pADMM-TY"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cmf_oracle.c")

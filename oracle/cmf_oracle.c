@@ -38,7 +38,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_PADMM = 0, ORC_RPADMM_FG = 1, ORC_RPADMM_EB = 2, ORC_RPDRQ = 3 };
+enum { ORC_PADMM = 0, ORC_RPADMM_FG = 1, ORC_RPADMM_EB = 2, ORC_RPDRQ = 3, ORC_TY = 4 };
 
 /* Parameters of one run.  Mirrored by a ctypes.Structure in __init__.py. */
 typedef struct {
@@ -274,12 +274,42 @@ static void binary_dr_step(int H, int W, const double *Cs, const double *Ct, con
     }
 }
 
+/* One pADMM-TY iteration (Eq. ADMM:Tai_yuan): the q-step of the other ADMM
+ * variants, then the sequential (Gauss-Seidel) maximisations of the
+ * augmented Lagrangian over p_s (with p_t^k) and over p_t (with p_s^{k+1}),
+ * then the multiplier step u^{k+1} = u^k - c (p_t - p_s + div q)^{k+1}. */
+static void binary_ty_step(int H, int W, const double *Cs, const double *Ct, const double *alpha,
+                           const orc_params *P, double *u, double *qx, double *qy, double *ps,
+                           double *pt, double *w1, double *w2, double *w3, double *w4,
+                           double *w5) {
+    const size_t n = (size_t)H * W;
+    const double c = P->c, a = P->a;
+    double *dq = w1, *sx = w2, *sy = w3, *gx = w4, *gy = w5;
+    orc_div(H, W, qx, qy, dq);
+    orc_div_adjoint(H, W, dq, sx, sy);
+    double *h = dq;
+    for (size_t k = 0; k < n; ++k) h[k] = pt[k] - ps[k] - u[k] / c;
+    orc_grad(H, W, h, gx, gy);
+    for (size_t k = 0; k < n; ++k) {
+        qx[k] = qx[k] - sx[k] / a + gx[k] / a;
+        qy[k] = qy[k] - sy[k] / a + gy[k] / a;
+    }
+    orc_project_alpha(n, qx, qy, alpha, P->aniso);
+    double *d = w1;
+    orc_div(H, W, qx, qy, d);
+    for (size_t k = 0; k < n; ++k) {
+        ps[k] = dmin(pt[k] + d[k] - u[k] / c + 1.0 / c, Cs[k]);
+        pt[k] = dmin(ps[k] - d[k] + u[k] / c, Ct[k]);
+        u[k] = u[k] - c * (pt[k] - ps[k] + d[k]);
+    }
+}
+
 /* Run n_iter iterations from the given state (cold start first if
  * `cold` != 0).  Returns 0, or -1 on a bad algorithm code / allocation. */
 int orc_binary_run(int H, int W, const double *Cs, const double *Ct, const double *alpha,
                    const orc_params *P, int n_iter, int cold, double *u, double *qx, double *qy,
                    double *ps, double *pt) {
-    if (P->algo < ORC_PADMM || P->algo > ORC_RPDRQ) return -1;
+    if (P->algo < ORC_PADMM || P->algo > ORC_TY) return -1;
     const size_t n = (size_t)H * W;
     if (cold) orc_binary_init(H, W, Cs, Ct, P->algo == ORC_RPDRQ, P->tau, u, qx, qy, ps, pt);
     double *w1 = dalloc(n), *w2 = dalloc(n), *w3 = dalloc(n), *w4 = dalloc(n), *w5 = dalloc(n);
@@ -287,6 +317,8 @@ int orc_binary_run(int H, int W, const double *Cs, const double *Ct, const doubl
     for (int it = 0; it < n_iter; ++it) {
         if (P->algo == ORC_RPDRQ)
             binary_dr_step(H, W, Cs, Ct, alpha, P, u, qx, qy, ps, pt, w1, w2, w3, w4, w5);
+        else if (P->algo == ORC_TY)
+            binary_ty_step(H, W, Cs, Ct, alpha, P, u, qx, qy, ps, pt, w1, w2, w3, w4, w5);
         else
             binary_admm_step(H, W, Cs, Ct, alpha, P, u, qx, qy, ps, pt, w1, w2, w3, w4, w5);
     }
@@ -434,6 +466,48 @@ static void potts_admm_step(int H, int W, int L, const double *C, const double *
     memcpy(ps, psn, n * sizeof(double));
 }
 
+/* One Potts pADMM-TY iteration (Eq. mADMM:Tai_yuan): the q_i-steps, then
+ * the maximisations of the augmented Lagrangian over each p_i (with p_s^k)
+ * and then over p_s (with the new p_i -- the sequential order the text after
+ * the equation describes; the equation prints p_i^k), then the multiplier
+ * steps u_i^{k+1} = u_i^k - c (p_i - p_s + div q_i)^{k+1}. */
+static void potts_ty_step(int H, int W, int L, const double *C, const double *alpha,
+                          const orc_params *P, double *u, double *qx, double *qy, double *p,
+                          double *ps, double *d, double *w1, double *w2, double *w3, double *w4,
+                          double *w5) {
+    const size_t n = (size_t)H * W;
+    const double c = P->c, a = P->a;
+    for (int i = 0; i < L; ++i) {
+        double *Qx = qx + i * n, *Qy = qy + i * n;
+        const double *Pi = p + i * n, *Ui = u + i * n;
+        orc_div(H, W, Qx, Qy, w1);
+        orc_div_adjoint(H, W, w1, w2, w3);
+        for (size_t k = 0; k < n; ++k) w1[k] = Pi[k] - ps[k] - Ui[k] / c;
+        orc_grad(H, W, w1, w4, w5);
+        for (size_t k = 0; k < n; ++k) {
+            Qx[k] = Qx[k] - w2[k] / a + w4[k] / a;
+            Qy[k] = Qy[k] - w3[k] / a + w5[k] / a;
+        }
+        orc_project_alpha(n, Qx, Qy, alpha, P->aniso);
+        orc_div(H, W, Qx, Qy, d + i * n);
+    }
+    for (int i = 0; i < L; ++i)
+        for (size_t k = 0; k < n; ++k) {
+            size_t ik = i * n + k;
+            p[ik] = dmin(ps[k] - d[ik] + u[ik] / c, C[ik]);
+        }
+    for (size_t k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < L; ++i) s += p[i * n + k] + d[i * n + k] - u[i * n + k] / c;
+        ps[k] = s / L + 1.0 / (L * c);
+    }
+    for (int i = 0; i < L; ++i)
+        for (size_t k = 0; k < n; ++k) {
+            size_t ik = i * n + k;
+            u[ik] = u[ik] - c * (p[ik] - ps[k] + d[ik]);
+        }
+}
+
 /* One Potts rPDRQ iteration (Eq. pdrq:4labels, general L).  State (u_i,
  * qbar_i, pbar_i, pbar_s). */
 static void potts_dr_step(int H, int W, int L, const double *C, const double *alpha,
@@ -490,7 +564,7 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
 
 int orc_potts_run(int H, int W, int L, const double *C, const double *alpha, const orc_params *P,
                   int n_iter, int cold, double *u, double *qx, double *qy, double *p, double *ps) {
-    if (P->algo < ORC_PADMM || P->algo > ORC_RPDRQ || L < 2 || L > 64) return -1;
+    if (P->algo < ORC_PADMM || P->algo > ORC_TY || L < 2 || L > 64) return -1;
     const size_t n = (size_t)H * W;
     if (cold) orc_potts_init(H, W, L, C, P->algo == ORC_RPDRQ, P->tau, u, qx, qy, p, ps);
     double *big = dalloc(n * L);
@@ -500,6 +574,8 @@ int orc_potts_run(int H, int W, int L, const double *C, const double *alpha, con
     for (int it = 0; it < n_iter; ++it) {
         if (P->algo == ORC_RPDRQ)
             potts_dr_step(H, W, L, C, alpha, P, u, qx, qy, p, ps, big, w1, w2, w3, w4, w6);
+        else if (P->algo == ORC_TY)
+            potts_ty_step(H, W, L, C, alpha, P, u, qx, qy, p, ps, big, w1, w2, w3, w4, w5);
         else
             potts_admm_step(H, W, L, C, alpha, P, u, qx, qy, p, ps, big, w1, w2, w3, w4, w5, w6);
     }

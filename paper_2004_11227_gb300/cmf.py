@@ -19,10 +19,11 @@ import torch
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED = range(6)
-PADMM, RPADMM_FG, RPADMM_EB, RPDRQ = range(4)
+PADMM, RPADMM_FG, RPADMM_EB, RPDRQ, TY = range(5)
 F32, F16, BF16 = range(3)
 FUSED, PLAIN = range(2)
-ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ"}
+ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ",
+              TY: "pADMM-TY"}
 _TORCH_DTYPE = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
 
 
@@ -40,6 +41,18 @@ class Params(ctypes.Structure):
         ("c", ctypes.c_double), ("a", ctypes.c_double), ("a1", ctypes.c_double),
         ("a2", ctypes.c_double), ("rho", ctypes.c_double), ("r", ctypes.c_double),
         ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("tol_gap", ctypes.c_double),
+    ]
+
+
+class Instance(ctypes.Structure):
+    """Mirror of cmf_instance (one problem of a batch)."""
+    _fields_ = [
+        ("model", ctypes.c_int), ("L", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+        ("pitch", ctypes.c_int), ("d_cost", ctypes.c_void_p), ("d_alpha", ctypes.c_void_p),
+        ("alpha0", ctypes.c_float), ("d_u", ctypes.c_void_p), ("d_qx", ctypes.c_void_p),
+        ("d_qy", ctypes.c_void_p), ("d_p", ctypes.c_void_p), ("d_ps", ctypes.c_void_p),
+        ("iters", ctypes.c_int), ("status", ctypes.c_int), ("energy", ctypes.c_double),
+        ("dual", ctypes.c_double), ("gap", ctypes.c_double), ("res", ctypes.c_double),
     ]
 
 
@@ -70,6 +83,14 @@ _SIGS = {
                        [ctypes.c_int] * 3 + [ctypes.c_void_p] * 7 +
                        [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                         ctypes.c_void_p],
+    "cmf_autotune_binary": [ctypes.c_void_p] * 3 + [ctypes.c_float] + [ctypes.c_int] * 3 +
+                           [ctypes.c_void_p] * 7 + [ctypes.c_size_t] + [ctypes.c_void_p] * 3,
+    "cmf_autotune_potts": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_float] +
+                          [ctypes.c_int] * 3 + [ctypes.c_void_p] * 7 + [ctypes.c_size_t] +
+                          [ctypes.c_void_p] * 3,
+    "cmf_batch_workspace_bytes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "cmf_solve_batch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_size_t, ctypes.c_void_p],
 }
 EXPORTED = tuple(_SIGS)
 
@@ -92,6 +113,7 @@ def lib():
             fn.restype = ctypes.c_int
         L.cmf_status_str.restype = ctypes.c_char_p
         L.cmf_workspace_bytes.restype = ctypes.c_size_t
+        L.cmf_batch_workspace_bytes.restype = ctypes.c_size_t
         _lib = L
     return _lib
 
@@ -314,3 +336,94 @@ def cmf_solve_potts(s: Potts, hist_cap: int = 4096, stream=None):
                 "cmf_solve_potts", allow=(OK, NOT_CONVERGED))
     n = int(np.count_nonzero(hist[:, 0]))
     return st, iters.value, hist[:n]
+
+
+def cmf_solve_batch(items, params: Params, stream=None):
+    """Solve a list of Binary / Potts containers as one batch.  Returns
+    (status, [per-instance result dicts]); the containers' state tensors hold
+    the solutions."""
+    n = len(items)
+    insts = (Instance * n)()
+    keep = []
+    for i, it in enumerate(items):
+        d = insts[i]
+        if isinstance(it, Binary):
+            cost = torch.stack([it.Cs, it.Ct]).contiguous()
+            keep.append(cost)
+            d.model, d.L = 0, 2
+            d.d_p, d.d_ps = _ptr(it.pt), _ptr(it.ps)
+        else:
+            cost = it.C
+            d.model, d.L = 1, it.L
+            d.d_p, d.d_ps = _ptr(it.p), _ptr(it.ps)
+        d.H, d.W, d.pitch = it.H, it.W, it.pitch
+        d.d_cost = _ptr(cost)
+        d.d_alpha = _ptr(it.alpha)
+        d.alpha0 = it.alpha0
+        d.d_u, d.d_qx, d.d_qy = _ptr(it.u), _ptr(it.qx), _ptr(it.qy)
+    nb = int(lib().cmf_batch_workspace_bytes(insts, n, ctypes.byref(params)))
+    if nb == 0:
+        raise CmfError("cmf_batch_workspace_bytes: invalid batch or parameters")
+    dev = items[0].u.device
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    st = _check(lib().cmf_solve_batch(insts, n, ctypes.byref(params), _ptr(ws), nb,
+                                      _stream(stream)),
+                "cmf_solve_batch", allow=(OK, NOT_CONVERGED))
+    res = [dict(iters=d.iters, status=d.status, energy=d.energy, dual=d.dual, gap=d.gap,
+                res=d.res) for d in insts]
+    del keep
+    return st, res
+
+
+def cmf_autotune_binary(b: Binary, stream=None):
+    """Launch-configuration search (see cmf.h); returns (best Params, ms)."""
+    best = Params()
+    ms = ctypes.c_double(0.0)
+    _check(lib().cmf_autotune_binary(*b._common(), *b._state_ptrs(), _ptr(b.ws), b.ws.numel(),
+                                     ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
+           "cmf_autotune_binary")
+    return best, ms.value
+
+
+def cmf_autotune_potts(s: Potts, stream=None):
+    best = Params()
+    ms = ctypes.c_double(0.0)
+    _check(lib().cmf_autotune_potts(*s._common(), *s._state_ptrs(), _ptr(s.ws), s.ws.numel(),
+                                    ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
+           "cmf_autotune_potts")
+    return best, ms.value
+
+
+def tuned_params(problem, cache_path: str | None = None) -> Params:
+    """Autotuned parameters for a Binary / Potts container, cached in a JSON
+    file keyed by (model, H, W, L, storage, algo, impl, SM count, device)."""
+    import json
+
+    p = problem.params
+    props = torch.cuda.get_device_properties(problem.u.device)
+    key = "|".join(str(v) for v in (
+        "binary" if isinstance(problem, Binary) else "potts", problem.H, problem.W,
+        getattr(problem, "L", 2), p.storage, p.algo, p.impl, props.multi_processor_count,
+        props.name))
+    path = cache_path or os.environ.get(
+        "CMF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cmf_tune.json"))
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    q = Params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(Params))
+    if key in cache:
+        q.variant, q.sweeps = cache[key]["variant"], cache[key]["sweeps"]
+        return q
+    if isinstance(problem, Binary):
+        best, ms = cmf_autotune_binary(problem)
+    else:
+        best, ms = cmf_autotune_potts(problem)
+    cache[key] = {"variant": best.variant, "sweeps": best.sweeps, "ms_to_gap": ms}
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(cache, f, indent=1)
+    q.variant, q.sweeps = best.variant, best.sweeps
+    return q

@@ -66,7 +66,7 @@ bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
 cmf_status check_params(const cmf_params* p, int L) {
     if (!p) return CMF_EINVAL;
-    if (p->algo < CMF_PADMM || p->algo > CMF_RPDRQ) return CMF_EINVAL;
+    if (p->algo < CMF_PADMM || p->algo > CMF_TY) return CMF_EINVAL;
     if (p->storage < CMF_F32 || p->storage > CMF_BF16) return CMF_EINVAL;
     if (p->impl != CMF_FUSED && p->impl != CMF_PLAIN) return CMF_EINVAL;
     if (p->sweeps < 1 || (p->impl == CMF_FUSED && p->sweeps > 4) || p->sweeps > 64)
@@ -176,7 +176,10 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
     const int ty = p->variant >= 8 ? p->variant : 16;
-    if (!call.cfg.dr && !call.cfg.plain && p->variant != 1 &&
+    // automatic choice: the persistent TMA kernel wins on grids that fit the
+    // L2 cache, the shared-memory tile kernel on larger ones (measured)
+    const bool auto_tma = p->variant == 0 && (size_t)H * (size_t)W <= ((size_t)1 << 21);
+    if (!call.cfg.dr && !call.cfg.plain && (p->variant >= 8 || auto_tma) &&
         binary_tma_eligible(call.P.g, p->storage, call.user) &&
         binary_tma_eligible(call.P.g, p->storage, call.ws)) {
         call.tma = binary_tma_maps(call.P.g, p->storage, call.user, ty, call.maps[0]) ==
@@ -523,7 +526,7 @@ cmf_status solve_loop(const cmf_params* p, Run run, Eval eval, Copy copy_back, d
 extern "C" {
 
 cmf_status cmf_default_params(int algo, int L, cmf_params* p) {
-    if (!p || algo < CMF_PADMM || algo > CMF_RPDRQ || L < 2) return CMF_EINVAL;
+    if (!p || algo < CMF_PADMM || algo > CMF_TY || L < 2) return CMF_EINVAL;
     memset(p, 0, sizeof(*p));
     p->algo = algo;
     p->storage = CMF_F32;
@@ -728,3 +731,99 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Autotuner: time to the gap for each candidate launch configuration
+// ===========================================================================
+namespace {
+
+// Candidate list for a parameter set: kernel variants of the fused ADMM path
+// and sRBGS sweep counts of the fused rPDRQ path.
+std::vector<cmf_params> tune_candidates(const cmf_params& p) {
+    std::vector<cmf_params> out;
+    const bool fused = p.impl == CMF_FUSED;
+    const bool dr = p.algo == CMF_RPDRQ;
+    std::vector<int> variants = {p.variant};
+    std::vector<int> sweeps = {p.sweeps};
+    if (fused && !dr) variants = {1, 8, 16, 32};
+    if (fused && dr) sweeps = {1, 2, 3};
+    for (int v : variants)
+        for (int s : sweeps) {
+            cmf_params q = p;
+            q.variant = v;
+            q.sweeps = s;
+            q.warm_start = 0;
+            out.push_back(q);
+        }
+    return out;
+}
+
+template <typename Solve>
+cmf_status tune_loop(const cmf_params* p, Solve solve, cmf_params* best, double* h_best_ms,
+                     cudaStream_t st) {
+    if (!p || !best) return CMF_EINVAL;
+    cudaEvent_t e0, e1;
+    CMF_CUDA_TRY(cudaEventCreate(&e0));
+    CMF_CUDA_TRY(cudaEventCreate(&e1));
+    double best_ms = 1e300;
+    bool found = false;
+    cmf_status last = CMF_EINVAL;
+    for (const cmf_params& q : tune_candidates(*p)) {
+        cmf_status s = solve(q);  // warm-up (and validity check)
+        last = s;
+        if (s != CMF_OK) continue;
+        double ms_min = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            s = solve(q);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (s == CMF_OK && ms < ms_min) ms_min = ms;
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            *best = q;
+            found = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!found) return last == CMF_OK ? CMF_NOT_CONVERGED : last;
+    if (h_best_ms) *h_best_ms = best_ms;
+    return CMF_OK;
+}
+
+}  // namespace
+
+extern "C" cmf_status cmf_autotune_binary(const float* d_Cs, const float* d_Ct,
+                                          const float* d_alpha, float alpha0, int H, int W,
+                                          int pitch, const cmf_params* p, float* d_u,
+                                          void* d_qx, void* d_qy, void* d_ps, void* d_pt,
+                                          void* d_ws, size_t ws_bytes, cmf_params* best,
+                                          double* h_best_ms, void* stream) {
+    return tune_loop(
+        p,
+        [&](const cmf_params& q) {
+            return cmf_solve_binary(d_Cs, d_Ct, d_alpha, alpha0, H, W, pitch, &q, d_u, d_qx,
+                                    d_qy, d_ps, d_pt, nullptr, 0, nullptr, d_ws, ws_bytes,
+                                    stream);
+        },
+        best, h_best_ms, (cudaStream_t)stream);
+}
+
+extern "C" cmf_status cmf_autotune_potts(const float* d_C, int L, const float* d_alpha,
+                                         float alpha0, int H, int W, int pitch,
+                                         const cmf_params* p, float* d_u, void* d_qx,
+                                         void* d_qy, void* d_p, void* d_ps, void* d_ws,
+                                         size_t ws_bytes, cmf_params* best, double* h_best_ms,
+                                         void* stream) {
+    return tune_loop(
+        p,
+        [&](const cmf_params& q) {
+            return cmf_solve_potts(d_C, L, d_alpha, alpha0, H, W, pitch, &q, d_u, d_qx, d_qy,
+                                   d_p, d_ps, nullptr, 0, nullptr, d_ws, ws_bytes, stream);
+        },
+        best, h_best_ms, (cudaStream_t)stream);
+}

@@ -50,15 +50,6 @@ __global__ void k_binary_init(BinProblem P, BinState<S> st, float tau) {
     Store<S>::st(st.pt + k, pt);
 }
 
-// Pointwise p / u step of rpADMMII / rpADMMI (Eq. rpADMMII, Eq. rpADMMI):
-// p_t, p_s both read p^k (Jacobi), then the multiplier update.
-__device__ __forceinline__ void binary_pu(const AdmmCoef& K, float d, float ps0, float pt0,
-                                          float u0, float cs, float ct, float& ps1, float& pt1) {
-    pt1 = fminf(pt0 - K.rho_a1 * (pt0 - ps0) + K.inv_a1 * (-K.rho_p * d + u0 * K.inv_c), ct);
-    ps1 = fminf(ps0 - K.rho_a1 * (ps0 - pt0) + K.inv_a1 * (K.rho_p * d - u0 * K.inv_c + K.inv_c),
-                cs);
-}
-
 // ---------------------------------------------------------------------------
 // Fused ADMM iteration.  With g = div q^k + p_t^k - p_s^k - u^k / c the
 // q-step of Eq. rpADMMII reads q^{k+1} = P_alpha(q^k + (1/a) grad g), since
@@ -68,8 +59,7 @@ __device__ __forceinline__ void binary_pu(const AdmmCoef& K, float d, float ps0,
 //   phase 3: d = div q^{k+1}, p^{k+1}, u^{k+1} on the tile.
 // ---------------------------------------------------------------------------
 template <typename S, bool ANISO, int ROWS>
-__global__ void __launch_bounds__(256)
-    k_binary_admm_fused(BinProblem P, BinState<S> s0, BinState<S> s1, AdmmCoef K) {
+__device__ __forceinline__ void binary_admm_tile(BinProblem P, BinState<S> s0, BinState<S> s1, AdmmCoef K, int bx_, int by_) {
     constexpr int TX = 32, TY = 8 * ROWS;
     constexpr int GX = TX + 2, GY = TY + 2;
     constexpr int QX = TX + 1, QY = TY + 1;
@@ -78,7 +68,7 @@ __global__ void __launch_bounds__(256)
     __shared__ float qy_s[QY][QX];
     using St = Store<S>;
     const Grid G = P.g;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx_ * TX, y0 = by_ * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
 
     for (int i = tid; i < GX * GY; i += 256) {
@@ -133,16 +123,19 @@ __global__ void __launch_bounds__(256)
             if (r > 0) d -= qy_s[ly][lx + 1];
             const float ps0 = St::ld(s0.ps + k), pt0 = St::ld(s0.pt + k);
             const float u0 = __ldg(s0.u + k);
-            float ps1, pt1;
-            binary_pu(K, d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1);
-            ps1 = St::rt(ps1);
-            pt1 = St::rt(pt1);
-            const float u1 = u0 - K.cu * ((pt1 - ps1) - K.omr * (pt0 - ps0) + K.rho_p * d);
+            float ps1, pt1, u1;
+            binary_pu<S>(K, d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1, u1);
             St::st(s1.ps + k, ps1);
             St::st(s1.pt + k, pt1);
             s1.u[k] = u1;
         }
     }
+}
+
+template <typename S, bool ANISO, int ROWS>
+__global__ void __launch_bounds__(256)
+    k_binary_admm_fused(BinProblem P, BinState<S> s0, BinState<S> s1, AdmmCoef K) {
+    binary_admm_tile<S, ANISO, ROWS>(P, s0, s1, K, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -203,11 +196,8 @@ __global__ void k_binary_plain_pu(BinProblem P, BinState<S> s, const float* dbuf
     using St = Store<S>;
     const float d = dbuf[k];
     const float ps0 = St::ldw(s.ps + k), pt0 = St::ldw(s.pt + k), u0 = s.u[k];
-    float ps1, pt1;
-    binary_pu(K, d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1);
-    ps1 = St::rt(ps1);
-    pt1 = St::rt(pt1);
-    const float u1 = u0 - K.cu * ((pt1 - ps1) - K.omr * (pt0 - ps0) + K.rho_p * d);
+    float ps1, pt1, u1;
+    binary_pu<S>(K, d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1, u1);
     St::st(s.ps + k, ps1);
     St::st(s.pt + k, pt1);
     s.u[k] = u1;
@@ -242,8 +232,7 @@ __device__ __forceinline__ void binary_dr_flows(const DrCoef& D, float uc, float
 // its colour on that region grown by h-1-s, so u^k is staged on the region
 // grown by h and b on the region grown by h-1.
 template <typename S, bool ANISO, int ROWS, int SW>
-__global__ void __launch_bounds__(256)
-    k_binary_dr_fused(BinProblem P, BinState<S> s0, BinState<S> s1, DrCoef D) {
+__device__ __forceinline__ void binary_dr_tile(BinProblem P, BinState<S> s0, BinState<S> s1, DrCoef D, int bx_, int by_) {
     constexpr int TX = 32, TY = 8 * ROWS;
     constexpr int NH = 2 * SW + 1;
     constexpr int UX = TX + 1 + 2 * NH, UY = TY + 1 + 2 * NH;
@@ -252,7 +241,7 @@ __global__ void __launch_bounds__(256)
     __shared__ float b_s[BY][BX];
     using St = Store<S>;
     const Grid G = P.g;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx_ * TX, y0 = by_ * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int ux0 = x0 - NH, uy0 = y0 - NH;  // grid coords of u_s[0][0]
 
@@ -324,6 +313,12 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <typename S, bool ANISO, int ROWS, int SW>
+__global__ void __launch_bounds__(256)
+    k_binary_dr_fused(BinProblem P, BinState<S> s0, BinState<S> s1, DrCoef D) {
+    binary_dr_tile<S, ANISO, ROWS, SW>(P, s0, s1, D, blockIdx.x, blockIdx.y);
+}
+
 // Plain rPDRQ: b, then one kernel per red/black half-sweep (in place: a
 // half-sweep reads only the other colour), then the flow reflections.
 template <typename S>
@@ -386,8 +381,7 @@ __global__ void k_binary_plain_dr_flows(BinProblem P, BinState<S> s, DrCoef D) {
 // order by k_reduce_partials.  For rPDRQ y = ybar + tau K u.
 // ---------------------------------------------------------------------------
 template <typename S, bool ANISO, bool DR>
-__global__ void __launch_bounds__(256)
-    k_binary_eval(BinProblem P, BinState<S> s, float tau, double* partials) {
+__device__ __forceinline__ void binary_eval_tile(BinProblem P, BinState<S> s, float tau, double* out3, int bx_, int by_) {
     constexpr int TX = 32, TY = 8 * EVAL_ROWS;
     __shared__ float u_s[TY + 2][TX + 2];   // grid (y0-1+i, x0-1+j)
     __shared__ float fx_s[TY + 1][TX + 1];  // grid (y0-1+i, x0-1+j)
@@ -396,7 +390,7 @@ __global__ void __launch_bounds__(256)
     __shared__ float py_s[TY + 1][TX + 1];
     using St = Store<S>;
     const Grid G = P.g;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx_ * TX, y0 = by_ * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
 
     for (int i = tid; i < (TY + 2) * (TX + 2); i += 256) {
@@ -460,7 +454,13 @@ __global__ void __launch_bounds__(256)
                          (r < G.H - 1 ? py_s[ly + 1][lx + 1] : 0.f) - py_s[ly][lx + 1];
         accD += (double)fminf(cs, ct + dp);
     }
-    block_reduce3_store(accE, accD, accR, partials);
+    block_reduce3_store(accE, accD, accR, out3);
+}
+
+template <typename S, bool ANISO, bool DR>
+__global__ void __launch_bounds__(256)
+    k_binary_eval(BinProblem P, BinState<S> s, float tau, double* partials) {
+    binary_eval_tile<S, ANISO, DR>(P, s, tau, partials + 3 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -576,5 +576,97 @@ cudaError_t binary_eval(int storage, const BinProblem& P, const BinStateV& s, bo
 }
 
 int eval_blocks(int H, int W) { return ((W + 31) / 32) * ((H + 8 * EVAL_ROWS - 1) / (8 * EVAL_ROWS)); }
+
+}  // namespace cmf
+
+// ---------------------------------------------------------------------------
+// Batch kernels: one block per tile of any binary instance of a batch; the
+// block finds its instance through the tile table and returns at once when
+// that instance has converged.
+// ---------------------------------------------------------------------------
+namespace cmf {
+
+template <typename S, bool ANISO>
+__global__ void __launch_bounds__(256)
+    k_batch_binary_admm(const BatchDesc* desc, const int* tile_inst, int parity) {
+    const BatchDesc* D = desc + tile_inst[blockIdx.x];
+    if (!D->active) return;
+    const int lt = blockIdx.x - D->tile_base;
+    const BinStateV a = parity ? D->bw : D->bu, b = parity ? D->bu : D->bw;
+    binary_admm_tile<S, ANISO, 4>(D->bp, a.as<S>(), b.as<S>(), D->ak, lt % D->ntx, lt / D->ntx);
+}
+
+template <typename S, bool ANISO>
+__global__ void __launch_bounds__(256)
+    k_batch_binary_dr(const BatchDesc* desc, const int* tile_inst, int parity) {
+    const BatchDesc* D = desc + tile_inst[blockIdx.x];
+    if (!D->active) return;
+    const int lt = blockIdx.x - D->tile_base;
+    const BinStateV a = parity ? D->bw : D->bu, b = parity ? D->bu : D->bw;
+    binary_dr_tile<S, ANISO, 4, 1>(D->bp, a.as<S>(), b.as<S>(), D->dk, lt % D->ntx, lt / D->ntx);
+}
+
+template <typename S, bool ANISO, bool DR>
+__global__ void __launch_bounds__(256)
+    k_batch_binary_eval(const BatchDesc* desc, const int* tile_inst, float tau,
+                        double* partials) {
+    const BatchDesc* D = desc + tile_inst[blockIdx.x];
+    if (!D->active) return;
+    const int lt = blockIdx.x - D->ev_tab;
+    binary_eval_tile<S, ANISO, DR>(D->bp, D->bu.as<S>(), tau,
+                                   partials + 3 * (size_t)(D->ev_base + lt), lt % D->ntx,
+                                   lt / D->ntx);
+}
+
+template <typename S>
+static cudaError_t batch_binary_step_s(bool aniso, bool dr, const BatchDesc* desc,
+                                       const int* tile_inst, int ntiles, int parity,
+                                       cudaStream_t st) {
+    const dim3 bl(32, 8);
+    if (dr) {
+        if (aniso) k_batch_binary_dr<S, true><<<ntiles, bl, 0, st>>>(desc, tile_inst, parity);
+        else k_batch_binary_dr<S, false><<<ntiles, bl, 0, st>>>(desc, tile_inst, parity);
+    } else {
+        if (aniso) k_batch_binary_admm<S, true><<<ntiles, bl, 0, st>>>(desc, tile_inst, parity);
+        else k_batch_binary_admm<S, false><<<ntiles, bl, 0, st>>>(desc, tile_inst, parity);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_binary_step(int storage, bool aniso, bool dr, int sweeps,
+                              const BatchDesc* desc, const int* tile_inst, int ntiles,
+                              int parity, cudaStream_t st) {
+    if (dr && sweeps != 1) return cudaErrorInvalidValue;
+    switch (storage) {
+        case CMF_F32: return batch_binary_step_s<float>(aniso, dr, desc, tile_inst, ntiles, parity, st);
+        case CMF_F16: return batch_binary_step_s<__half>(aniso, dr, desc, tile_inst, ntiles, parity, st);
+        default: return batch_binary_step_s<__nv_bfloat16>(aniso, dr, desc, tile_inst, ntiles, parity, st);
+    }
+}
+
+template <typename S>
+static cudaError_t batch_binary_eval_s(bool aniso, bool dr, float tau, const BatchDesc* desc,
+                                       const int* tile_inst, int ntiles, double* partials,
+                                       cudaStream_t st) {
+    const dim3 bl(32, 8);
+    if (aniso) {
+        if (dr) k_batch_binary_eval<S, true, true><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+        else k_batch_binary_eval<S, true, false><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+    } else {
+        if (dr) k_batch_binary_eval<S, false, true><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+        else k_batch_binary_eval<S, false, false><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_binary_eval(int storage, bool aniso, bool dr, float tau,
+                              const BatchDesc* desc, const int* tile_inst, int ntiles,
+                              double* partials, cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return batch_binary_eval_s<float>(aniso, dr, tau, desc, tile_inst, ntiles, partials, st);
+        case CMF_F16: return batch_binary_eval_s<__half>(aniso, dr, tau, desc, tile_inst, ntiles, partials, st);
+        default: return batch_binary_eval_s<__nv_bfloat16>(aniso, dr, tau, desc, tile_inst, ntiles, partials, st);
+    }
+}
 
 }  // namespace cmf

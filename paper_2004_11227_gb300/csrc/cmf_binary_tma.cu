@@ -187,14 +187,9 @@ __global__ void __launch_bounds__(256, 4)
                 const int so = (ly + 2) * BXS + lx + XO;
                 const float ps0 = bload(sps + so), pt0 = bload(spt + so);
                 const float u0 = su[(ly + 2) * BXU + lx + XO];
-                float pt1 = fminf(pt0 - K.rho_a1 * (pt0 - ps0) + K.inv_a1 * (-K.rho_p * d + u0 * K.inv_c),
-                                  __ldg(P.Ct + kk));
-                float ps1 = fminf(ps0 - K.rho_a1 * (ps0 - pt0) +
-                                      K.inv_a1 * (K.rho_p * d - u0 * K.inv_c + K.inv_c),
-                                  __ldg(P.Cs + kk));
-                ps1 = St::rt(ps1);
-                pt1 = St::rt(pt1);
-                const float u1 = u0 - K.cu * ((pt1 - ps1) - K.omr * (pt0 - ps0) + K.rho_p * d);
+                float ps1, pt1, u1;
+                binary_pu<S>(K, d, ps0, pt0, u0, __ldg(P.Cs + kk), __ldg(P.Ct + kk), ps1, pt1,
+                             u1);
                 St::st(s1.ps + kk, ps1);
                 St::st(s1.pt + kk, pt1);
                 s1.u[kk] = u1;

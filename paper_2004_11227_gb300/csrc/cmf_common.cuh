@@ -99,9 +99,65 @@ struct AdmmCoef {
     float rho_a1;    // rho_p / a1
     float inv_a1;    // 1 / a1
     float inv_a2;    // 1 / a2 (Potts)
-    float cu;        // c (EB) or r c (FG)
-    float omr;       // 1 - rho (EB) or 0 (FG)
+    float cu;        // c (EB, TY) or r c (FG)
+    float omr;       // 1 - rho (EB) or 0 (FG, TY)
+    float inv_L;     // 1 / L (Potts pADMM-TY)
+    int ty;          // 1: pADMM-TY sequential p-steps (Eq. ADMM:Tai_yuan)
 };
+
+// Pointwise p / u step of the binary ADMM family, rounded to the storage
+// type.  rpADMMII / rpADMMI (Eq. rpADMMII, Eq. rpADMMI): p_t and p_s both
+// read p^k (Jacobi), then the multiplier update.  pADMM-TY (Eq.
+// ADMM:Tai_yuan): p_s from p_t^k, then p_t from p_s^{k+1}, then u.
+template <typename S>
+__device__ __forceinline__ void binary_pu(const AdmmCoef& K, float d, float ps0, float pt0,
+                                          float u0, float cs, float ct, float& ps1, float& pt1,
+                                          float& u1) {
+    using St = Store<S>;
+    if (K.ty) {
+        ps1 = St::rt(fminf(pt0 + d - u0 * K.inv_c + K.inv_c, cs));
+        pt1 = St::rt(fminf(ps1 - d + u0 * K.inv_c, ct));
+        u1 = u0 - K.cu * (pt1 - ps1 + d);
+    } else {
+        pt1 = St::rt(fminf(pt0 - K.rho_a1 * (pt0 - ps0) + K.inv_a1 * (-K.rho_p * d + u0 * K.inv_c),
+                           ct));
+        ps1 = St::rt(fminf(ps0 - K.rho_a1 * (ps0 - pt0) +
+                               K.inv_a1 * (K.rho_p * d - u0 * K.inv_c + K.inv_c),
+                           cs));
+        u1 = u0 - K.cu * ((pt1 - ps1) - K.omr * (pt0 - ps0) + K.rho_p * d);
+    }
+}
+
+// Potts, one label of one pixel: p_i^{k+1} (rounded), the label's share of
+// the p_s update (acc_a, acc_b) and v_i with u_i^{k+1} = v_i + cu p_s^{k+1}.
+// rpADMMII / rpADMMI: Eqs. after Thm 2 / Eq. multi:fg:4; pADMM-TY: Eq.
+// mADMM:Tai_yuan with p_s from the new p_i.
+template <typename S>
+__device__ __forceinline__ float potts_label_pu(const AdmmCoef& K, float d, float p0, float ps0,
+                                                float u0, float cl, float& acc_a, float& acc_b,
+                                                float& v) {
+    using St = Store<S>;
+    float p1;
+    if (K.ty) {
+        p1 = St::rt(fminf(ps0 - d + u0 * K.inv_c, cl));
+        acc_a += p1 + d - u0 * K.inv_c;
+        v = u0 - K.cu * (p1 + d);
+    } else {
+        p1 = St::rt(fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * d) * K.inv_a1, cl));
+        acc_a += K.rho_p * d;
+        acc_b += K.rho_p * (p0 - ps0) - u0 * K.inv_c;
+        v = u0 - K.cu * (p1 - K.omr * (p0 - ps0) + K.rho_p * d);
+    }
+    return p1;
+}
+
+// p_s^{k+1} from the accumulated label terms (rounded to the storage type).
+template <typename S>
+__device__ __forceinline__ float potts_ps_update(const AdmmCoef& K, float ps0, float acc_a,
+                                                 float acc_b) {
+    return K.ty ? Store<S>::rt((acc_a + K.inv_c) * K.inv_L)
+                : Store<S>::rt(ps0 + (acc_a + acc_b + K.inv_c) * K.inv_a2);
+}
 
 // ---- DR coefficients -----------------------------------------------------
 struct DrCoef {

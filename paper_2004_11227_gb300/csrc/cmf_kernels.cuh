@@ -36,7 +36,7 @@ struct BinStateV {
     void* ps;
     void* pt;
     template <typename S>
-    BinState<S> as() const {
+    __host__ __device__ BinState<S> as() const {
         return BinState<S>{u, (S*)qx, (S*)qy, (S*)ps, (S*)pt};
     }
 };
@@ -65,7 +65,7 @@ struct PottsStateV {
     void* p;
     void* ps;
     template <typename S>
-    PottsState<S> as() const {
+    __host__ __device__ PottsState<S> as() const {
         return PottsState<S>{u, (S*)qx, (S*)qy, (S*)p, (S*)ps};
     }
 };
@@ -80,7 +80,7 @@ struct StepConfig {
 };
 
 // Block-level FP64 reduction of three accumulators; thread 0 stores the
-// block's triple at partials[3 * linear block index].
+// block's triple at out3[0..2].
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -88,7 +88,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 __device__ __forceinline__ void block_reduce3_store(double a, double b, double c,
-                                                    double* partials) {
+                                                    double* out3) {
     __shared__ double red[3][32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nw = (blockDim.x * blockDim.y) >> 5;
@@ -109,10 +109,9 @@ __device__ __forceinline__ void block_reduce3_store(double a, double b, double c
         b = warp_sum(b);
         c = warp_sum(c);
         if (tid == 0) {
-            const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-            partials[3 * blk + 0] = a;
-            partials[3 * blk + 1] = b;
-            partials[3 * blk + 2] = c;
+            out3[0] = a;
+            out3[1] = b;
+            out3[2] = c;
         }
     }
 }
@@ -165,6 +164,40 @@ cudaError_t binary_tma_maps(const Grid& G, int storage, const BinStateV& s, int 
 cudaError_t binary_admm_tma_step(int storage, const BinProblem& P, const BinStateV& b,
                                  bool aniso, const AdmmCoef& K, const BinTmaMaps& src_maps,
                                  int* err, cudaStream_t st);
+
+// --- batched solve (cmf_batch.cu) ---
+// One instance of a batch, as the batch kernels see it (device memory).
+struct BatchDesc {
+    int model;       // 0 binary, 1 Potts
+    int active;      // 1 while the instance still iterates
+    int ntx;         // 32-wide tile columns
+    int tile_base;   // first entry of this instance in its model's iteration tile table
+    int ev_tab;      // first entry in its model's certificate tile table
+    int ev_base;     // first certificate partial of this instance
+    int ev_count;    // certificate tiles of this instance
+    int iters, status;
+    double energy, dual, gap, res;
+    BinProblem bp;
+    BinStateV bu, bw;      // caller's and workspace state (binary)
+    PottsProblem pp;
+    PottsStateV pu, pw;    // caller's and workspace state (Potts)
+    AdmmCoef ak;           // coefficients for this instance's L
+    DrCoef dk;
+};
+
+// parity 0: caller's buffers -> workspace; 1: workspace -> caller's buffers
+cudaError_t batch_binary_step(int storage, bool aniso, bool dr, int sweeps,
+                              const BatchDesc* desc, const int* tile_inst, int ntiles,
+                              int parity, cudaStream_t st);
+cudaError_t batch_potts_step(int storage, bool aniso, bool dr, int sweeps, int rows, int maxL,
+                             const BatchDesc* desc, const int* tile_inst, int ntiles,
+                             int parity, cudaStream_t st);
+cudaError_t batch_binary_eval(int storage, bool aniso, bool dr, float tau,
+                              const BatchDesc* desc, const int* tile_inst, int ntiles,
+                              double* partials, cudaStream_t st);
+cudaError_t batch_potts_eval(int storage, bool aniso, bool dr, float tau,
+                             const BatchDesc* desc, const int* tile_inst, int ntiles,
+                             double* partials, cudaStream_t st);
 
 // --- reductions ---
 // Sum n partial triples in a fixed order into out[0..2] (one block).

@@ -75,8 +75,7 @@ __global__ void k_potts_init(PottsProblem P, PottsState<S> s, float tau) {
 // so v_i is kept in shared memory until p_s^{k+1} is known.
 // ---------------------------------------------------------------------------
 template <typename S, bool ANISO, int ROWS>
-__global__ void __launch_bounds__(256)
-    k_potts_admm_fused(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K) {
+__device__ __forceinline__ void potts_admm_tile(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, int bx_, int by_) {
     constexpr int TX = 32, TY = 8 * ROWS;
     constexpr int GX = TX + 2, GY = TY + 2;
     constexpr int QX = TX + 1, QY = TY + 1;
@@ -88,7 +87,7 @@ __global__ void __launch_bounds__(256)
     using St = Store<S>;
     const Grid G = P.g;
     const size_t pl = G.plane;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx_ * TX, y0 = by_ * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
 
     for (int i = tid; i < GX * GY; i += 256) {
@@ -159,13 +158,9 @@ __global__ void __launch_bounds__(256)
                 const float ps0 = ps_s[ly + 1][lx + 1];
                 const float p0 = St::ld(s0.p + lo + k);
                 const float u0 = __ldg(s0.u + lo + k);
-                float p1 = fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * d) * K.inv_a1,
-                                 __ldg(P.C + lo + k));
-                p1 = St::rt(p1);
+                const float p1 = potts_label_pu<S>(K, d, p0, ps0, u0, __ldg(P.C + lo + k),
+                                                   accd[j], accp[j], v);
                 St::st(s1.p + lo + k, p1);
-                accd[j] += K.rho_p * d;
-                accp[j] += K.rho_p * (p0 - ps0) - u0 * K.inv_c;
-                v = u0 - K.cu * (p1 - K.omr * (p0 - ps0) + K.rho_p * d);
             }
             v_s[(l * TY + ly) * TX + lx] = v;
         }
@@ -179,7 +174,7 @@ __global__ void __launch_bounds__(256)
         ps1[j] = 0.f;
         if (r < G.H && c < G.W) {
             const float ps0 = ps_s[ly + 1][lx + 1];
-            ps1[j] = St::rt(ps0 + (accd[j] + accp[j] + K.inv_c) * K.inv_a2);
+            ps1[j] = potts_ps_update<S>(K, ps0, accd[j], accp[j]);
             St::st(s1.ps + G.idx(r, c), ps1[j]);
         }
     }
@@ -193,6 +188,12 @@ __global__ void __launch_bounds__(256)
                 s1.u[(size_t)l * pl + G.idx(r, c)] = v_s[(l * TY + ly) * TX + lx] + K.cu * ps1[j];
         }
     }
+}
+
+template <typename S, bool ANISO, int ROWS>
+__global__ void __launch_bounds__(256)
+    k_potts_admm_fused(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K) {
+    potts_admm_tile<S, ANISO, ROWS>(P, s0, s1, K, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -247,21 +248,19 @@ __global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* d
     using St = Store<S>;
     const size_t pl = G.plane;
     const float ps0 = St::ldw(s.ps + k);
-    float acc = 0.f;
+    // p_i^{k+1} and v_i per label (v_i parked in u_i), then p_s^{k+1}, then
+    // u_i^{k+1} = v_i + cu p_s^{k+1}
+    float acc_a = 0.f, acc_b = 0.f;
     for (int l = 0; l < P.L; ++l) {
         const size_t ki = l * pl + k;
-        acc += K.rho_p * d[ki] + K.rho_p * (St::ldw(s.p + ki) - ps0) - s.u[ki] * K.inv_c;
-    }
-    const float ps1 = St::rt(ps0 + (acc + K.inv_c) * K.inv_a2);
-    for (int l = 0; l < P.L; ++l) {
-        const size_t ki = l * pl + k;
-        const float p0 = St::ldw(s.p + ki), u0 = s.u[ki], dd = d[ki];
-        const float p1 = St::rt(
-            fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * dd) * K.inv_a1,
-                  __ldg(P.C + ki)));
+        float v;
+        const float p1 = potts_label_pu<S>(K, d[ki], St::ldw(s.p + ki), ps0, s.u[ki],
+                                           __ldg(P.C + ki), acc_a, acc_b, v);
         St::st(s.p + ki, p1);
-        s.u[ki] = u0 - K.cu * ((p1 - ps1) - K.omr * (p0 - ps0) + K.rho_p * dd);
+        s.u[ki] = v;
     }
+    const float ps1 = potts_ps_update<S>(K, ps0, acc_a, acc_b);
+    for (int l = 0; l < P.L; ++l) s.u[l * pl + k] += K.cu * ps1;
     St::st(s.ps + k, ps1);
 }
 
@@ -275,8 +274,7 @@ __global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* d
 //   pbar_s += rho ((2 p_s - pbar_s + tau) - p_s), p_s = pbar_s - tau sum u_i
 // ---------------------------------------------------------------------------
 template <typename S, bool ANISO, int ROWS, int SW>
-__global__ void __launch_bounds__(256)
-    k_potts_dr_fused(PottsProblem P, PottsState<S> s0, PottsState<S> s1, DrCoef D) {
+__device__ __forceinline__ void potts_dr_tile(PottsProblem P, PottsState<S> s0, PottsState<S> s1, DrCoef D, int bx_, int by_) {
     constexpr int TX = 32, TY = 8 * ROWS;
     constexpr int NH = 2 * SW + 1;
     constexpr int UX = TX + 1 + 2 * NH, UY = TY + 1 + 2 * NH;
@@ -288,7 +286,7 @@ __global__ void __launch_bounds__(256)
     using St = Store<S>;
     const Grid G = P.g;
     const size_t pl = G.plane;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx_ * TX, y0 = by_ * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int ux0 = x0 - NH, uy0 = y0 - NH;
     const float st_ = D.sigma * D.tau;
@@ -393,6 +391,12 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <typename S, bool ANISO, int ROWS, int SW>
+__global__ void __launch_bounds__(256)
+    k_potts_dr_fused(PottsProblem P, PottsState<S> s0, PottsState<S> s1, DrCoef D) {
+    potts_dr_tile<S, ANISO, ROWS, SW>(P, s0, s1, D, blockIdx.x, blockIdx.y);
+}
+
 // Plain rPDRQ pieces.
 template <typename S>
 __global__ void k_potts_plain_usum(PottsProblem P, PottsState<S> s, float* U) {
@@ -489,15 +493,14 @@ __device__ __forceinline__ void potts_flow_at(const PottsProblem& P, const Potts
 }
 
 template <typename S, bool ANISO, bool DR>
-__global__ void __launch_bounds__(256)
-    k_potts_eval(PottsProblem P, PottsState<S> s, float tau, double* partials) {
+__device__ __forceinline__ void potts_eval_tile(PottsProblem P, PottsState<S> s, float tau, double* out3, int bx_, int by_) {
     using St = Store<S>;
     const Grid G = P.g;
     const size_t pl = G.plane;
-    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int c = bx_ * 32 + threadIdx.x;
     double accE = 0.0, accD = 0.0, accR = 0.0;
     for (int j = 0; j < EVAL_ROWS; ++j) {
-        const int r = (blockIdx.y * 8 + threadIdx.y) * EVAL_ROWS + j;
+        const int r = (by_ * 8 + threadIdx.y) * EVAL_ROWS + j;
         if (r >= G.H || c >= G.W) continue;
         const size_t k = G.idx(r, c);
         const float al = P.alpha.at(k);
@@ -536,7 +539,13 @@ __global__ void __launch_bounds__(256)
         accD += (double)dmin;
         accR += (double)rr2;
     }
-    block_reduce3_store(accE, accD, accR, partials);
+    block_reduce3_store(accE, accD, accR, out3);
+}
+
+template <typename S, bool ANISO, bool DR>
+__global__ void __launch_bounds__(256)
+    k_potts_eval(PottsProblem P, PottsState<S> s, float tau, double* partials) {
+    potts_eval_tile<S, ANISO, DR>(P, s, tau, partials + 3 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -676,6 +685,119 @@ cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s,
         case CMF_F32: return potts_eval_s<float>(P, s, aniso, dr, tau, partials, st);
         case CMF_F16: return potts_eval_s<__half>(P, s, aniso, dr, tau, partials, st);
         default: return potts_eval_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+    }
+}
+
+}  // namespace cmf
+
+// ---------------------------------------------------------------------------
+// Batch kernels (see the binary ones): one block per tile of any Potts
+// instance of a batch; dynamic shared memory sized for the largest L.
+// ---------------------------------------------------------------------------
+namespace cmf {
+
+template <typename S, bool ANISO, int ROWS>
+__global__ void __launch_bounds__(256)
+    k_batch_potts_admm(const BatchDesc* desc, const int* tile_inst, int parity) {
+    const BatchDesc* D = desc + tile_inst[blockIdx.x];
+    if (!D->active) return;
+    const int lt = blockIdx.x - D->tile_base;
+    const PottsStateV a = parity ? D->pw : D->pu, b = parity ? D->pu : D->pw;
+    potts_admm_tile<S, ANISO, ROWS>(D->pp, a.as<S>(), b.as<S>(), D->ak, lt % D->ntx,
+                                    lt / D->ntx);
+}
+
+template <typename S, bool ANISO>
+__global__ void __launch_bounds__(256)
+    k_batch_potts_dr(const BatchDesc* desc, const int* tile_inst, int parity) {
+    const BatchDesc* D = desc + tile_inst[blockIdx.x];
+    if (!D->active) return;
+    const int lt = blockIdx.x - D->tile_base;
+    const PottsStateV a = parity ? D->pw : D->pu, b = parity ? D->pu : D->pw;
+    potts_dr_tile<S, ANISO, 4, 1>(D->pp, a.as<S>(), b.as<S>(), D->dk, lt % D->ntx, lt / D->ntx);
+}
+
+template <typename S, bool ANISO, bool DR>
+__global__ void __launch_bounds__(256)
+    k_batch_potts_eval(const BatchDesc* desc, const int* tile_inst, float tau, double* partials) {
+    const BatchDesc* D = desc + tile_inst[blockIdx.x];
+    if (!D->active) return;
+    const int lt = blockIdx.x - D->ev_tab;
+    potts_eval_tile<S, ANISO, DR>(D->pp, D->pu.as<S>(), tau,
+                                  partials + 3 * (size_t)(D->ev_base + lt), lt % D->ntx,
+                                  lt / D->ntx);
+}
+
+template <typename S, bool ANISO, int ROWS>
+static cudaError_t launch_batch_potts_admm(int maxL, const BatchDesc* desc, const int* tile_inst,
+                                           int ntiles, int parity, cudaStream_t st) {
+    const size_t dyn = (size_t)maxL * (8 * ROWS) * 32 * sizeof(float);
+    auto kern = k_batch_potts_admm<S, ANISO, ROWS>;
+    static size_t configured = 0;
+    if (dyn > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn);
+        if (e != cudaSuccess) return e;
+        configured = dyn;
+    }
+    kern<<<ntiles, dim3(32, 8), dyn, st>>>(desc, tile_inst, parity);
+    return cudaGetLastError();
+}
+
+template <typename S, bool ANISO>
+static cudaError_t batch_potts_step_t(bool dr, int rows, int maxL, const BatchDesc* desc,
+                                      const int* tile_inst, int ntiles, int parity,
+                                      cudaStream_t st) {
+    if (dr) {
+        k_batch_potts_dr<S, ANISO><<<ntiles, dim3(32, 8), 0, st>>>(desc, tile_inst, parity);
+        return cudaGetLastError();
+    }
+    if (rows == 4) return launch_batch_potts_admm<S, ANISO, 4>(maxL, desc, tile_inst, ntiles, parity, st);
+    if (rows == 2) return launch_batch_potts_admm<S, ANISO, 2>(maxL, desc, tile_inst, ntiles, parity, st);
+    return launch_batch_potts_admm<S, ANISO, 1>(maxL, desc, tile_inst, ntiles, parity, st);
+}
+
+template <typename S>
+static cudaError_t batch_potts_step_s(bool aniso, bool dr, int rows, int maxL,
+                                      const BatchDesc* desc, const int* tile_inst, int ntiles,
+                                      int parity, cudaStream_t st) {
+    return aniso ? batch_potts_step_t<S, true>(dr, rows, maxL, desc, tile_inst, ntiles, parity, st)
+                 : batch_potts_step_t<S, false>(dr, rows, maxL, desc, tile_inst, ntiles, parity, st);
+}
+
+cudaError_t batch_potts_step(int storage, bool aniso, bool dr, int sweeps, int rows, int maxL,
+                             const BatchDesc* desc, const int* tile_inst, int ntiles,
+                             int parity, cudaStream_t st) {
+    if (dr && (sweeps != 1 || rows != 4)) return cudaErrorInvalidValue;
+    switch (storage) {
+        case CMF_F32: return batch_potts_step_s<float>(aniso, dr, rows, maxL, desc, tile_inst, ntiles, parity, st);
+        case CMF_F16: return batch_potts_step_s<__half>(aniso, dr, rows, maxL, desc, tile_inst, ntiles, parity, st);
+        default: return batch_potts_step_s<__nv_bfloat16>(aniso, dr, rows, maxL, desc, tile_inst, ntiles, parity, st);
+    }
+}
+
+template <typename S>
+static cudaError_t batch_potts_eval_s(bool aniso, bool dr, float tau, const BatchDesc* desc,
+                                      const int* tile_inst, int ntiles, double* partials,
+                                      cudaStream_t st) {
+    const dim3 bl(32, 8);
+    if (aniso) {
+        if (dr) k_batch_potts_eval<S, true, true><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+        else k_batch_potts_eval<S, true, false><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+    } else {
+        if (dr) k_batch_potts_eval<S, false, true><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+        else k_batch_potts_eval<S, false, false><<<ntiles, bl, 0, st>>>(desc, tile_inst, tau, partials);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t batch_potts_eval(int storage, bool aniso, bool dr, float tau,
+                             const BatchDesc* desc, const int* tile_inst, int ntiles,
+                             double* partials, cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return batch_potts_eval_s<float>(aniso, dr, tau, desc, tile_inst, ntiles, partials, st);
+        case CMF_F16: return batch_potts_eval_s<__half>(aniso, dr, tau, desc, tile_inst, ntiles, partials, st);
+        default: return batch_potts_eval_s<__nv_bfloat16>(aniso, dr, tau, desc, tile_inst, ntiles, partials, st);
     }
 }
 

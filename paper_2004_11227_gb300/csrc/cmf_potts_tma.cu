@@ -223,12 +223,10 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
             const float u0 = su[(ly + 2) * BXU + lx + XO];
             const bool own = o_k[j] >= 0;
             const float cl = __ldg(C_l + (own ? o_k[j] : 0));
-            float p1 = fminf(p0 - (K.rho_p * (p0 - ps0) - u0 * K.inv_c + K.rho_p * d) * K.inv_a1, cl);
-            p1 = St::rt(p1);
+            float v;
+            const float p1 = potts_label_pu<S>(K, d, p0, ps0, u0, cl, accd[j], accp[j], v);
             if (own) St::st(p_out + o_k[j], p1);
-            accd[j] += K.rho_p * d;
-            accp[j] += K.rho_p * (p0 - ps0) - u0 * K.inv_c;
-            v_s[(l * TY + ly) * TX + lx] = u0 - K.cu * (p1 - K.omr * (p0 - ps0) + K.rho_p * d);
+            v_s[(l * TY + ly) * TX + lx] = v;
         }
         __syncthreads();
         if (tid == 0 && l + 2 < L) {
@@ -242,7 +240,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     for (int j = 0; j < ROWS; ++j) {
         const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
         const float ps0 = sload(ps_s + (ly + 2) * BXS + lx + XO);
-        ps1[j] = St::rt(ps0 + (accd[j] + accp[j] + K.inv_c) * K.inv_a2);
+        ps1[j] = potts_ps_update<S>(K, ps0, accd[j], accp[j]);
         if (o_k[j] >= 0) St::st(s1.ps + o_k[j], ps1[j]);
     }
 #pragma unroll 1

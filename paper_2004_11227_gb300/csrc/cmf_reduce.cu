@@ -45,6 +45,7 @@ cudaError_t reduce_partials(const double* partials, int n, double* out, cudaStre
 
 AdmmCoef make_admm_coef(const cmf_params& p, int L) {
     const bool eb = p.algo == CMF_RPADMM_EB;
+    const bool ty = p.algo == CMF_TY;
     const double rho_p = eb ? p.rho : 1.0;
     const double r = p.algo == CMF_RPADMM_FG ? p.r : 1.0;
     const double a2 = p.a2 > 0.0 ? p.a2 : 2.0 * L;
@@ -55,8 +56,10 @@ AdmmCoef make_admm_coef(const cmf_params& p, int L) {
     k.rho_a1 = (float)(rho_p / p.a1);
     k.inv_a1 = (float)(1.0 / p.a1);
     k.inv_a2 = (float)(1.0 / a2);
-    k.cu = (float)(eb ? p.c : r * p.c);
+    k.cu = (float)((eb || ty) ? p.c : r * p.c);
     k.omr = (float)(eb ? 1.0 - p.rho : 0.0);
+    k.inv_L = (float)(1.0 / L);
+    k.ty = ty ? 1 : 0;
     return k;
 }
 

@@ -17,7 +17,7 @@ from paper_2004_11227_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = [0, 1, 2, 3]
+ALGOS = [0, 1, 2, 3, 4]
 TOL_U = 1e-4
 
 
@@ -248,3 +248,18 @@ def test_tma_tiles_match_smem_tiles(cmf, storage, variant, shape):
         tol = 1e-6 if storage == 0 else 1e-2
         for k in a:
             assert np.abs(a[k] - b[k]).max() <= tol, k
+
+
+def test_autotune_picks_a_converging_configuration(cmf, tmp_path):
+    inst = synth.config2(200, 240)
+    for algo in (2, 3):
+        p = cmf.default_params(algo, 2, tol_gap=1e-4, max_iter=4000)
+        b = cmf.alloc_binary(inst, p)
+        best, ms = cmf.cmf_autotune_binary(b)
+        assert ms > 0 and best.algo == algo
+        assert best.variant in (1, 8, 16, 32) if algo != 3 else best.sweeps in (1, 2, 3)
+        q = cmf.tuned_params(b, cache_path=str(tmp_path / "tune.json"))
+        assert (tmp_path / "tune.json").exists()
+        b2 = cmf.alloc_binary(inst, q)
+        st, it, hist = cmf.cmf_solve_binary(b2)
+        assert st == cmf.OK

@@ -9,7 +9,7 @@ from paper_2004_11227_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = [0, 1, 2, 3]
+ALGOS = [0, 1, 2, 3, 4]
 TOL_U = 1e-4
 
 

@@ -11,7 +11,7 @@ import pytest
 
 from paper_2004_11227_gb300 import synth
 
-ALGOS = [0, 1, 2, 3]
+ALGOS = [0, 1, 2, 3, 4]
 
 
 def _converge(orc, inst, algo, tol, max_iter=40000, **kw):
@@ -269,3 +269,78 @@ def test_label_permutation_potts(orc, algo):
     for k in ("u", "qx", "qy", "p"):
         np.testing.assert_allclose(b[k], a[k][perm], atol=1e-12)
     np.testing.assert_allclose(b["ps"], a["ps"], atol=1e-12)
+
+
+def test_ty_p_steps_maximise_the_augmented_lagrangian(orc):
+    """pADMM-TY (Eq. ADMM:Tai_yuan, Remark 1): p_s^{k+1} maximises the
+    augmented Lagrangian of Eq. augfunc:twolabel over p_s <= C_s with p_t^k,
+    q^{k+1}, u^k fixed; then p_t^{k+1} maximises it over p_t <= C_t with
+    p_s^{k+1}; then u^{k+1} = u^k - c (p_t - p_s + div q)^{k+1}.  Checked per
+    pixel with a bounded scalar optimiser on the Lagrangian as written."""
+    from scipy.optimize import minimize_scalar
+
+    rng = np.random.default_rng(7)
+    inst = synth.random_binary(4, 5, seed=71, alpha=0.4)
+    Cs, Ct = inst.costs.astype(np.float64)
+    p = orc.default_params(orc.TY, 2)
+    c = p.c
+    st0 = {k: rng.normal(scale=0.3, size=(4, 5)) for k in ("u", "qx", "qy", "ps", "pt")}
+    st1 = orc.binary_run(Cs, Ct, inst.alpha, p, 1, st0)
+    d = orc.div(st1["qx"], st1["qy"])
+    for i in range(4):
+        for j in range(5):
+            u0, pt0 = st0["u"][i, j], st0["pt"][i, j]
+
+            def neg_ps(ps):  # -(p_s + u (p_t - p_s + div q) - c/2 (p_t - p_s + div q)^2)
+                r = pt0 - ps + d[i, j]
+                return -(ps + u0 * r - 0.5 * c * r * r)
+            ps_best = minimize_scalar(neg_ps, bounds=(-50, Cs[i, j]), method="bounded",
+                                      options={"xatol": 1e-12}).x
+            assert abs(st1["ps"][i, j] - ps_best) < 1e-6
+            ps1 = st1["ps"][i, j]
+
+            def neg_pt(pt):
+                r = pt - ps1 + d[i, j]
+                return -(u0 * r - 0.5 * c * r * r)
+            pt_best = minimize_scalar(neg_pt, bounds=(-50, Ct[i, j]), method="bounded",
+                                      options={"xatol": 1e-12}).x
+            assert abs(st1["pt"][i, j] - pt_best) < 1e-6
+            u1 = u0 - c * (st1["pt"][i, j] - ps1 + d[i, j])
+            assert abs(st1["u"][i, j] - u1) < 1e-12
+
+
+def test_ty_potts_p_steps_maximise_the_augmented_lagrangian(orc):
+    """Potts pADMM-TY (Eq. mADMM:Tai_yuan, with Eq. multi:aug:func): each p_i
+    maximises over p_i <= C_i with p_s^k, then p_s maximises over p_s with
+    the new p_i (the sequential order described after the equation)."""
+    from scipy.optimize import minimize_scalar
+
+    rng = np.random.default_rng(8)
+    L = 3
+    inst = synth.random_potts(3, 4, L, seed=72, alpha=0.3)
+    C = inst.costs.astype(np.float64)
+    p = orc.default_params(orc.TY, L)
+    c = p.c
+    st0 = {k: rng.normal(scale=0.3, size=(L, 3, 4)) for k in ("u", "qx", "qy", "p")}
+    st0["ps"] = rng.normal(scale=0.3, size=(3, 4))
+    st1 = orc.potts_run(C, inst.alpha, p, 1, st0)
+    d = np.stack([orc.div(st1["qx"][i], st1["qy"][i]) for i in range(L)])
+    for y in range(3):
+        for x in range(4):
+            ps0 = st0["ps"][y, x]
+            for i in range(L):
+                u0 = st0["u"][i, y, x]
+
+                def neg_pi(pi):
+                    r = d[i, y, x] + pi - ps0
+                    return -(u0 * r - 0.5 * c * r * r)
+                best = minimize_scalar(neg_pi, bounds=(-50, C[i, y, x]), method="bounded",
+                                       options={"xatol": 1e-12}).x
+                assert abs(st1["p"][i, y, x] - best) < 1e-6
+
+            def neg_ps(ps):
+                r = d[:, y, x] + st1["p"][:, y, x] - ps
+                return -(ps + np.dot(st0["u"][:, y, x], r) - 0.5 * c * np.dot(r, r))
+            best = minimize_scalar(neg_ps, bounds=(-50, 50), method="bounded",
+                                   options={"xatol": 1e-12}).x
+            assert abs(st1["ps"][y, x] - best) < 1e-6
