@@ -322,7 +322,8 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
     const bool want_tma = !call.cfg.dr && !call.cfg.plain && p->variant != 1;
-    const int ty = p->variant >= 8 ? p->variant : 16;
+    const int ty = p->variant >= 8 ? p->variant
+                                   : (want_tma ? potts_tma_auto_ty(p->storage, p->aniso, L) : 16);
     if (want_tma && potts_tma_fits(p->storage, L, ty) &&
         potts_tma_eligible(call.P.g, p->storage, call.user) &&
         potts_tma_eligible(call.P.g, p->storage, call.ws)) {

@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(256, 4)
         q_c[n] = qx_ - 1;
     }
 
+    // warps whose slots of the last round all lie past the cell count skip it
+    const bool g_tail = (tid & ~31) < GW * GH - 256 * (NG - 1);
+    const bool q_tail = (tid & ~31) < QW * QH - 256 * (NQ - 1);
 #pragma unroll 1
     for (int t = t0, k = 0; t < ntiles; t += dt, ++k) {
         const int s = k & 1;
@@ -139,6 +142,7 @@ __global__ void __launch_bounds__(256, 4)
         // g = div q + p_t - p_s - u / c on rows y0-1..y0+TY, cols x0-1..x0+TX
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
+            if (n == NG - 1 && !g_tail) break;
             const int o = g_off[n];
             const int r = y0 + g_r[n], c = x0 + g_c[n];
             float dv = c < G.W - 1 ? bload(sqx + o) : 0.f;
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(256, 4)
         // q^{k+1} = P_alpha(q + grad g / a) on rows y0-1.., cols x0-1..
 #pragma unroll
         for (int n = 0; n < NQ; ++n) {
+            if (n == NQ - 1 && !q_tail) break;
             const int o = q_off[n], go = q_goff[n];
             const int r = y0 + q_r[n], c = x0 + q_c[n];
             const bool in = q_cell[n] && r >= 0 && r < G.H && c >= 0 && c < G.W;

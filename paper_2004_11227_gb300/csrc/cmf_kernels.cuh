@@ -145,6 +145,9 @@ struct PottsTmaMaps {
 };
 bool potts_tma_eligible(const Grid& G, int storage, const PottsStateV& s);
 bool potts_tma_fits(int storage, int L, int ty);  // shared memory within the block limit
+// tile height (8 or 16) with the most resident warps per SM for L labels;
+// ties go to 16 (less halo per output row)
+int potts_tma_auto_ty(int storage, bool aniso, int L);
 cudaError_t potts_tma_maps(const Grid& G, int L, int storage, const PottsStateV& s, int ty,
                            PottsTmaMaps& m);
 // One iteration reading the state described by src_maps, writing b; a

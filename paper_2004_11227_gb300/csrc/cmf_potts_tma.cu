@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) accd[j] = accp[j] = 0.f;
 
+    // warps whose slots of the last round all lie past the cell count skip it
+    const bool g_tail = (tid & ~31) < GW * GH - 256 * (NG - 1);
+    const bool q_tail = (tid & ~31) < QW * QH - 256 * (NQ - 1);
 #pragma unroll 1
     for (int l = 0; l < L; ++l) {
         const int s = l & 1;
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
         // g_l = div q_l + p_l - p_s - u_l / c (zero-filled outside the grid)
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
+            if (n == NG - 1 && !g_tail) break;
             const int o = g_off[n];
             float dv = g_mx[n] * sload(sqx + o);
             dv -= sload(sqx + o - 1);
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
         // q_l^{k+1} = P_alpha(q_l + grad g_l / a); 0 outside the grid
 #pragma unroll
         for (int n = 0; n < NQ; ++n) {
+            if (n == NQ - 1 && !q_tail) break;
             const int o = q_off[n], go = q_goff[n];
             const float gc = g_s[go];
             float tx = sload(sqx + o) + (g_s[go + 1] - gc) * q_mx[n];
@@ -302,19 +307,55 @@ cudaError_t potts_tma_maps(const Grid& G, int L, int storage, const PottsStateV&
     return cudaSuccess;
 }
 
+// Raise the kernel's dynamic shared-memory limit to what L labels need.
+template <typename S, bool ANISO, int TY>
+static cudaError_t configure_tma(size_t dyn) {
+    static size_t configured = 0;
+    if (dyn > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_potts_admm_tma<S, ANISO, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn);
+        if (e != cudaSuccess) return e;
+        configured = dyn;
+    }
+    return cudaSuccess;
+}
+
+// Warps of this kernel resident per SM for L labels (0 on error).
+template <typename S, bool ANISO, int TY>
+static int resident_warps(int L) {
+    const size_t dyn = PottsTmaLayout<S, TY>::dyn_bytes(L);
+    int blocks = 0;
+    if (configure_tma<S, ANISO, TY>(dyn) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_potts_admm_tma<S, ANISO, TY>,
+                                                      256, dyn) != cudaSuccess)
+        return 0;
+    return blocks * 8;
+}
+
+template <typename S, bool ANISO>
+static int auto_ty(int L) {
+    if (!potts_tma_fits(sizeof(S) == 4 ? CMF_F32 : CMF_F16, L, 16)) return 8;
+    return resident_warps<S, ANISO, 8>(L) > resident_warps<S, ANISO, 16>(L) ? 8 : 16;
+}
+
+int potts_tma_auto_ty(int storage, bool aniso, int L) {
+    switch (storage) {
+        case CMF_F32: return aniso ? auto_ty<float, true>(L) : auto_ty<float, false>(L);
+        case CMF_F16: return aniso ? auto_ty<__half, true>(L) : auto_ty<__half, false>(L);
+        default:
+            return aniso ? auto_ty<__nv_bfloat16, true>(L) : auto_ty<__nv_bfloat16, false>(L);
+    }
+}
+
 template <typename S, bool ANISO, int TY>
 static cudaError_t launch_tma(const PottsProblem& P, const PottsState<S>& b, const AdmmCoef& K,
                               const PottsTmaMaps& m, int* err, cudaStream_t st) {
     using Lay = PottsTmaLayout<S, TY>;
     const size_t dyn = Lay::dyn_bytes(P.L);
     auto kern = k_potts_admm_tma<S, ANISO, TY>;
-    static size_t configured = 0;
-    if (dyn > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
-        if (e != cudaSuccess) return e;
-        configured = dyn;
-    }
+    cudaError_t e = configure_tma<S, ANISO, TY>(dyn);
+    if (e != cudaSuccess) return e;
     const dim3 grid((P.g.W + 31) / 32, (P.g.H + TY - 1) / TY);
     kern<<<grid, dim3(32, 8), dyn, st>>>(P, b, K, m.qx, m.qy, m.p, m.u, m.ps, err);
     return cudaGetLastError();
