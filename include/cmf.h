@@ -104,10 +104,15 @@ typedef struct {
                           certificates, stop test} with no host round trip; used
                           when max_iter % check_every == 0 and, for CMF_FUSED,
                           check_every is even), else a host-driven loop        */
-    int variant;       /* kernel variant: 0 = automatic (TMA-staged tiles where the
-                          layout allows: rows and planes 16-byte aligned), 1 = the
-                          shared-memory tile kernels, 8 / 16 / 32 = TMA tiles of that
-                          many rows (Potts ADMM)                               */
+    int variant;       /* kernel variant: 0 = automatic (Potts ADMM: warp strips
+                          where the layout allows them, else as for binary; binary
+                          ADMM: TMA-staged tiles where the layout allows: rows and
+                          planes 16-byte aligned), 1 = the
+                          shared-memory tile kernels, 2 = warp strips (Potts ADMM;
+                          even W and pitch, planes aligned to two elements; the
+                          multipliers are kept as u - cu p_s between iterations
+                          of one call), 8 / 16 / 32 = TMA tiles of that many rows
+                          (Potts ADMM)                                         */
     double c;          /* ADMM step size                                       */
     double a;          /* q preconditioner N = a c I (a >= 8, Thm 1)           */
     double a1;         /* p preconditioner a~ (binary) / a_1 (Potts), >= 2     */
@@ -238,7 +243,7 @@ cmf_status cmf_solve_potts(const float *d_C, int L, const float *d_alpha, float 
 /* ------------------------------------------------------------------------ */
 /* Autotuning (no counterpart in the paper: a launch-configuration search).  */
 /* Solves the problem from a cold start once per candidate configuration --  */
-/* the kernel variant (1, 8, 16, 32) of the fused ADMM algorithms, or the    */
+/* the kernel variant (1, 2, 8, 16, 32) of the fused ADMM algorithms, or the */
 /* sRBGS sweep count (1, 2, 3) of fused rPDRQ -- with everything else taken  */
 /* from *p, and writes the candidate with the shortest time to p->tol_gap    */
 /* (CUDA events on `stream`, best of two runs after a warm-up) to *best and  */

@@ -75,8 +75,8 @@ cmf_status check_params(const cmf_params* p, int L) {
     if (!(p->rho > 0) || !(p->rho < 2)) return CMF_EINVAL;
     if (!(p->r > 0) || !(p->sigma > 0) || !(p->tau > 0)) return CMF_EINVAL;
     if (p->max_iter < 0 || p->check_every < 1 || !(p->tol_gap >= 0)) return CMF_EINVAL;
-    if (p->variant != 0 && p->variant != 1 && p->variant != 8 && p->variant != 16 &&
-        p->variant != 32)
+    if (p->variant != 0 && p->variant != 1 && p->variant != 2 && p->variant != 8 &&
+        p->variant != 16 && p->variant != 32)
         return CMF_EINVAL;
     (void)L;
     return CMF_OK;
@@ -175,6 +175,7 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     call.storage = p->storage;
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
+    if (p->variant == 2) return CMF_EINVAL;  // warp strips: Potts only
     const int ty = p->variant >= 8 ? p->variant : 16;
     // automatic choice: the persistent TMA kernel wins on grids that fit the
     // L2 cache, the shared-memory tile kernel on larger ones (measured)
@@ -293,6 +294,7 @@ struct PottsCall {
     StepConfig cfg;
     int storage;
     bool tma;                    // fused ADMM through TMA-staged tiles
+    bool strip;                  // fused ADMM by warp strips
     PottsTmaMaps maps[2];        // tensor maps of the user / workspace state sets
     int* err;                    // sticky device error word
 };
@@ -321,6 +323,18 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.storage = p->storage;
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
+    call.strip = false;
+    // automatic choice: warp strips where the layout allows them (fastest on
+    // every measured Potts case), else TMA tiles, else shared-memory tiles
+    if (!call.cfg.dr && !call.cfg.plain && (p->variant == 2 || p->variant == 0)) {
+        const bool ok = potts_strip_eligible(call.P.g, p->storage, C, alpha, call.user, call.ws);
+        if (!ok && p->variant == 2)
+            return CMF_EINVAL;  // warp strips requested but the layout does not allow them
+        if (ok) {
+            call.strip = true;
+            return CMF_OK;
+        }
+    }
     const bool want_tma = !call.cfg.dr && !call.cfg.plain && p->variant != 1;
     const int ty = p->variant >= 8 ? p->variant
                                    : (want_tma ? potts_tma_auto_ty(p->storage, p->aniso, L) : 16);
@@ -344,6 +358,17 @@ cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st) {
             cudaError_t e = potts_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur = 0;
+        } else if (c.strip) {
+            const PottsStateV& a = cur == 0 ? c.user : c.ws;
+            const PottsStateV& b = cur == 0 ? c.ws : c.user;
+            // the first iteration reads u itself, later ones the w form
+            cudaError_t e = potts_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac,
+                                             i == 0 ? 0.0f : c.cfg.ac.cu, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+            if (i == n - 1 &&
+                (e = potts_strip_finalize(c.storage, c.P, b, c.cfg.ac.cu, st)) != cudaSuccess)
+                return e;
         } else if (c.tma) {
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
             cudaError_t e = potts_admm_tma_step(c.storage, c.P, b, c.cfg.aniso, c.cfg.ac,
@@ -746,7 +771,7 @@ std::vector<cmf_params> tune_candidates(const cmf_params& p) {
     const bool dr = p.algo == CMF_RPDRQ;
     std::vector<int> variants = {p.variant};
     std::vector<int> sweeps = {p.sweeps};
-    if (fused && !dr) variants = {1, 8, 16, 32};
+    if (fused && !dr) variants = {1, 2, 8, 16, 32};
     if (fused && dr) sweeps = {1, 2, 3};
     for (int v : variants)
         for (int s : sweeps) {

@@ -138,6 +138,19 @@ cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s,
 cudaError_t halfsweeps(const Grid& G, float* u, const float* b, const DrCoef& D,
                        cudaStream_t st);
 
+// --- warp-strip Potts ADMM (cmf_potts_strip.cu) ---
+// Eligible: even W and pitch, H * pitch within int, pair-aligned planes.
+bool potts_strip_eligible(const Grid& G, int storage, const float* C, const float* alpha,
+                          const PottsStateV& a, const PottsStateV& b);
+// One iteration a -> b.  Reads u_i = a.u_i + cu_in * a.p_s; writes
+// w_i = u_i^{k+1} - cu * p_s^{k+1} into b.u (see potts_strip_finalize).
+cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
+                             const PottsStateV& b, bool aniso, const AdmmCoef& K, float cu_in,
+                             cudaStream_t st);
+// s.u_i += cu * s.p_s on every label (w back to u).
+cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const PottsStateV& s,
+                                 float cu, cudaStream_t st);
+
 // --- TMA-staged Potts ADMM (cmf_potts_tma.cu) ---
 struct PottsTmaMaps {
     CUtensorMap qx, qy, p, u, ps;

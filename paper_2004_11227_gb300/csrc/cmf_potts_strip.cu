@@ -1,0 +1,364 @@
+// Potts ADMM iteration by warp strips (Eq. multi:fg:4, the Eckstein-Bertsekas
+// Potts equations after Thm 2, and pADMM-TY, Eq. mADMM:Tai_yuan).
+//
+// Work unit: one warp, a strip of 64 columns (two adjacent columns per lane)
+// and a band of R output rows.  The warp walks the labels one after another;
+// for each label it streams down the band row by row, keeping the stencil's
+// rolling values (g of the next row, the previous row's new q_y) in registers
+// and exchanging column neighbours with warp shuffles.  There are no block
+// barriers and no shared-memory halo tiles; loads of row t+2 are in flight
+// while row t is computed.  Lanes cover columns cs-2 .. cs+61 and own the
+// output columns cs .. cs+59; lane 0 and lane 31 only carry the halo.
+//
+// Multiplier representation.  Every ADMM variant updates u_i linearly in
+// p_s^{k+1}: u_i^{k+1} = v_i + cu p_s^{k+1}.  This kernel stores
+// w_i = v_i instead of u_i^{k+1}, so the labels need no second pass once
+// p_s^{k+1} is known, and it reads u_i^k = w_i + cu_in p_s^k (cu_in = 0 when
+// the input holds u itself).  k_potts_strip_finalize turns w back into u.
+//
+// The per-label shares of the p_s update are summed in shared memory (one
+// float2 per lane and band row); p_s^{k+1} is formed after the last label.
+#include <climits>
+
+#include "cmf_kernels.cuh"
+
+namespace cmf {
+
+namespace {
+
+constexpr int kStripOut = 60;   // output columns per warp strip
+constexpr int kStripWarps = 4;  // warps per block
+constexpr int kStripRmax = 32;  // band rows at most (shared accumulators)
+
+// Two adjacent elements of a plane: raw pair type and conversions.
+template <typename S>
+struct Pair;
+template <>
+struct Pair<float> {
+    using T = float2;
+    static __device__ __forceinline__ T ld(const float* p) {
+        return __ldg(reinterpret_cast<const float2*>(p));
+    }
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ float2 f2(T v) { return v; }
+    static __device__ __forceinline__ void st(float* p, float a, float b) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+};
+template <>
+struct Pair<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ T ld(const __half* p) {
+        return __ldg(reinterpret_cast<const __half2*>(p));
+    }
+    static __device__ __forceinline__ T zero() { return __float2half2_rn(0.f); }
+    static __device__ __forceinline__ float2 f2(T v) { return __half22float2(v); }
+    static __device__ __forceinline__ void st(__half* p, float a, float b) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ T ld(const __nv_bfloat16* p) {
+        return __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    static __device__ __forceinline__ T zero() { return __float2bfloat162_rn(0.f); }
+    static __device__ __forceinline__ float2 f2(T v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// P_alpha without a branch (Eq. projections): the scale is selected, so the
+// reciprocal square root of a zero norm is computed and discarded.
+template <bool ANISO>
+__device__ __forceinline__ void project_sel(float& x, float& y, float al) {
+    al = fmaxf(al, 0.0f);
+    if (ANISO) {
+        x = fminf(fmaxf(x, -al), al);
+        y = fminf(fmaxf(y, -al), al);
+    } else {
+        const float n2 = x * x + y * y;
+        const float s = n2 > al * al ? al * rsqrtf(n2) : 1.0f;
+        x *= s;
+        y *= s;
+    }
+}
+
+// State values of one row of one label at this lane's column pair.
+template <typename S>
+struct RowVals {
+    typename Pair<S>::T qx, qy, p, ps;
+    float2 w;
+};
+
+}  // namespace
+
+template <typename S, bool ANISO>
+__global__ void __launch_bounds__(kStripWarps * 32)
+    k_potts_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, float cu_in,
+                  int R, int nstrips, int nitems) {
+    using St = Store<S>;
+    using PS = Pair<S>;
+    using PF = Pair<float>;
+    __shared__ float2 acc_s[kStripWarps][kStripRmax][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float2(*acc)[32] = acc_s[wib];
+    const Grid G = P.g;
+    const int L = P.L;
+    const unsigned full = 0xffffffffu;
+
+    for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
+         item += gridDim.x * kStripWarps) {
+        const int cs = (item % nstrips) * kStripOut;
+        const int r0 = (item / nstrips) * R;
+        const int r1 = min(r0 + R, G.H);
+        const int c = cs - 2 + 2 * lane;  // even column of the pair (W is even)
+        const bool colin = c >= 0 && c < G.W;
+        const bool own = colin && lane >= 1 && lane <= 30;
+        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;  // odd column is not the last
+
+        // one row of state at (r, c..c+1): zero outside the grid
+        auto load_row = [&](const S* qx, const S* qy, const S* pp, const float* w, int r,
+                            RowVals<S>& x) {
+            const bool ok = colin && r >= 0 && r < G.H;
+            const int o = r * G.pitch + c;
+            x.qx = ok ? PS::ld(qx + o) : PS::zero();
+            x.qy = ok ? PS::ld(qy + o) : PS::zero();
+            x.p = ok ? PS::ld(pp + o) : PS::zero();
+            x.ps = ok ? PS::ld(s0.ps + o) : PS::zero();
+            x.w = ok ? PF::ld(w + o) : PF::zero();
+        };
+        // weight of a row's own y term: row H-1 has no forward difference
+        auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+        // g = div q + p_i - p_s - u_i / c at row r, given the row above's q_y
+        // (outside the grid the loaded values are zero)
+        auto g_of = [&](const RowVals<S>& x, float2 qy_up, int r) {
+            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy), p = PS::f2(x.p);
+            const float2 ps = PS::f2(x.ps);
+            const float qx_left = __shfl_up_sync(full, qx.y, 1);
+            const float wy = row_w(r);
+            const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
+            float2 g;
+            g.x = qx.x - qx_left + wy * qy.x - qy_up.x + p.x - ps.x - u_e * K.inv_c;
+            g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + p.y - ps.y - u_o * K.inv_c;
+            return g;
+        };
+
+#pragma unroll 1
+        for (int l = 0; l < L; ++l) {
+            const size_t lo = (size_t)l * G.plane;
+            const S* qx0 = s0.qx + lo;
+            const S* qy0 = s0.qy + lo;
+            const S* p0 = s0.p + lo;
+            const float* w0 = s0.u + lo;
+            const float* Cl = P.C + lo;
+            S* qx1 = s1.qx + lo;
+            S* qy1 = s1.qy + lo;
+            S* p1o = s1.p + lo;
+            float* w1 = s1.u + lo;
+
+            // prologue: g at row r0-1 needs q_y of row r0-2
+            RowVals<S> a, b, nx;
+            const int rm2 = r0 - 2;
+            const float2 qy_m2 = PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c)
+                                                            : PS::zero());
+            load_row(qx0, qy0, p0, w0, r0 - 1, a);
+            load_row(qx0, qy0, p0, w0, r0, b);
+            float2 g_t = g_of(a, qy_m2, r0 - 1);
+            float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
+            // C and alpha of row t (prefetched one row ahead)
+            auto ld_c = [&](int r) {
+                return (colin && r >= 0 && r < G.H) ? PF::ld(Cl + r * G.pitch + c) : PF::zero();
+            };
+            auto ld_al = [&](int r) {
+                if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+                return (colin && r >= 0 && r < G.H) ? PF::ld(P.alpha.plane + r * G.pitch + c)
+                                                    : PF::zero();
+            };
+            float2 al_t = ld_al(r0 - 1), cl_t = PF::zero();  // row t's alpha and cost
+
+#pragma unroll 1
+            for (int t = r0 - 1; t < r1; ++t) {
+                load_row(qx0, qy0, p0, w0, t + 2, nx);  // in flight during this row
+                const float2 al_n = ld_al(t + 1), cl_n = ld_c(t + 1);
+                const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);  // g at row t+1
+
+                // q^{k+1} = P_alpha(q + grad g / a) at row t
+                const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
+                const float my = row_w(t) * K.inv_a;
+                const float2 qx = PS::f2(a.qx), qy = PS::f2(a.qy);
+                float tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
+                float tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
+                float ty_e = qy.x + (g_n.x - g_t.x) * my;
+                float ty_o = qy.y + (g_n.y - g_t.y) * my;
+                project_sel<ANISO>(tx_e, ty_e, al_t.x);
+                project_sel<ANISO>(tx_o, ty_o, al_t.y);
+                const bool in = colin && t >= 0;  // t < r1 <= H
+                tx_e = in ? St::rt(tx_e) : 0.f;
+                tx_o = in ? St::rt(tx_o) : 0.f;
+                ty_e = in ? St::rt(ty_e) : 0.f;
+                ty_o = in ? St::rt(ty_o) : 0.f;
+
+                const float txl = __shfl_up_sync(full, tx_o, 1);  // new q_x at c-1
+                if (t >= r0) {
+                    const int o = t * G.pitch + c;
+                    // d = div q^{k+1} at row t
+                    const float wy = row_w(t);
+                    const float d_e = tx_e - txl + wy * ty_e - qyn_up.x;
+                    const float d_o = mxo * tx_o - tx_e + wy * ty_o - qyn_up.y;
+                    // p_i^{k+1}, w_i and the p_s share at row t
+                    const float2 pv = PS::f2(a.p), ps = PS::f2(a.ps);
+                    const float u_e = fmaf(cu_in, ps.x, a.w.x), u_o = fmaf(cu_in, ps.y, a.w.y);
+                    float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
+                    const float p1_e =
+                        potts_label_pu<S>(K, d_e, pv.x, ps.x, u_e, cl_t.x, sa_e, sb_e, v_e);
+                    const float p1_o =
+                        potts_label_pu<S>(K, d_o, pv.y, ps.y, u_o, cl_t.y, sa_o, sb_o, v_o);
+                    float2& ac = acc[t - r0][lane];
+                    const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
+                    if (l == 0) {
+                        ac = share;
+                    } else {
+                        ac.x += share.x;
+                        ac.y += share.y;
+                    }
+                    if (own) {
+                        PS::st(qx1 + o, tx_e, tx_o);
+                        PS::st(qy1 + o, ty_e, ty_o);
+                        PS::st(p1o + o, p1_e, p1_o);
+                        PF::st(w1 + o, v_e, v_o);
+                    }
+                }
+                qyn_up = make_float2(ty_e, ty_o);
+                a = b;
+                b = nx;
+                g_t = g_n;
+                al_t = al_n;
+                cl_t = cl_n;
+            }
+        }
+
+        // p_s^{k+1} on the band from the summed label shares
+#pragma unroll 1
+        for (int t = r0; t < r1; ++t) {
+            if (!own) continue;
+            const int o = t * G.pitch + c;
+            const float2 ps = PS::f2(PS::ld(s0.ps + o));
+            const float2 ac = acc[t - r0][lane];
+            PS::st(s1.ps + o, potts_ps_update<S>(K, ps.x, ac.x, 0.f),
+                   potts_ps_update<S>(K, ps.y, ac.y, 0.f));
+        }
+    }
+}
+
+// u_i = w_i + cu p_s on every label plane (turns the strip kernel's output
+// back into the multipliers themselves).
+template <typename S>
+__global__ void k_potts_strip_finalize(Grid G, int L, float* u, const S* ps, float cu) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (c >= G.W) return;
+    const size_t k = G.idx(r, c);
+    const float s = cu * Store<S>::ld(ps + k);
+#pragma unroll 4
+    for (int l = 0; l < L; ++l) u[(size_t)l * G.plane + k] += s;
+}
+
+// ---- host side -------------------------------------------------------------
+
+bool potts_strip_eligible(const Grid& G, int storage, const float* C, const float* alpha,
+                          const PottsStateV& a, const PottsStateV& b) {
+    if (G.W % 2 || G.pitch % 2) return false;
+    if ((size_t)G.H * (size_t)G.pitch > (size_t)INT_MAX) return false;
+    const size_t es2 = 2 * dtype_size(storage);
+    auto al = [](const void* p, size_t n) { return ((uintptr_t)p % n) == 0; };
+    if (!al(C, 8) || (alpha && !al(alpha, 8))) return false;
+    for (const PottsStateV* s : {&a, &b})
+        if (!al(s->u, 8) || !al(s->qx, es2) || !al(s->qy, es2) || !al(s->p, es2) ||
+            !al(s->ps, es2))
+            return false;
+    return true;
+}
+
+template <typename S, bool ANISO>
+static cudaError_t launch_strip(const PottsProblem& P, const PottsState<S>& a,
+                                const PottsState<S>& b, const AdmmCoef& K, float cu_in,
+                                cudaStream_t st) {
+    auto kern = k_potts_strip<S, ANISO>;
+    static int resident = 0;  // warps resident on the whole device
+    if (!resident) {
+        int dev = 0, sms = 0, blocks = 0;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
+                                                                0)) != cudaSuccess)
+            return e;
+        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    }
+    const Grid& G = P.g;
+    const int nstrips = (G.W + kStripOut - 1) / kStripOut;
+    // band height: fewest rounds of work items over the resident warps, each
+    // round costing R + 3 rows (the band plus its halo rows)
+    int best_r = kStripRmax;
+    long long best_cost = -1;
+    for (int r = 8; r <= kStripRmax; ++r) {
+        const long long items = (long long)nstrips * ((G.H + r - 1) / r);
+        const long long rounds = (items + resident - 1) / resident;
+        const long long cost = rounds * (r + 3);
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best_r = r;
+        }
+    }
+    const int nitems = nstrips * ((G.H + best_r - 1) / best_r);
+    const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
+    const int grid = blocks < resident / kStripWarps ? blocks : resident / kStripWarps;
+    kern<<<grid, kStripWarps * 32, 0, st>>>(P, a, b, K, cu_in, best_r, nstrips, nitems);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t strip_step_s(const PottsProblem& P, const PottsStateV& a,
+                                const PottsStateV& b, bool aniso, const AdmmCoef& K,
+                                float cu_in, cudaStream_t st) {
+    const PottsState<S> A = a.as<S>(), B = b.as<S>();
+    return aniso ? launch_strip<S, true>(P, A, B, K, cu_in, st)
+                 : launch_strip<S, false>(P, A, B, K, cu_in, st);
+}
+
+cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
+                             const PottsStateV& b, bool aniso, const AdmmCoef& K, float cu_in,
+                             cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return strip_step_s<float>(P, a, b, aniso, K, cu_in, st);
+        case CMF_F16: return strip_step_s<__half>(P, a, b, aniso, K, cu_in, st);
+        default: return strip_step_s<__nv_bfloat16>(P, a, b, aniso, K, cu_in, st);
+    }
+}
+
+cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const PottsStateV& s,
+                                 float cu, cudaStream_t st) {
+    const Grid& G = P.g;
+    const dim3 grid((G.W + 127) / 128, G.H);
+    switch (storage) {
+        case CMF_F32:
+            k_potts_strip_finalize<float><<<grid, 128, 0, st>>>(G, P.L, s.u, (const float*)s.ps,
+                                                                 cu);
+            break;
+        case CMF_F16:
+            k_potts_strip_finalize<__half><<<grid, 128, 0, st>>>(G, P.L, s.u,
+                                                                  (const __half*)s.ps, cu);
+            break;
+        default:
+            k_potts_strip_finalize<__nv_bfloat16>
+                <<<grid, 128, 0, st>>>(G, P.L, s.u, (const __nv_bfloat16*)s.ps, cu);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cmf

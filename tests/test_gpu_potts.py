@@ -120,8 +120,9 @@ def test_solve_certified_by_oracle(cmf, algo):
     assert np.mean(O.potts_labels(st["u"]) == O.potts_labels(opt["u"])) >= 0.99
 
 
-def _window_step_check(cmf, inst, algo, k_before, windows, margin=8, storage=0, tol=2e-5):
-    p = cmf.default_params(algo, inst.L, storage=storage)
+def _window_step_check(cmf, inst, algo, k_before, windows, margin=8, storage=0, tol=2e-5,
+                       variant=0):
+    p = cmf.default_params(algo, inst.L, storage=storage, variant=variant)
     s = cmf.alloc_potts(inst, p)
     cmf.cmf_init_potts(s)
     cmf.cmf_iterate_potts(s, k_before)
@@ -204,3 +205,116 @@ def test_tma_tiles_match_smem_tiles(cmf, storage, variant, L, shape):
     tol = 1e-6 if storage == 0 else 1e-2
     for k in a:
         assert np.abs(a[k] - b[k]).max() <= tol, k
+
+
+# ---- warp-strip kernel (variant 2) ---------------------------------------------
+
+STRIP_CASES = {
+    "voronoi4_48x40": (synth.config3(48, 40), 60),
+    "voronoi16_edge_45x64": (synth.config5(45, 64), 31),
+    "L4_ragged_70x130": (synth.random_potts(70, 130, 4, seed=81, alpha=0.3,
+                                            field_alpha=True), 25),
+    "L3_1x50": (synth.random_potts(1, 50, 3, seed=22, alpha=0.3), 30),
+    "L8_37x2": (synth.random_potts(37, 2, 8, seed=23, alpha=0.3), 30),
+    "L2_tall_301x62": (synth.random_potts(301, 62, 2, seed=82, alpha=0.4,
+                                          field_alpha=True), 17),
+}
+
+
+@pytest.mark.parametrize("algo", ALGOS[:3] + [4])
+@pytest.mark.parametrize("case", list(STRIP_CASES))
+def test_strip_matches_oracle_f32(cmf, case, algo):
+    """Warp-strip ADMM kernel against the oracle after a fixed number of
+    iterations (odd and even counts: the result lands in either buffer set,
+    and the multipliers are turned back from the w form at the end)."""
+    inst, n = STRIP_CASES[case]
+    s = _gpu_run(cmf, inst, algo, n, variant=2)
+    got = s.state()
+    ref, _ = _oracle_run(inst, algo, n)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        err = np.abs(got[k] - ref[k]).max()
+        assert err <= TOL_U, (k, err)
+
+
+@pytest.mark.parametrize("algo", [1, 2])
+def test_strip_anisotropic(cmf, algo):
+    inst = synth.random_potts(31, 26, 4, seed=40, alpha=0.3, field_alpha=True)
+    s = _gpu_run(cmf, inst, algo, 30, aniso=1, variant=2)
+    ref, _ = _oracle_run(inst, algo, 30, aniso=1)
+    assert np.abs(s.state()["u"] - ref["u"]).max() <= TOL_U
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("L,shape", [(4, (70, 98)), (16, (33, 40)), (3, (5, 130))])
+def test_strip_matches_smem_tiles_half(cmf, storage, L, shape):
+    """16-bit flow storage: the strip kernel computes what the shared-memory
+    tile kernel computes, up to the storage rounding of close values."""
+    inst = synth.random_potts(*shape, L, seed=70 + L, alpha=0.3, field_alpha=True)
+    a = _gpu_run(cmf, inst, 2, 7, storage=storage, variant=1).state()
+    b = _gpu_run(cmf, inst, 2, 7, storage=storage, variant=2).state()
+    for k in a:
+        assert np.abs(a[k] - b[k]).max() <= 1e-2, k
+
+
+def test_strip_rejects_odd_width(cmf):
+    inst = synth.random_potts(20, 33, 3, seed=83, alpha=0.3)
+    p = cmf.default_params(2, 3, variant=2)
+    s = cmf.alloc_potts(inst, p)
+    with pytest.raises(cmf.CmfError):
+        cmf.cmf_iterate_potts(s, 2)
+
+
+def test_strip_iterate_then_solve_continues(cmf):
+    """Calls chain: the state after cmf_iterate holds u (not the w form), so
+    two calls of n iterations equal one call of 2n."""
+    inst = synth.random_potts(40, 64, 4, seed=84, alpha=0.3, field_alpha=True)
+    p = cmf.default_params(2, 4, variant=2)
+    a = cmf.alloc_potts(inst, p)
+    cmf.cmf_init_potts(a)
+    cmf.cmf_iterate_potts(a, 9)
+    cmf.cmf_iterate_potts(a, 8)
+    b = cmf.alloc_potts(inst, p)
+    cmf.cmf_init_potts(b)
+    cmf.cmf_iterate_potts(b, 17)
+    ga, gb = a.state(), b.state()
+    for k in ga:
+        assert np.abs(ga[k] - gb[k]).max() <= 1e-6, k
+
+
+@pytest.mark.parametrize("algo", [2, 4])
+def test_strip_full_size_2048_L4_windows(cmf, algo):
+    inst = synth.config3()
+    wins = [(0, 0, 40, 40), (2048 - 37, 2048 - 45, 37, 45), (1000, 1500, 64, 64),
+            (0, 1111, 33, 70)]
+    _window_step_check(cmf, inst, algo, 23, wins, variant=2)
+
+
+def test_strip_full_size_4096_L16_f16_windows(cmf):
+    inst = synth.config5()
+    wins = [(0, 0, 32, 32), (4096 - 29, 4096 - 40, 29, 40), (2001, 3007, 40, 40)]
+    _window_step_check(cmf, inst, 2, 11, wins, storage=1, tol=2e-3, variant=2)
+
+
+def test_strip_matches_tma_full_size_2048_L4(cmf):
+    """Every output of a few full-size iterations: strip kernel against the
+    TMA tile kernel (many work items per warp, ragged last strip)."""
+    inst = synth.config3()
+    a = _gpu_run(cmf, inst, 2, 6, variant=16)
+    b = _gpu_run(cmf, inst, 2, 6, variant=2)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        err = (getattr(a, k).float() - getattr(b, k).float()).abs().max().item()
+        assert err <= 1e-5, (k, err)
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_strip_solve_certified(cmf, use_graph):
+    """Solve to the gap with the strip kernel (checks between chunks see u,
+    not the w form); the oracle certifies the returned state."""
+    inst = synth.config3(96, 80)
+    p = cmf.default_params(2, 4, tol_gap=1e-4, max_iter=30000, check_every=10, variant=2,
+                           use_graph=use_graph)
+    s = cmf.alloc_potts(inst, p)
+    status, iters, hist = cmf.cmf_solve_potts(s)
+    assert status == cmf.OK and hist[-1, 3] <= 1e-4
+    E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, s.state(), O.default_params(2, 4))
+    assert gap <= 1.01e-4
