@@ -28,7 +28,8 @@ namespace {
 
 constexpr int kStripOut = 60;   // output columns per warp strip
 constexpr int kStripWarps = 4;  // warps per block
-constexpr int kStripRmax = 32;  // band rows at most (shared accumulators)
+constexpr int kStripRmax = 24;  // band rows at most (shared accumulators: 24 KB per
+                                // block, so seven blocks of 72 registers fit an SM)
 
 // Two adjacent elements of a plane: raw pair type and conversions.
 template <typename S>
@@ -96,7 +97,7 @@ struct RowVals {
 }  // namespace
 
 template <typename S, bool ANISO>
-__global__ void __launch_bounds__(kStripWarps * 32)
+__global__ void __launch_bounds__(kStripWarps * 32, 7)
     k_potts_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, float cu_in,
                   int R, int nstrips, int nitems) {
     using St = Store<S>;
@@ -146,6 +147,30 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             return g;
         };
 
+        // q^{k+1} = P_alpha(q + grad g / a) at row t of this pair, from g at
+        // rows t and t+1 (zero outside the grid)
+        struct QN {
+            float tx_e, tx_o, ty_e, ty_o;
+        };
+        auto q_new = [&](const RowVals<S>& x, float2 g_t, float2 g_b, float2 al, int t) {
+            const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
+            const float my = row_w(t) * K.inv_a;
+            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
+            QN q;
+            q.tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
+            q.tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
+            q.ty_e = qy.x + (g_b.x - g_t.x) * my;
+            q.ty_o = qy.y + (g_b.y - g_t.y) * my;
+            project_sel<ANISO>(q.tx_e, q.ty_e, al.x);
+            project_sel<ANISO>(q.tx_o, q.ty_o, al.y);
+            const bool in = colin && t >= 0 && t < G.H;
+            q.tx_e = in ? St::rt(q.tx_e) : 0.f;
+            q.tx_o = in ? St::rt(q.tx_o) : 0.f;
+            q.ty_e = in ? St::rt(q.ty_e) : 0.f;
+            q.ty_o = in ? St::rt(q.ty_o) : 0.f;
+            return q;
+        };
+
 #pragma unroll 1
         for (int l = 0; l < L; ++l) {
             const size_t lo = (size_t)l * G.plane;
@@ -158,17 +183,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             S* qy1 = s1.qy + lo;
             S* p1o = s1.p + lo;
             float* w1 = s1.u + lo;
-
-            // prologue: g at row r0-1 needs q_y of row r0-2
-            RowVals<S> a, b, nx;
-            const int rm2 = r0 - 2;
-            const float2 qy_m2 = PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c)
-                                                            : PS::zero());
-            load_row(qx0, qy0, p0, w0, r0 - 1, a);
-            load_row(qx0, qy0, p0, w0, r0, b);
-            float2 g_t = g_of(a, qy_m2, r0 - 1);
-            float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
-            // C and alpha of row t (prefetched one row ahead)
+            auto row = [&](int r, RowVals<S>& x) { load_row(qx0, qy0, p0, w0, r, x); };
             auto ld_c = [&](int r) {
                 return (colin && r >= 0 && r < G.H) ? PF::ld(Cl + r * G.pitch + c) : PF::zero();
             };
@@ -177,61 +192,58 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                 return (colin && r >= 0 && r < G.H) ? PF::ld(P.alpha.plane + r * G.pitch + c)
                                                     : PF::zero();
             };
-            float2 al_t = ld_al(r0 - 1), cl_t = PF::zero();  // row t's alpha and cost
+            // d = div q^{k+1} at output row t from the new q of rows t and t-1,
+            // then p_i^{k+1}, w_i and this label's share of the p_s update
+            auto finish = [&](int t, const QN& q, float2 qy_up, const RowVals<S>& x,
+                              float2 cl) {
+                const float txl = __shfl_up_sync(full, q.tx_o, 1);  // new q_x at c-1
+                const float wy = row_w(t);
+                const float d_e = q.tx_e - txl + wy * q.ty_e - qy_up.x;
+                const float d_o = mxo * q.tx_o - q.tx_e + wy * q.ty_o - qy_up.y;
+                const float2 pv = PS::f2(x.p), ps = PS::f2(x.ps);
+                const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
+                float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
+                const float p1_e = potts_label_pu<S>(K, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
+                const float p1_o = potts_label_pu<S>(K, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
+                float2& ac = acc[t - r0][lane];
+                const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
+                if (l == 0) {
+                    ac = share;
+                } else {
+                    ac.x += share.x;
+                    ac.y += share.y;
+                }
+                if (own) {
+                    const int o = t * G.pitch + c;
+                    PS::st(qx1 + o, q.tx_e, q.tx_o);
+                    PS::st(qy1 + o, q.ty_e, q.ty_o);
+                    PS::st(p1o + o, p1_e, p1_o);
+                    PF::st(w1 + o, v_e, v_o);
+                }
+            };
 
+            // top-down: step t makes q^{k+1} of row t and finishes row t;
+            // row t+2 is loaded during the step
+            RowVals<S> a, b, nx;
+            const int rm2 = r0 - 2;
+            const float2 qy_m2 = PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c)
+                                                            : PS::zero());
+            row(r0 - 1, a);
+            row(r0, b);
+            float2 g_t = g_of(a, qy_m2, r0 - 1);
+            float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
+            float2 al_t = ld_al(r0 - 1), cl_t = PF::zero(), al_n = al_t, cl_n = cl_t;
 #pragma unroll 1
             for (int t = r0 - 1; t < r1; ++t) {
-                load_row(qx0, qy0, p0, w0, t + 2, nx);  // in flight during this row
-                const float2 al_n = ld_al(t + 1), cl_n = ld_c(t + 1);
-                const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);  // g at row t+1
-
-                // q^{k+1} = P_alpha(q + grad g / a) at row t
-                const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
-                const float my = row_w(t) * K.inv_a;
-                const float2 qx = PS::f2(a.qx), qy = PS::f2(a.qy);
-                float tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
-                float tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
-                float ty_e = qy.x + (g_n.x - g_t.x) * my;
-                float ty_o = qy.y + (g_n.y - g_t.y) * my;
-                project_sel<ANISO>(tx_e, ty_e, al_t.x);
-                project_sel<ANISO>(tx_o, ty_o, al_t.y);
-                const bool in = colin && t >= 0;  // t < r1 <= H
-                tx_e = in ? St::rt(tx_e) : 0.f;
-                tx_o = in ? St::rt(tx_o) : 0.f;
-                ty_e = in ? St::rt(ty_e) : 0.f;
-                ty_o = in ? St::rt(ty_o) : 0.f;
-
-                const float txl = __shfl_up_sync(full, tx_o, 1);  // new q_x at c-1
-                if (t >= r0) {
-                    const int o = t * G.pitch + c;
-                    // d = div q^{k+1} at row t
-                    const float wy = row_w(t);
-                    const float d_e = tx_e - txl + wy * ty_e - qyn_up.x;
-                    const float d_o = mxo * tx_o - tx_e + wy * ty_o - qyn_up.y;
-                    // p_i^{k+1}, w_i and the p_s share at row t
-                    const float2 pv = PS::f2(a.p), ps = PS::f2(a.ps);
-                    const float u_e = fmaf(cu_in, ps.x, a.w.x), u_o = fmaf(cu_in, ps.y, a.w.y);
-                    float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
-                    const float p1_e =
-                        potts_label_pu<S>(K, d_e, pv.x, ps.x, u_e, cl_t.x, sa_e, sb_e, v_e);
-                    const float p1_o =
-                        potts_label_pu<S>(K, d_o, pv.y, ps.y, u_o, cl_t.y, sa_o, sb_o, v_o);
-                    float2& ac = acc[t - r0][lane];
-                    const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
-                    if (l == 0) {
-                        ac = share;
-                    } else {
-                        ac.x += share.x;
-                        ac.y += share.y;
-                    }
-                    if (own) {
-                        PS::st(qx1 + o, tx_e, tx_o);
-                        PS::st(qy1 + o, ty_e, ty_o);
-                        PS::st(p1o + o, p1_e, p1_o);
-                        PF::st(w1 + o, v_e, v_o);
-                    }
+                if (t + 2 <= r1) row(t + 2, nx);
+                if (t + 1 < r1) {
+                    al_n = ld_al(t + 1);
+                    cl_n = ld_c(t + 1);
                 }
-                qyn_up = make_float2(ty_e, ty_o);
+                const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);
+                const QN q = q_new(a, g_t, g_n, al_t, t);
+                if (t >= r0) finish(t, q, qyn_up, a, cl_t);
+                qyn_up = make_float2(q.ty_e, q.ty_o);
                 a = b;
                 b = nx;
                 g_t = g_n;
