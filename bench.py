@@ -456,8 +456,8 @@ def main():
     kern_ms = e0.elapsed_time(e1) / n_rf
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_PX * H * W / (kern_ms / 1000.0) / 1e9
-    # at this size the solver picks the persistent TMA kernel (one launch per iteration)
-    traffic = _traffic("paper_2004_11227_gb300/csrc/cmf_binary_tma.cu", "k_binary_admm_tma")
+    # the solver picks the warp-strip kernel here (one launch per iteration)
+    traffic = _traffic("paper_2004_11227_gb300/csrc/cmf_binary_strip.cu", "k_binary_strip")
 
     # --- plain one-kernel-per-step form and the other algorithms: time to gap ---------
     def time_to_gap(algo, impl):
@@ -505,7 +505,7 @@ def main():
                                "iterations": iters, "all": ttg},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_binary_admm_tma", "peak_kind": peak_kind,
+                         "kernel": "k_binary_strip", "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": BYTES_PER_PX * H * W,
                          "launch_ms": kern_ms},
             "cpu_baseline": {"value": rate, "unit": "px*label*it/s", "cores": 1,

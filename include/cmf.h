@@ -104,15 +104,16 @@ typedef struct {
                           certificates, stop test} with no host round trip; used
                           when max_iter % check_every == 0 and, for CMF_FUSED,
                           check_every is even), else a host-driven loop        */
-    int variant;       /* kernel variant: 0 = automatic (Potts ADMM: warp strips
-                          where the layout allows them, else as for binary; binary
-                          ADMM: TMA-staged tiles where the layout allows: rows and
-                          planes 16-byte aligned), 1 = the
-                          shared-memory tile kernels, 2 = warp strips (Potts ADMM;
-                          even W and pitch, planes aligned to two elements; the
-                          multipliers are kept as u - cu p_s between iterations
-                          of one call), 8 / 16 / 32 = TMA tiles of that many rows
-                          (Potts ADMM)                                         */
+    int variant;       /* kernel variant of the fused ADMM algorithms:
+                          0 = automatic: warp strips where the layout allows
+                          them, else TMA-staged tiles (Potts, and binary grids
+                          of at most 2^21 pixels) where rows and planes are
+                          16-byte aligned, else shared-memory tiles;
+                          1 = shared-memory tiles;
+                          2 = warp strips (even W and pitch, planes aligned to
+                          two elements; for Potts the multipliers are kept as
+                          u - cu p_s between the iterations of one call);
+                          8 / 16 / 32 = TMA tiles of that many rows         */
     double c;          /* ADMM step size                                       */
     double a;          /* q preconditioner N = a c I (a >= 8, Thm 1)           */
     double a1;         /* p preconditioner a~ (binary) / a_1 (Potts), >= 2     */

@@ -568,6 +568,9 @@ static cudaError_t binary_eval_s(const BinProblem& P, const BinStateV& sv, bool 
 
 cudaError_t binary_eval(int storage, const BinProblem& P, const BinStateV& s, bool aniso, bool dr,
                         float tau, double* partials, cudaStream_t st) {
+    const float* al = P.alpha.plane;
+    if (binary_strip_eligible(P.g, storage, P.Cs, P.Ct, al, s, s))
+        return binary_eval_strip(storage, P, s, aniso, dr, tau, partials, st);
     switch (storage) {
         case CMF_F32: return binary_eval_s<float>(P, s, aniso, dr, tau, partials, st);
         case CMF_F16: return binary_eval_s<__half>(P, s, aniso, dr, tau, partials, st);

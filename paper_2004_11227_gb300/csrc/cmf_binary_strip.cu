@@ -1,0 +1,387 @@
+// Binary ADMM iteration by warp strips (Eq. rpADMMII, Eq. rpADMMI, pADMM-TY
+// Eq. ADMM:Tai_yuan).
+//
+// Work unit: one warp, a strip of 64 columns (two adjacent columns per lane)
+// and a band of R output rows, streamed top-down.  Step t holds rows t and
+// t+1 of the state in registers while row t+2 is in flight, makes g of row
+// t+1, the new flow q of row t (column neighbours by warp shuffles), its
+// divergence, and the pointwise p_s, p_t, u update of row t.  Lanes cover
+// columns cs-2 .. cs+61 and own the output columns cs .. cs+59.
+#include <climits>
+
+#include "cmf_kernels.cuh"
+#include "cmf_strip.cuh"
+
+namespace cmf {
+
+using strip::kStripOut;
+using strip::kStripWarps;
+using strip::Pair;
+using strip::project_sel;
+
+namespace {
+
+// State values of one row at this lane's column pair.
+template <typename S>
+struct BinRow {
+    typename Pair<S>::T qx, qy, ps, pt;
+    float2 u;
+};
+
+}  // namespace
+
+template <typename S, bool ANISO>
+__global__ void __launch_bounds__(kStripWarps * 32, 8)
+    k_binary_strip(BinProblem P, BinState<S> s0, BinState<S> s1, AdmmCoef K, int R,
+                   int nstrips, int nitems) {
+    using St = Store<S>;
+    using PS = Pair<S>;
+    using PF = Pair<float>;
+    const int lane = threadIdx.x & 31;
+    const Grid G = P.g;
+    const unsigned full = 0xffffffffu;
+
+    for (int item = blockIdx.x * kStripWarps + (threadIdx.x >> 5); item < nitems;
+         item += gridDim.x * kStripWarps) {
+        const int cs = (item % nstrips) * kStripOut;
+        const int r0 = (item / nstrips) * R;
+        const int r1 = min(r0 + R, G.H);
+        const int c = cs - 2 + 2 * lane;  // even column of the pair (W is even)
+        const bool colin = c >= 0 && c < G.W;
+        const bool own = colin && lane >= 1 && lane <= 30;
+        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;  // odd column is not the last
+
+        auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
+        auto row = [&](int r, BinRow<S>& x) {
+            const bool ok = ok_row(r);
+            const int o = r * G.pitch + c;
+            x.qx = ok ? PS::ld(s0.qx + o) : PS::zero();
+            x.qy = ok ? PS::ld(s0.qy + o) : PS::zero();
+            x.ps = ok ? PS::ld(s0.ps + o) : PS::zero();
+            x.pt = ok ? PS::ld(s0.pt + o) : PS::zero();
+            x.u = ok ? PF::ld(s0.u + o) : PF::zero();
+        };
+        auto ld_f = [&](const float* base, int r) {
+            return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
+        };
+        auto ld_al = [&](int r) {
+            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+            return ld_f(P.alpha.plane, r);
+        };
+        auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+        // g = div q + p_t - p_s - u / c at row r, given the row above's q_y
+        auto g_of = [&](const BinRow<S>& x, float2 qy_up, int r) {
+            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
+            const float2 ps = PS::f2(x.ps), pt = PS::f2(x.pt);
+            const float qx_left = __shfl_up_sync(full, qx.y, 1);
+            const float wy = row_w(r);
+            float2 g;
+            g.x = qx.x - qx_left + wy * qy.x - qy_up.x + pt.x - ps.x - x.u.x * K.inv_c;
+            g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + pt.y - ps.y - x.u.y * K.inv_c;
+            return g;
+        };
+
+        BinRow<S> a, b, nx;
+        const int rm2 = r0 - 2;
+        const float2 qy_m2 =
+            PS::f2(ok_row(rm2) ? PS::ld(s0.qy + rm2 * G.pitch + c) : PS::zero());
+        row(r0 - 1, a);
+        row(r0, b);
+        float2 g_t = g_of(a, qy_m2, r0 - 1);
+        float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
+        float2 al_t = ld_al(r0 - 1), cs_t = PF::zero(), ct_t = PF::zero();
+        float2 al_n = al_t, cs_n = cs_t, ct_n = ct_t;
+#pragma unroll 1
+        for (int t = r0 - 1; t < r1; ++t) {
+            if (t + 2 <= r1) row(t + 2, nx);  // in flight during this row
+            if (t + 1 < r1) {
+                al_n = ld_al(t + 1);
+                cs_n = ld_f(P.Cs, t + 1);
+                ct_n = ld_f(P.Ct, t + 1);
+            }
+            const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);  // g at row t+1
+
+            // q^{k+1} = P_alpha(q + grad g / a) at row t
+            const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
+            const float my = row_w(t) * K.inv_a;
+            const float2 qx = PS::f2(a.qx), qy = PS::f2(a.qy);
+            float tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
+            float tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
+            float ty_e = qy.x + (g_n.x - g_t.x) * my;
+            float ty_o = qy.y + (g_n.y - g_t.y) * my;
+            project_sel<ANISO>(tx_e, ty_e, al_t.x);
+            project_sel<ANISO>(tx_o, ty_o, al_t.y);
+            const bool in = colin && t >= 0;  // t < r1 <= H
+            tx_e = in ? St::rt(tx_e) : 0.f;
+            tx_o = in ? St::rt(tx_o) : 0.f;
+            ty_e = in ? St::rt(ty_e) : 0.f;
+            ty_o = in ? St::rt(ty_o) : 0.f;
+
+            if (t >= r0) {
+                // d = div q^{k+1}, then p_s, p_t, u at row t
+                const float txl = __shfl_up_sync(full, tx_o, 1);  // new q_x at c-1
+                const float wy = row_w(t);
+                const float d_e = tx_e - txl + wy * ty_e - qyn_up.x;
+                const float d_o = mxo * tx_o - tx_e + wy * ty_o - qyn_up.y;
+                const float2 ps = PS::f2(a.ps), pt = PS::f2(a.pt);
+                float ps_e, pt_e, u_e, ps_o, pt_o, u_o;
+                binary_pu<S>(K, d_e, ps.x, pt.x, a.u.x, cs_t.x, ct_t.x, ps_e, pt_e, u_e);
+                binary_pu<S>(K, d_o, ps.y, pt.y, a.u.y, cs_t.y, ct_t.y, ps_o, pt_o, u_o);
+                if (own) {
+                    const int o = t * G.pitch + c;
+                    PS::st(s1.qx + o, tx_e, tx_o);
+                    PS::st(s1.qy + o, ty_e, ty_o);
+                    PS::st(s1.ps + o, ps_e, ps_o);
+                    PS::st(s1.pt + o, pt_e, pt_o);
+                    PF::st(s1.u + o, u_e, u_o);
+                }
+            }
+            qyn_up = make_float2(ty_e, ty_o);
+            a = b;
+            b = nx;
+            g_t = g_n;
+            al_t = al_n;
+            cs_t = cs_n;
+            ct_t = ct_n;
+        }
+    }
+}
+
+// ---- host side -------------------------------------------------------------
+
+bool binary_strip_eligible(const Grid& G, int storage, const float* Cs, const float* Ct,
+                           const float* alpha, const BinStateV& a, const BinStateV& b) {
+    if (G.W % 2 || G.pitch % 2) return false;
+    if ((size_t)G.H * (size_t)G.pitch > (size_t)INT_MAX) return false;
+    const size_t es2 = 2 * dtype_size(storage);
+    auto al = [](const void* p, size_t n) { return ((uintptr_t)p % n) == 0; };
+    if (!al(Cs, 8) || !al(Ct, 8) || (alpha && !al(alpha, 8))) return false;
+    for (const BinStateV* s : {&a, &b})
+        if (!al(s->u, 8) || !al(s->qx, es2) || !al(s->qy, es2) || !al(s->ps, es2) ||
+            !al(s->pt, es2))
+            return false;
+    return true;
+}
+
+template <typename S, bool ANISO>
+static cudaError_t launch_bin_strip(const BinProblem& P, const BinState<S>& a,
+                                    const BinState<S>& b, const AdmmCoef& K, cudaStream_t st) {
+    auto kern = k_binary_strip<S, ANISO>;
+    static int resident = 0;  // warps resident on the whole device
+    if (!resident) {
+        int dev = 0, sms = 0, blocks = 0;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
+                                                                0)) != cudaSuccess)
+            return e;
+        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    }
+    const Grid& G = P.g;
+    const int nstrips = (G.W + kStripOut - 1) / kStripOut;
+    const int R = strip::choose_rows(G.H, nstrips, resident, 4, 64, 3);
+    const int nitems = nstrips * ((G.H + R - 1) / R);
+    const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
+    const int grid = blocks < resident / kStripWarps ? blocks : resident / kStripWarps;
+    kern<<<grid, kStripWarps * 32, 0, st>>>(P, a, b, K, R, nstrips, nitems);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t bin_strip_s(const BinProblem& P, const BinStateV& a, const BinStateV& b,
+                               bool aniso, const AdmmCoef& K, cudaStream_t st) {
+    const BinState<S> A = a.as<S>(), B = b.as<S>();
+    return aniso ? launch_bin_strip<S, true>(P, A, B, K, st)
+                 : launch_bin_strip<S, false>(P, A, B, K, st);
+}
+
+cudaError_t binary_strip_step(int storage, const BinProblem& P, const BinStateV& a,
+                              const BinStateV& b, bool aniso, const AdmmCoef& K,
+                              cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return bin_strip_s<float>(P, a, b, aniso, K, st);
+        case CMF_F16: return bin_strip_s<__half>(P, a, b, aniso, K, st);
+        default: return bin_strip_s<__nv_bfloat16>(P, a, b, aniso, K, st);
+    }
+}
+
+}  // namespace cmf
+
+// ---- certificates by warp strips (Eq. seg:chanvese, Eq. two-label-mf) ------
+//
+// The same strips and bands as the iteration.  Per output pixel, in float32:
+// the primal energy at clip(u, 0, 1), the conservation residual of the flows
+// y (q for ADMM; q - tau grad u, p_t + tau u, p_s - tau u for rPDRQ) and the
+// max-flow value min(C_s, C_t + div P_alpha(y)).  Each row's pair is added to
+// per-lane FP64 sums; the block's sums go to partials[blockIdx.x].  The grid
+// has exactly eval_blocks(H, W) blocks so the partial count is the tile
+// kernel's.
+namespace cmf {
+
+template <typename S, bool ANISO, bool DR>
+__global__ void __launch_bounds__(kStripWarps * 32)
+    k_binary_eval_strip(BinProblem P, BinState<S> s, float tau, int R, int nstrips, int nitems,
+                        double* partials) {
+    using PS = Pair<S>;
+    using PF = Pair<float>;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const Grid G = P.g;
+    const unsigned full = 0xffffffffu;
+    double accE = 0.0, accD = 0.0, accR = 0.0;
+
+    for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
+         item += gridDim.x * kStripWarps) {
+        const int cs0 = (item % nstrips) * kStripOut;
+        const int r0 = (item / nstrips) * R;
+        const int r1 = min(r0 + R, G.H);
+        const int c = cs0 - 2 + 2 * lane;
+        const bool colin = c >= 0 && c < G.W;
+        const bool own = colin && lane >= 1 && lane <= 30;
+        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;
+        auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
+        auto ld_s = [&](const S* base, int r) {
+            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
+        };
+        auto ld_f = [&](const float* base, int r) {
+            return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
+        };
+        auto ld_al = [&](int r) {
+            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+            return ld_f(P.alpha.plane, r);
+        };
+        auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+        // flows y of row r (zero outside the grid) from q and, for rPDRQ, u of
+        // rows r and r+1; every lane takes part in the shuffle
+        auto flows = [&](int r, float2 u_r, float2 u_d, float2& f_x, float2& f_y) {
+            const float2 qx = ld_s(s.qx, r), qy = ld_s(s.qy, r);
+            const float u_right = __shfl_down_sync(full, u_r.x, 1);  // u(r, c+2)
+            f_x = qx;
+            f_y = qy;
+            if (DR) {
+                const float wy = row_w(r);
+                f_x.x -= tau * (u_r.y - u_r.x);
+                f_x.y -= tau * mxo * (u_right - u_r.y);
+                f_y.x -= tau * wy * (u_d.x - u_r.x);
+                f_y.y -= tau * wy * (u_d.y - u_r.y);
+            }
+            if (!ok_row(r)) f_x = f_y = make_float2(0.f, 0.f);
+        };
+
+        // row r0-1: its y flows and their projections enter the divergence at r0
+        float2 u_t = ld_f(s.u, r0 - 1), u_n = ld_f(s.u, r0);
+        float2 fx, fy;
+        flows(r0 - 1, u_t, u_n, fx, fy);
+        float2 al = ld_al(r0 - 1);
+        float2 fy_up = fy, py_up;
+        project_sel<ANISO>(fx.x, fy.x, al.x);
+        project_sel<ANISO>(fx.y, fy.y, al.y);
+        py_up = fy;
+        u_t = u_n;
+#pragma unroll 1
+        for (int t = r0; t < r1; ++t) {
+            u_n = ld_f(s.u, t + 1);
+            const float2 cs = ld_f(P.Cs, t), ct = ld_f(P.Ct, t);
+            float2 ps = ld_s(s.ps, t), pt = ld_s(s.pt, t);
+            al = ld_al(t);
+            flows(t, u_t, u_n, fx, fy);
+            const float wy = row_w(t);
+            // primal energy at ub = clip(u, 0, 1)
+            const float ub_e = fminf(fmaxf(u_t.x, 0.f), 1.f);
+            const float ub_o = fminf(fmaxf(u_t.y, 0.f), 1.f);
+            const float ub_r = __shfl_down_sync(full, ub_e, 1);
+            const float gx_e = ub_o - ub_e, gx_o = mxo * (ub_r - ub_o);
+            const float gy_e = wy * (fminf(fmaxf(u_n.x, 0.f), 1.f) - ub_e);
+            const float gy_o = wy * (fminf(fmaxf(u_n.y, 0.f), 1.f) - ub_o);
+            const float tv_e = ANISO ? fabsf(gx_e) + fabsf(gy_e) : sqrtf(gx_e * gx_e + gy_e * gy_e);
+            const float tv_o = ANISO ? fabsf(gx_o) + fabsf(gy_o) : sqrtf(gx_o * gx_o + gy_o * gy_o);
+            const float e_e = (1.f - ub_e) * cs.x + ub_e * ct.x + al.x * tv_e;
+            const float e_o = (1.f - ub_o) * cs.y + ub_o * ct.y + al.y * tv_o;
+            // conservation residual of y
+            if (DR) {
+                pt.x += tau * u_t.x;
+                pt.y += tau * u_t.y;
+                ps.x -= tau * u_t.x;
+                ps.y -= tau * u_t.y;
+            }
+            const float fxl = __shfl_up_sync(full, fx.y, 1);
+            const float r_e = fx.x - fxl + wy * fy.x - fy_up.x - ps.x + pt.x;
+            const float r_o = mxo * fx.y - fx.x + wy * fy.y - fy_up.y - ps.y + pt.y;
+            // max-flow value of P_alpha(y)
+            float px = fx.x, py = fy.x, qx_ = fx.y, qy_ = fy.y;
+            project_sel<ANISO>(px, py, al.x);
+            project_sel<ANISO>(qx_, qy_, al.y);
+            const float pxl = __shfl_up_sync(full, qx_, 1);
+            const float dp_e = px - pxl + wy * py - py_up.x;
+            const float dp_o = mxo * qx_ - px + wy * qy_ - py_up.y;
+            if (own) {
+                accE += (double)(e_e + e_o);
+                accR += (double)(r_e * r_e + r_o * r_o);
+                accD += (double)(fminf(cs.x, ct.x + dp_e) + fminf(cs.y, ct.y + dp_o));
+            }
+            fy_up = fy;
+            py_up = make_float2(py, qy_);
+            u_t = u_n;
+        }
+    }
+    // block sums, fixed order
+    __shared__ double red[3][kStripWarps];
+    accE = warp_sum(accE);
+    accD = warp_sum(accD);
+    accR = warp_sum(accR);
+    if (lane == 0) {
+        red[0][wib] = accE;
+        red[1][wib] = accD;
+        red[2][wib] = accR;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, cc = 0.0;
+        for (int w = 0; w < kStripWarps; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            cc += red[2][w];
+        }
+        double* out = partials + 3 * (size_t)blockIdx.x;
+        out[0] = a;
+        out[1] = b;
+        out[2] = cc;
+    }
+}
+
+template <typename S, bool ANISO, bool DR>
+static cudaError_t launch_bin_eval_strip(const BinProblem& P, const BinState<S>& s, float tau,
+                                         double* partials, cudaStream_t st) {
+    const Grid& G = P.g;
+    const int blocks = eval_blocks(G.H, G.W);
+    const int nstrips = (G.W + kStripOut - 1) / kStripOut;
+    const int R = strip::choose_rows(G.H, nstrips, (long long)blocks * kStripWarps, 4, 64, 2);
+    const int nitems = nstrips * ((G.H + R - 1) / R);
+    k_binary_eval_strip<S, ANISO, DR>
+        <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t bin_eval_strip_s(const BinProblem& P, const BinStateV& sv, bool aniso, bool dr,
+                                    float tau, double* partials, cudaStream_t st) {
+    const BinState<S> s = sv.as<S>();
+    if (dr)
+        return aniso ? launch_bin_eval_strip<S, true, true>(P, s, tau, partials, st)
+                     : launch_bin_eval_strip<S, false, true>(P, s, tau, partials, st);
+    return aniso ? launch_bin_eval_strip<S, true, false>(P, s, tau, partials, st)
+                 : launch_bin_eval_strip<S, false, false>(P, s, tau, partials, st);
+}
+
+cudaError_t binary_eval_strip(int storage, const BinProblem& P, const BinStateV& s, bool aniso,
+                              bool dr, float tau, double* partials, cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return bin_eval_strip_s<float>(P, s, aniso, dr, tau, partials, st);
+        case CMF_F16: return bin_eval_strip_s<__half>(P, s, aniso, dr, tau, partials, st);
+        default: return bin_eval_strip_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+    }
+}
+
+}  // namespace cmf

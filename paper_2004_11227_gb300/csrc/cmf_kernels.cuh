@@ -138,6 +138,16 @@ cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s,
 cudaError_t halfsweeps(const Grid& G, float* u, const float* b, const DrCoef& D,
                        cudaStream_t st);
 
+// --- warp-strip binary ADMM (cmf_binary_strip.cu) ---
+bool binary_strip_eligible(const Grid& G, int storage, const float* Cs, const float* Ct,
+                           const float* alpha, const BinStateV& a, const BinStateV& b);
+cudaError_t binary_strip_step(int storage, const BinProblem& P, const BinStateV& a,
+                              const BinStateV& b, bool aniso, const AdmmCoef& K,
+                              cudaStream_t st);
+// Certificates of a strip-eligible state into eval_blocks(H, W) partials.
+cudaError_t binary_eval_strip(int storage, const BinProblem& P, const BinStateV& s, bool aniso,
+                              bool dr, float tau, double* partials, cudaStream_t st);
+
 // --- warp-strip Potts ADMM (cmf_potts_strip.cu) ---
 // Eligible: even W and pitch, H * pitch within int, pair-aligned planes.
 bool potts_strip_eligible(const Grid& G, int storage, const float* C, const float* alpha,

@@ -21,71 +21,19 @@
 #include <climits>
 
 #include "cmf_kernels.cuh"
+#include "cmf_strip.cuh"
 
 namespace cmf {
 
+using strip::kStripOut;
+using strip::kStripWarps;
+using strip::Pair;
+using strip::project_sel;
+
 namespace {
 
-constexpr int kStripOut = 60;   // output columns per warp strip
-constexpr int kStripWarps = 4;  // warps per block
 constexpr int kStripRmax = 24;  // band rows at most (shared accumulators: 24 KB per
                                 // block, so seven blocks of 72 registers fit an SM)
-
-// Two adjacent elements of a plane: raw pair type and conversions.
-template <typename S>
-struct Pair;
-template <>
-struct Pair<float> {
-    using T = float2;
-    static __device__ __forceinline__ T ld(const float* p) {
-        return __ldg(reinterpret_cast<const float2*>(p));
-    }
-    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
-    static __device__ __forceinline__ float2 f2(T v) { return v; }
-    static __device__ __forceinline__ void st(float* p, float a, float b) {
-        *reinterpret_cast<float2*>(p) = make_float2(a, b);
-    }
-};
-template <>
-struct Pair<__half> {
-    using T = __half2;
-    static __device__ __forceinline__ T ld(const __half* p) {
-        return __ldg(reinterpret_cast<const __half2*>(p));
-    }
-    static __device__ __forceinline__ T zero() { return __float2half2_rn(0.f); }
-    static __device__ __forceinline__ float2 f2(T v) { return __half22float2(v); }
-    static __device__ __forceinline__ void st(__half* p, float a, float b) {
-        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
-    }
-};
-template <>
-struct Pair<__nv_bfloat16> {
-    using T = __nv_bfloat162;
-    static __device__ __forceinline__ T ld(const __nv_bfloat16* p) {
-        return __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
-    }
-    static __device__ __forceinline__ T zero() { return __float2bfloat162_rn(0.f); }
-    static __device__ __forceinline__ float2 f2(T v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
-    }
-};
-
-// P_alpha without a branch (Eq. projections): the scale is selected, so the
-// reciprocal square root of a zero norm is computed and discarded.
-template <bool ANISO>
-__device__ __forceinline__ void project_sel(float& x, float& y, float al) {
-    al = fmaxf(al, 0.0f);
-    if (ANISO) {
-        x = fminf(fmaxf(x, -al), al);
-        y = fminf(fmaxf(y, -al), al);
-    } else {
-        const float n2 = x * x + y * y;
-        const float s = n2 > al * al ? al * rsqrtf(n2) : 1.0f;
-        x *= s;
-        y *= s;
-    }
-}
 
 // State values of one row of one label at this lane's column pair.
 template <typename S>
@@ -316,17 +264,7 @@ static cudaError_t launch_strip(const PottsProblem& P, const PottsState<S>& a,
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
     // band height: fewest rounds of work items over the resident warps, each
     // round costing R + 3 rows (the band plus its halo rows)
-    int best_r = kStripRmax;
-    long long best_cost = -1;
-    for (int r = 8; r <= kStripRmax; ++r) {
-        const long long items = (long long)nstrips * ((G.H + r - 1) / r);
-        const long long rounds = (items + resident - 1) / resident;
-        const long long cost = rounds * (r + 3);
-        if (best_cost < 0 || cost <= best_cost) {
-            best_cost = cost;
-            best_r = r;
-        }
-    }
+    const int best_r = strip::choose_rows(G.H, nstrips, resident, 8, kStripRmax, 3);
     const int nitems = nstrips * ((G.H + best_r - 1) / best_r);
     const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
     const int grid = blocks < resident / kStripWarps ? blocks : resident / kStripWarps;

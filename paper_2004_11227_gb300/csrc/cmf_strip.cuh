@@ -1,0 +1,88 @@
+// Shared pieces of the warp-strip kernels (cmf_potts_strip.cu,
+// cmf_binary_strip.cu): a warp owns a strip of 64 columns, two adjacent
+// columns per lane, and streams down a band of rows.
+#pragma once
+
+#include "cmf_common.cuh"
+
+namespace cmf {
+namespace strip {
+
+constexpr int kStripOut = 60;   // output columns per warp strip
+constexpr int kStripWarps = 4;  // warps per block
+
+// Two adjacent elements of a plane: raw pair type and conversions.
+template <typename S>
+struct Pair;
+template <>
+struct Pair<float> {
+    using T = float2;
+    static __device__ __forceinline__ T ld(const float* p) {
+        return __ldg(reinterpret_cast<const float2*>(p));
+    }
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ float2 f2(T v) { return v; }
+    static __device__ __forceinline__ void st(float* p, float a, float b) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+};
+template <>
+struct Pair<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ T ld(const __half* p) {
+        return __ldg(reinterpret_cast<const __half2*>(p));
+    }
+    static __device__ __forceinline__ T zero() { return __float2half2_rn(0.f); }
+    static __device__ __forceinline__ float2 f2(T v) { return __half22float2(v); }
+    static __device__ __forceinline__ void st(__half* p, float a, float b) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ T ld(const __nv_bfloat16* p) {
+        return __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    static __device__ __forceinline__ T zero() { return __float2bfloat162_rn(0.f); }
+    static __device__ __forceinline__ float2 f2(T v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// P_alpha without a branch (Eq. projections): the scale is selected, so the
+// reciprocal square root of a zero norm is computed and discarded.
+template <bool ANISO>
+__device__ __forceinline__ void project_sel(float& x, float& y, float al) {
+    al = fmaxf(al, 0.0f);
+    if (ANISO) {
+        x = fminf(fmaxf(x, -al), al);
+        y = fminf(fmaxf(y, -al), al);
+    } else {
+        const float n2 = x * x + y * y;
+        const float s = n2 > al * al ? al * rsqrtf(n2) : 1.0f;
+        x *= s;
+        y *= s;
+    }
+}
+
+// Band height for a grid: the fewest rounds of work items over the resident
+// warps, each round costing its rows plus `halo` rows; ties go to taller bands.
+inline int choose_rows(int H, int nstrips, long long resident, int rmin, int rmax, int halo) {
+    int best_r = rmax;
+    long long best_cost = -1;
+    for (int r = rmin; r <= rmax; ++r) {
+        const long long items = (long long)nstrips * ((H + r - 1) / r);
+        const long long rounds = (items + resident - 1) / resident;
+        const long long cost = rounds * (r + halo);
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best_r = r;
+        }
+    }
+    return best_r;
+}
+
+}  // namespace strip
+}  // namespace cmf

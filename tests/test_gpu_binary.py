@@ -88,9 +88,12 @@ def test_fused_equals_plain(cmf, algo):
         assert np.abs(a[k] - b[k]).max() <= 1e-5, k
 
 
+@pytest.mark.parametrize("shape", [(70, 90), (70, 91), (1, 64), (131, 2), (300, 250)])
 @pytest.mark.parametrize("algo", ALGOS)
-def test_certificates_match_oracle(cmf, algo):
-    inst = synth.config2(70, 90)
+def test_certificates_match_oracle(cmf, algo, shape):
+    """Even widths go through the warp-strip certificate kernel, odd ones
+    through the tile kernel; both against the oracle's evaluation."""
+    inst = synth.config2(*shape)
     b = _gpu_run(cmf, inst, algo, 25)
     E, D, gap, res = cmf.cmf_eval_binary(b)
     st = b.state()
@@ -160,12 +163,12 @@ def test_warm_start_split_equals_single_run(cmf):
         np.testing.assert_array_equal(a[k], s[k])
 
 
-def _window_step_check(cmf, inst, algo, k_before, windows, margin=8):
+def _window_step_check(cmf, inst, algo, k_before, windows, margin=8, variant=0):
     """Full-size state: GPU runs k_before iterations, then one more; the
     oracle runs that last iteration on cropped windows (with a margin that
     covers the iteration's stencil reach) and the window interiors must
     match element by element."""
-    p = cmf.default_params(algo, 2)
+    p = cmf.default_params(algo, 2, variant=variant)
     b = cmf.alloc_binary(inst, p)
     cmf.cmf_init_binary(b)
     cmf.cmf_iterate_binary(b, k_before)
@@ -263,3 +266,109 @@ def test_autotune_picks_a_converging_configuration(cmf, tmp_path):
         b2 = cmf.alloc_binary(inst, q)
         st, it, hist = cmf.cmf_solve_binary(b2)
         assert st == cmf.OK
+
+
+# ---- warp-strip kernel (variant 2) ---------------------------------------------
+
+STRIP_CASES = {
+    "disk64": (synth.config1(), 200),
+    "shapes37x54": (synth.config2(37, 54), 60),
+    "row1x68": (synth.random_binary(1, 68, seed=3, alpha=0.3), 40),
+    "col45x2": (synth.random_binary(45, 2, seed=4, alpha=0.3), 40),
+    "ragged70x130": (synth.random_binary(70, 130, seed=6, alpha=0.4, field_alpha=True), 51),
+    "tall301x62": (synth.random_binary(301, 62, seed=7, alpha=0.3, field_alpha=True), 17),
+}
+
+
+@pytest.mark.parametrize("algo", [0, 1, 2, 4])
+@pytest.mark.parametrize("case", list(STRIP_CASES))
+def test_strip_matches_oracle_f32(cmf, case, algo):
+    inst, n = STRIP_CASES[case]
+    b = _gpu_run(cmf, inst, algo, n, variant=2)
+    got = b.state()
+    ref, _ = _oracle_run(inst, algo, n)
+    for k in ("u", "qx", "qy", "ps", "pt"):
+        err = np.abs(got[k] - ref[k]).max()
+        assert err <= TOL_U, (k, err)
+
+
+@pytest.mark.parametrize("algo", [1, 2])
+def test_strip_anisotropic(cmf, algo):
+    inst = synth.random_binary(41, 36, seed=8, alpha=0.3, field_alpha=True)
+    b = _gpu_run(cmf, inst, algo, 40, aniso=1, variant=2)
+    ref, _ = _oracle_run(inst, algo, 40, aniso=1)
+    assert np.abs(b.state()["u"] - ref["u"]).max() <= TOL_U
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("shape", [(70, 98), (5, 130), (130, 6)])
+def test_strip_matches_smem_tiles_half(cmf, storage, shape):
+    inst = synth.random_binary(*shape, seed=91, alpha=0.3, field_alpha=True)
+    for algo in (0, 2):
+        a = _gpu_run(cmf, inst, algo, 9, storage=storage, variant=1).state()
+        b = _gpu_run(cmf, inst, algo, 9, storage=storage, variant=2).state()
+        for k in a:
+            assert np.abs(a[k] - b[k]).max() <= 1e-2, k
+
+
+def test_strip_rejects_odd_width(cmf):
+    inst = synth.random_binary(20, 33, seed=9, alpha=0.3)
+    p = cmf.default_params(2, 2, variant=2)
+    b = cmf.alloc_binary(inst, p)
+    with pytest.raises(cmf.CmfError):
+        cmf.cmf_iterate_binary(b, 2)
+
+
+@pytest.mark.parametrize("algo", [1, 2])
+def test_strip_full_size_1024_windows(cmf, algo):
+    inst = synth.config2()
+    wins = [(0, 0, 48, 48), (0, 1024 - 40, 40, 40), (1024 - 33, 0, 33, 64),
+            (1024 - 50, 1024 - 50, 50, 50), (500, 500, 64, 64), (257, 771, 31, 45)]
+    _window_step_check(cmf, inst, algo, 37, wins, variant=2)
+
+
+def test_strip_matches_tma_full_size_1024(cmf):
+    inst = synth.config2()
+    a = _gpu_run(cmf, inst, 2, 6, variant=16)
+    b = _gpu_run(cmf, inst, 2, 6, variant=2)
+    for k in ("u", "qx", "qy", "ps", "pt"):
+        err = (getattr(a, k).float() - getattr(b, k).float()).abs().max().item()
+        assert err <= 1e-5, (k, err)
+
+
+def test_strip_solve_certified(cmf):
+    inst = synth.config2(256, 256)
+    p = cmf.default_params(2, 2, tol_gap=1e-4, max_iter=20000, check_every=10, variant=2)
+    b = cmf.alloc_binary(inst, p)
+    status, iters, hist = cmf.cmf_solve_binary(b)
+    assert status == cmf.OK and hist[-1, 3] <= 1e-4
+    st = b.state()
+    E, D, gap, res = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, st,
+                                   O.default_params(2, 2))
+    assert gap <= 1.01e-4
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("algo", [2, 3])
+def test_strip_certificates_half_storage(cmf, storage, algo):
+    inst = synth.config2(64, 96)
+    b = _gpu_run(cmf, inst, algo, 25, storage=storage)
+    E, D, gap, res = cmf.cmf_eval_binary(b)
+    Eo, Do, gapo, reso = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, b.state(),
+                                       O.default_params(algo, 2))
+    assert abs(E - Eo) <= 1e-5 * abs(Eo)
+    assert abs(D - Do) <= 1e-5 * abs(Eo)
+
+
+@pytest.mark.parametrize("aniso", [0, 1])
+def test_strip_certificates_full_size(cmf, aniso):
+    """1024^2 state after some iterations: strip certificates against the
+    oracle's evaluation of the same state (FP64, whole grid)."""
+    inst = synth.config2()
+    b = _gpu_run(cmf, inst, 2, 30, aniso=aniso)
+    E, D, gap, res = cmf.cmf_eval_binary(b)
+    Eo, Do, gapo, reso = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, b.state(),
+                                       O.default_params(2, 2, aniso=aniso))
+    assert abs(E - Eo) <= 1e-6 * abs(Eo)
+    assert abs(D - Do) <= 1e-6 * abs(Eo)
+    assert abs(res - reso) <= 1e-5 * reso + 1e-6
