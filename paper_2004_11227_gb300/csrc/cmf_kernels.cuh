@@ -157,6 +157,9 @@ bool potts_strip_eligible(const Grid& G, int storage, const float* C, const floa
 cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
                              const PottsStateV& b, bool aniso, const AdmmCoef& K, float cu_in,
                              cudaStream_t st);
+// Certificates of a strip-eligible state into eval_blocks(H, W) partials.
+cudaError_t potts_eval_strip(int storage, const PottsProblem& P, const PottsStateV& s,
+                             bool aniso, bool dr, float tau, double* partials, cudaStream_t st);
 // s.u_i += cu * s.p_s on every label (w back to u).
 cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const PottsStateV& s,
                                  float cu, cudaStream_t st);

@@ -681,6 +681,8 @@ static cudaError_t potts_eval_s(const PottsProblem& P, const PottsStateV& sv, bo
 
 cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s, bool aniso,
                        bool dr, float tau, double* partials, cudaStream_t st) {
+    if (potts_strip_eligible(P.g, storage, P.C, P.alpha.plane, s, s))
+        return potts_eval_strip(storage, P, s, aniso, dr, tau, partials, st);
     switch (storage) {
         case CMF_F32: return potts_eval_s<float>(P, s, aniso, dr, tau, partials, st);
         case CMF_F16: return potts_eval_s<__half>(P, s, aniso, dr, tau, partials, st);

@@ -311,4 +311,254 @@ cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const Potts
     return cudaGetLastError();
 }
 
+// ---- certificates by warp strips (Eq. relaxed-potts, Eq. potts-mf) ---------
+//
+// Same strips as the iteration, bands of at most kEvalRmax rows.  Phase 1
+// walks the band's rows (and the row below) once over all labels: the simplex
+// threshold theta of every pixel (Michelot's active-set iteration, as in the
+// tile kernel) and, for rPDRQ, sum_i u_i; both go to shared memory.  Phase 2
+// walks the labels, streaming each label down the band: the primal energy at
+// max(u_i - theta, 0), the conservation residual of the flows y and the
+// running minimum over labels of C_i + div P_alpha(y_i) (shared memory).  Sums
+// are FP64 per lane, then per block into partials[blockIdx.x]; the grid has
+// eval_blocks(H, W) blocks, the tile kernel's partial count.
+namespace {
+constexpr int kEvalRmax = 15;  // 4 warps x (16 + 15 + 15) rows x 256 B = 46 KB static
+}  // namespace
+
+template <typename S, bool ANISO, bool DR>
+__global__ void __launch_bounds__(kStripWarps * 32)
+    k_potts_eval_strip(PottsProblem P, PottsState<S> s, float tau, int R, int nstrips,
+                       int nitems, double* partials) {
+    using PS = Pair<S>;
+    using PF = Pair<float>;
+    __shared__ float2 th_s[kStripWarps][kEvalRmax + 1][32];
+    __shared__ float2 us_s[kStripWarps][kEvalRmax][32];
+    __shared__ float2 dm_s[kStripWarps][kEvalRmax][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const Grid G = P.g;
+    const int L = P.L;
+    const unsigned full = 0xffffffffu;
+    double accE = 0.0, accD = 0.0, accR = 0.0;
+
+    for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
+         item += gridDim.x * kStripWarps) {
+        const int cs0 = (item % nstrips) * kStripOut;
+        const int r0 = (item / nstrips) * R;
+        const int r1 = min(r0 + R, G.H);
+        const int c = cs0 - 2 + 2 * lane;
+        const bool colin = c >= 0 && c < G.W;
+        const bool own = colin && lane >= 1 && lane <= 30;
+        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;
+        auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
+        auto ld_s = [&](const S* base, int r) {
+            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
+        };
+        auto ld_f = [&](const float* base, int r) {
+            return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
+        };
+        auto ld_al = [&](int r) {
+            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+            return ld_f(P.alpha.plane, r);
+        };
+        auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+
+        // phase 1: theta of rows r0 .. r1 (the row below the band enters the
+        // y differences of row r1-1), sum_i u_i of the band's rows
+        for (int t = r0; t <= r1; ++t) {
+            float2 th = make_float2(0.f, 0.f), us = make_float2(0.f, 0.f);
+            if (ok_row(t)) {
+                const float* ub = s.u + t * G.pitch + c;
+                float sx = 0.f, sy = 0.f;
+                for (int l = 0; l < L; ++l) {
+                    const float2 v = PF::ld(ub + (size_t)l * G.plane);
+                    sx += v.x;
+                    sy += v.y;
+                }
+                us = make_float2(sx, sy);
+                // Michelot: drop entries <= theta, theta = (sum_active - 1) / n
+                unsigned long long ax = L >= 64 ? ~0ull : ((1ull << L) - 1ull), ay = ax;
+                int nx = L, ny = L;
+                float tx = (sx - 1.f) / (float)nx, ty = (sy - 1.f) / (float)ny;
+                bool run_x = true, run_y = true;
+                for (int it = 0; it < L && (run_x || run_y); ++it) {
+                    bool chx = false, chy = false;
+                    for (int l = 0; l < L; ++l) {
+                        const float2 v = PF::ld(ub + (size_t)l * G.plane);
+                        if (run_x && ((ax >> l) & 1ull) && v.x <= tx) {
+                            ax &= ~(1ull << l);
+                            sx -= v.x;
+                            --nx;
+                            chx = true;
+                        }
+                        if (run_y && ((ay >> l) & 1ull) && v.y <= ty) {
+                            ay &= ~(1ull << l);
+                            sy -= v.y;
+                            --ny;
+                            chy = true;
+                        }
+                    }
+                    if (run_x) {
+                        if (!chx || nx == 0) run_x = false;
+                        else tx = (sx - 1.f) / (float)nx;
+                    }
+                    if (run_y) {
+                        if (!chy || ny == 0) run_y = false;
+                        else ty = (sy - 1.f) / (float)ny;
+                    }
+                }
+                th = make_float2(tx, ty);
+            }
+            th_s[wib][t - r0][lane] = th;
+            if (t < r1) us_s[wib][t - r0][lane] = us;
+        }
+        __syncwarp();
+
+        // phase 2: per label, stream down the band
+        for (int l = 0; l < L; ++l) {
+            const size_t lo = (size_t)l * G.plane;
+            const float* ul = s.u + lo;
+            const S* qxl = s.qx + lo;
+            const S* qyl = s.qy + lo;
+            // flows y of row r (zero outside the grid); every lane shuffles
+            auto flows = [&](int r, float2 u_r, float2 u_d, float2& f_x, float2& f_y) {
+                f_x = ld_s(qxl, r);
+                f_y = ld_s(qyl, r);
+                const float u_right = __shfl_down_sync(full, u_r.x, 1);
+                if (DR) {
+                    const float wy = row_w(r);
+                    f_x.x -= tau * (u_r.y - u_r.x);
+                    f_x.y -= tau * mxo * (u_right - u_r.y);
+                    f_y.x -= tau * wy * (u_d.x - u_r.x);
+                    f_y.y -= tau * wy * (u_d.y - u_r.y);
+                }
+                if (!ok_row(r)) f_x = f_y = make_float2(0.f, 0.f);
+            };
+            float2 u_t = ld_f(ul, r0 - 1), u_n = ld_f(ul, r0);
+            float2 fx, fy;
+            flows(r0 - 1, u_t, u_n, fx, fy);
+            float2 al = ld_al(r0 - 1);
+            float2 fy_up = fy, py_up;
+            project_sel<ANISO>(fx.x, fy.x, al.x);
+            project_sel<ANISO>(fx.y, fy.y, al.y);
+            py_up = fy;
+            u_t = u_n;
+            float2 th_t = th_s[wib][0][lane];
+            for (int t = r0; t < r1; ++t) {
+                u_n = ld_f(ul, t + 1);
+                const float2 th_n = th_s[wib][t + 1 - r0][lane];
+                const float2 Cl = ld_f(P.C + lo, t);
+                float2 fp = ld_s(s.p + lo, t), fs = ld_s(s.ps, t);
+                al = ld_al(t);
+                flows(t, u_t, u_n, fx, fy);
+                const float wy = row_w(t);
+                // primal energy at ub_i = max(u_i - theta, 0)
+                const float ub_e = fmaxf(u_t.x - th_t.x, 0.f);
+                const float ub_o = fmaxf(u_t.y - th_t.y, 0.f);
+                const float ub_r = __shfl_down_sync(full, ub_e, 1);
+                const float gx_e = ub_o - ub_e, gx_o = mxo * (ub_r - ub_o);
+                const float gy_e = wy * (fmaxf(u_n.x - th_n.x, 0.f) - ub_e);
+                const float gy_o = wy * (fmaxf(u_n.y - th_n.y, 0.f) - ub_o);
+                const float tv_e =
+                    ANISO ? fabsf(gx_e) + fabsf(gy_e) : sqrtf(gx_e * gx_e + gy_e * gy_e);
+                const float tv_o =
+                    ANISO ? fabsf(gx_o) + fabsf(gy_o) : sqrtf(gx_o * gx_o + gy_o * gy_o);
+                const float e = (ub_e * Cl.x + al.x * tv_e) + (ub_o * Cl.y + al.y * tv_o);
+                // conservation residual of y
+                if (DR) {
+                    const float2 us = us_s[wib][t - r0][lane];
+                    fp.x += tau * u_t.x;
+                    fp.y += tau * u_t.y;
+                    fs.x -= tau * us.x;
+                    fs.y -= tau * us.y;
+                }
+                const float fxl = __shfl_up_sync(full, fx.y, 1);
+                const float r_e = fx.x - fxl + wy * fy.x - fy_up.x - fs.x + fp.x;
+                const float r_o = mxo * fx.y - fx.x + wy * fy.y - fy_up.y - fs.y + fp.y;
+                // C_i + div P_alpha(y_i), running minimum over the labels
+                float px = fx.x, py = fy.x, qx_ = fx.y, qy_ = fy.y;
+                project_sel<ANISO>(px, py, al.x);
+                project_sel<ANISO>(qx_, qy_, al.y);
+                const float pxl = __shfl_up_sync(full, qx_, 1);
+                const float dp_e = px - pxl + wy * py - py_up.x;
+                const float dp_o = mxo * qx_ - px + wy * qy_ - py_up.y;
+                float2& dm = dm_s[wib][t - r0][lane];
+                const float2 cand = make_float2(Cl.x + dp_e, Cl.y + dp_o);
+                dm = l == 0 ? cand : make_float2(fminf(dm.x, cand.x), fminf(dm.y, cand.y));
+                if (own) {
+                    accE += (double)e;
+                    accR += (double)(r_e * r_e + r_o * r_o);
+                }
+                fy_up = fy;
+                py_up = make_float2(py, qy_);
+                u_t = u_n;
+                th_t = th_n;
+            }
+        }
+        if (own)
+            for (int t = r0; t < r1; ++t) {
+                const float2 dm = dm_s[wib][t - r0][lane];
+                accD += (double)(dm.x + dm.y);
+            }
+        __syncwarp();
+    }
+    __shared__ double red[3][kStripWarps];
+    accE = warp_sum(accE);
+    accD = warp_sum(accD);
+    accR = warp_sum(accR);
+    if (lane == 0) {
+        red[0][wib] = accE;
+        red[1][wib] = accD;
+        red[2][wib] = accR;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, cc = 0.0;
+        for (int w = 0; w < kStripWarps; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            cc += red[2][w];
+        }
+        double* out = partials + 3 * (size_t)blockIdx.x;
+        out[0] = a;
+        out[1] = b;
+        out[2] = cc;
+    }
+}
+
+template <typename S, bool ANISO, bool DR>
+static cudaError_t launch_potts_eval_strip(const PottsProblem& P, const PottsState<S>& s,
+                                           float tau, double* partials, cudaStream_t st) {
+    const Grid& G = P.g;
+    const int blocks = eval_blocks(G.H, G.W);
+    const int nstrips = (G.W + kStripOut - 1) / kStripOut;
+    const int R = strip::choose_rows(G.H, nstrips, (long long)blocks * kStripWarps, 4,
+                                     kEvalRmax, 2);
+    const int nitems = nstrips * ((G.H + R - 1) / R);
+    k_potts_eval_strip<S, ANISO, DR>
+        <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials);
+    return cudaGetLastError();
+}
+
+template <typename S>
+static cudaError_t potts_eval_strip_s(const PottsProblem& P, const PottsStateV& sv, bool aniso,
+                                      bool dr, float tau, double* partials, cudaStream_t st) {
+    const PottsState<S> s = sv.as<S>();
+    if (dr)
+        return aniso ? launch_potts_eval_strip<S, true, true>(P, s, tau, partials, st)
+                     : launch_potts_eval_strip<S, false, true>(P, s, tau, partials, st);
+    return aniso ? launch_potts_eval_strip<S, true, false>(P, s, tau, partials, st)
+                 : launch_potts_eval_strip<S, false, false>(P, s, tau, partials, st);
+}
+
+cudaError_t potts_eval_strip(int storage, const PottsProblem& P, const PottsStateV& s,
+                             bool aniso, bool dr, float tau, double* partials,
+                             cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return potts_eval_strip_s<float>(P, s, aniso, dr, tau, partials, st);
+        case CMF_F16: return potts_eval_strip_s<__half>(P, s, aniso, dr, tau, partials, st);
+        default: return potts_eval_strip_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+    }
+}
+
 }  // namespace cmf

@@ -81,9 +81,12 @@ def test_anisotropic_and_multisweep(cmf, algo):
         assert np.abs(s.state()["u"] - ref["u"]).max() <= TOL_U
 
 
+@pytest.mark.parametrize("shape", [(64, 72), (64, 71), (1, 64), (131, 2), (300, 250)])
 @pytest.mark.parametrize("algo", ALGOS)
-def test_certificates_match_oracle(cmf, algo):
-    inst = synth.config3(64, 72)
+def test_certificates_match_oracle(cmf, algo, shape):
+    """Even widths go through the warp-strip certificate kernel, odd ones
+    through the tile kernel; both against the oracle's evaluation."""
+    inst = synth.config3(*shape)
     s = _gpu_run(cmf, inst, algo, 25)
     E, D, gap, res = cmf.cmf_eval_potts(s)
     st = s.state()
@@ -318,3 +321,36 @@ def test_strip_solve_certified(cmf, use_graph):
     assert status == cmf.OK and hist[-1, 3] <= 1e-4
     E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, s.state(), O.default_params(2, 4))
     assert gap <= 1.01e-4
+
+
+@pytest.mark.parametrize("aniso", [0, 1])
+@pytest.mark.parametrize("algo", [2, 3])
+def test_strip_certificates_many_labels(cmf, algo, aniso):
+    inst = synth.config5(70, 96)
+    s = _gpu_run(cmf, inst, algo, 20, aniso=aniso)
+    E, D, gap, res = cmf.cmf_eval_potts(s)
+    Eo, Do, gapo, reso = O.potts_eval(inst.costs, inst.alpha, s.state(),
+                                      O.default_params(algo, 16, aniso=aniso))
+    assert abs(E - Eo) <= 1e-5 * abs(Eo)
+    assert abs(D - Do) <= 1e-5 * abs(Eo)
+    assert abs(res - reso) <= 1e-4 * reso + 1e-6
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_strip_certificates_half_storage(cmf, storage):
+    inst = synth.config3(64, 96)
+    s = _gpu_run(cmf, inst, 2, 25, storage=storage)
+    E, D, gap, res = cmf.cmf_eval_potts(s)
+    Eo, Do, gapo, reso = O.potts_eval(inst.costs, inst.alpha, s.state(), O.default_params(2, 4))
+    assert abs(E - Eo) <= 1e-5 * abs(Eo)
+    assert abs(D - Do) <= 1e-5 * abs(Eo)
+
+
+def test_strip_certificates_full_size_2048_L4(cmf):
+    inst = synth.config3()
+    s = _gpu_run(cmf, inst, 2, 30)
+    E, D, gap, res = cmf.cmf_eval_potts(s)
+    Eo, Do, gapo, reso = O.potts_eval(inst.costs, inst.alpha, s.state(), O.default_params(2, 4))
+    assert abs(E - Eo) <= 1e-6 * abs(Eo)
+    assert abs(D - Do) <= 1e-6 * abs(Eo)
+    assert abs(res - reso) <= 1e-5 * reso + 1e-6
