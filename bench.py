@@ -195,12 +195,15 @@ def potts_workloads(cmf, synth, flush) -> dict:
 
     peak, _ = _peaks()
     out = {}
-    # (the 4096^2 solve is capped at 1000 iterations; see --precision-study
-    # for its convergence in float32 / float16 / bfloat16 storage)
-    cases = [("potts L=4 2048x2048 float32, alpha 0.3", lambda: synth.config3(), 0, 20000),
+    # The 4096^2 float16 solve is capped at 1000 iterations: with 16-bit flow
+    # storage this workload's certified gap stalls near 1e-3 (--precision-study);
+    # the same workload with float32 flows is then solved to the 1e-4 gap.
+    cases = [("potts L=4 2048x2048 float32, alpha 0.3", lambda: synth.config3(), 0, 20000, True),
              ("potts L=16 4096x4096 float16 flows, edge-weighted alpha", lambda: synth.config5(),
-              1, 1000)]
-    for name, make, storage, max_iter in cases:
+              1, 1000, True),
+             ("potts L=16 4096x4096 float32 flows, edge-weighted alpha", lambda: synth.config5(),
+              0, 6000, False)]
+    for name, make, storage, max_iter, warm in cases:
         inst = make()
         p = cmf.default_params(2, inst.L, storage=storage, tol_gap=1e-4, max_iter=max_iter,
                                check_every=10)
@@ -218,7 +221,8 @@ def potts_workloads(cmf, synth, flush) -> dict:
         ms = e0.elapsed_time(e1) / n
         nb = algorithmic_bytes_per_px("potts", inst.L, storage,
                                       isinstance(inst.alpha, np.ndarray)) * inst.H * inst.W
-        cmf.cmf_solve_potts(s)  # warm
+        if warm:
+            cmf.cmf_solve_potts(s)
         flush.zero_()
         torch.cuda.synchronize()
         e0.record()
