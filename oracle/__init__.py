@@ -9,7 +9,8 @@ Algorithm codes: 0 pADMMI (Fortin-Glowinski with r = 1), 1 rpADMMI
 (Fortin-Glowinski, Eq. rpADMMI), 2 rpADMMII (Eckstein-Bertsekas, Eq. rpADMMII),
 3 rPDRQ (preconditioned Douglas-Rachford, Eq. iteration:quadratic:seg /
 Eq. pdrq:4labels), 4 pADMM-TY (the classical multi-block ADMM, Eq. ADMM:Tai_yuan /
-Eq. mADMM:Tai_yuan).
+Eq. mADMM:Tai_yuan), 5 ALG1 (the Chambolle-Pock primal-dual method of the
+Appendix, Eq. iteration:pd:seg / Eq. alg1:4labels).
 """
 from __future__ import annotations
 
@@ -19,9 +20,9 @@ import subprocess
 
 import numpy as np
 
-PADMM, RPADMM_FG, RPADMM_EB, RPDRQ, TY = 0, 1, 2, 3, 4
+PADMM, RPADMM_FG, RPADMM_EB, RPDRQ, TY, CP = 0, 1, 2, 3, 4, 5
 ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ",
-              TY: "pADMM-TY"}
+              TY: "pADMM-TY", CP: "ALG1"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cmf_oracle.c")
@@ -41,10 +42,14 @@ class Params(ctypes.Structure):
 def default_params(algo: int, L: int = 2, **kw) -> Params:
     """The paper's settings (Sec. 4): c = 0.3, a = 8, a~ = a_1 = 2, a_2 = 2L,
     rho = 1.9, r = 1.618; rPDRQ sigma = 0.2, tau = 1.0 (two labels) or
-    sigma = 5, tau = 0.4 (Potts); one sRBGS sweep."""
+    sigma = 5, tau = 0.4 (Potts); ALG1 sigma = 0.4, tau = 1/(L'^2 sigma) with
+    L'^2 = 10 (two labels) or 9 + L; one sRBGS sweep."""
+    sigma, tau = (0.2, 1.0) if L == 2 else (5.0, 0.4)
+    if algo == CP:
+        sigma = 0.4
+        tau = 1.0 / ((10.0 if L == 2 else 9.0 + L) * sigma)
     p = Params(algo=algo, aniso=0, sweeps=1, literal_potts_u=0, c=0.3, a=8.0, a1=2.0,
-               a2=2.0 * L, rho=1.9, r=1.618,
-               sigma=0.2 if L == 2 else 5.0, tau=1.0 if L == 2 else 0.4)
+               a2=2.0 * L, rho=1.9, r=1.618, sigma=sigma, tau=tau)
     for k, v in kw.items():
         setattr(p, k, v)
     return p

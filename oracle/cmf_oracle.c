@@ -30,6 +30,12 @@
  *    Potts rPDRQ (Eq. pdrq:4labels).
  *  - Potts a2 = 2L (Eq. multilabel:pre:p); rPDRQ for general L uses
  *    (L-1) in b_i and T_0 = -Lap + (L+1) I (Lemma 1).
+ *  - ALG1 (Chambolle-Pock, Appendix): the binary p_s step adds +sigma (prox
+ *    of -sigma<1,p_s>, as in its Potts form); the Potts q_i step uses the
+ *    extrapolated ubar_i of the general scheme (Eq. alg:pd), not u_i.  The
+ *    state between calls is (u, q, p); a run recovers ubar^k = 2u^k - u^{k-1}
+ *    from u^k - u^{k-1} = -tau (div q + p_t - p_s)^k, which its own
+ *    multiplier step makes exact.
  *  - Cold start (the paper gives none): the alpha = 0 saddle point, i.e.
  *    q = 0, p = min cost, u = indicator of the cheapest label; rPDRQ holds
  *    ybar = y - tau K u of that point.
@@ -38,7 +44,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_PADMM = 0, ORC_RPADMM_FG = 1, ORC_RPADMM_EB = 2, ORC_RPDRQ = 3, ORC_TY = 4 };
+enum { ORC_PADMM = 0, ORC_RPADMM_FG = 1, ORC_RPADMM_EB = 2, ORC_RPDRQ = 3, ORC_TY = 4,
+       ORC_CP = 5 };
 
 /* Parameters of one run.  Mirrored by a ctypes.Structure in __init__.py. */
 typedef struct {
@@ -52,7 +59,7 @@ typedef struct {
     double a2;         /* Potts p_s preconditioner a_2 (>= 2L)              */
     double rho;        /* EB / DR relaxation                                */
     double r;          /* FG relaxation on u                               */
-    double sigma, tau; /* rPDRQ step sizes                                  */
+    double sigma, tau; /* rPDRQ and ALG1 step sizes                         */
 } orc_params;
 
 #define AT(a, i, j) ((a)[(size_t)(i) * (size_t)W + (size_t)(j)])
@@ -304,18 +311,57 @@ static void binary_ty_step(int H, int W, const double *Cs, const double *Ct, con
     }
 }
 
+/* ubar = u - tau (div q + p_t - p_s): the extrapolated multiplier of ALG1
+ * recovered from the state (see the readings above). */
+static void binary_cp_ubar(int H, int W, double tau, const double *u, const double *qx,
+                           const double *qy, const double *ps, const double *pt, double *ubar) {
+    const size_t n = (size_t)H * W;
+    orc_div(H, W, qx, qy, ubar);
+    for (size_t k = 0; k < n; ++k) ubar[k] = u[k] - tau * (ubar[k] + pt[k] - ps[k]);
+}
+
+/* One ALG1 iteration (Chambolle-Pock, Eq. iteration:pd:seg): dual steps on
+ * q, p_t, p_s with the extrapolated ubar^k, the primal step on u, then
+ * ubar^{k+1} = 2 u^{k+1} - u^k. */
+static void binary_cp_step(int H, int W, const double *Cs, const double *Ct, const double *alpha,
+                           const orc_params *P, double *u, double *qx, double *qy, double *ps,
+                           double *pt, double *ubar, double *w1, double *w2, double *w3) {
+    const size_t n = (size_t)H * W;
+    const double sg = P->sigma, tau = P->tau;
+    double *gx = w1, *gy = w2, *d = w3;
+    orc_grad(H, W, ubar, gx, gy);
+    for (size_t k = 0; k < n; ++k) {
+        qx[k] = qx[k] - sg * gx[k];
+        qy[k] = qy[k] - sg * gy[k];
+    }
+    orc_project_alpha(n, qx, qy, alpha, P->aniso);
+    for (size_t k = 0; k < n; ++k) {
+        pt[k] = dmin(pt[k] + sg * ubar[k], Ct[k]);
+        ps[k] = dmin(ps[k] - sg * ubar[k] + sg, Cs[k]);
+    }
+    orc_div(H, W, qx, qy, d);
+    for (size_t k = 0; k < n; ++k) {
+        const double u0 = u[k];
+        u[k] = u0 - tau * (d[k] + pt[k] - ps[k]);
+        ubar[k] = 2.0 * u[k] - u0;
+    }
+}
+
 /* Run n_iter iterations from the given state (cold start first if
  * `cold` != 0).  Returns 0, or -1 on a bad algorithm code / allocation. */
 int orc_binary_run(int H, int W, const double *Cs, const double *Ct, const double *alpha,
                    const orc_params *P, int n_iter, int cold, double *u, double *qx, double *qy,
                    double *ps, double *pt) {
-    if (P->algo < ORC_PADMM || P->algo > ORC_TY) return -1;
+    if (P->algo < ORC_PADMM || P->algo > ORC_CP) return -1;
     const size_t n = (size_t)H * W;
     if (cold) orc_binary_init(H, W, Cs, Ct, P->algo == ORC_RPDRQ, P->tau, u, qx, qy, ps, pt);
     double *w1 = dalloc(n), *w2 = dalloc(n), *w3 = dalloc(n), *w4 = dalloc(n), *w5 = dalloc(n);
     if (!w1 || !w2 || !w3 || !w4 || !w5) return -1;
+    if (P->algo == ORC_CP) binary_cp_ubar(H, W, P->tau, u, qx, qy, ps, pt, w5);
     for (int it = 0; it < n_iter; ++it) {
-        if (P->algo == ORC_RPDRQ)
+        if (P->algo == ORC_CP)
+            binary_cp_step(H, W, Cs, Ct, alpha, P, u, qx, qy, ps, pt, w5, w1, w2, w3);
+        else if (P->algo == ORC_RPDRQ)
             binary_dr_step(H, W, Cs, Ct, alpha, P, u, qx, qy, ps, pt, w1, w2, w3, w4, w5);
         else if (P->algo == ORC_TY)
             binary_ty_step(H, W, Cs, Ct, alpha, P, u, qx, qy, ps, pt, w1, w2, w3, w4, w5);
@@ -562,17 +608,66 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
     }
 }
 
+/* ubar_i = u_i - tau (div q_i + p_i - p_s) (ALG1; see the readings above). */
+static void potts_cp_ubar(int H, int W, int L, double tau, const double *u, const double *qx,
+                          const double *qy, const double *p, const double *ps, double *ubar) {
+    const size_t n = (size_t)H * W;
+    for (int i = 0; i < L; ++i) {
+        double *Ub = ubar + i * n;
+        orc_div(H, W, qx + i * n, qy + i * n, Ub);
+        for (size_t k = 0; k < n; ++k)
+            Ub[k] = u[i * n + k] - tau * (Ub[k] + p[i * n + k] - ps[k]);
+    }
+}
+
+/* One Potts ALG1 iteration (Eq. alg1:4labels, general L): q_i, p_i and p_s
+ * dual steps with ubar^k, the primal steps on u_i, ubar^{k+1} = 2u^{k+1} - u^k. */
+static void potts_cp_step(int H, int W, int L, const double *C, const double *alpha,
+                          const orc_params *P, double *u, double *qx, double *qy, double *p,
+                          double *ps, double *ubar, double *w1, double *w2, double *w3) {
+    const size_t n = (size_t)H * W;
+    const double sg = P->sigma, tau = P->tau;
+    for (int i = 0; i < L; ++i) {
+        double *Qx = qx + i * n, *Qy = qy + i * n, *Pi = p + i * n;
+        const double *Ub = ubar + i * n, *Ci = C + i * n;
+        orc_grad(H, W, Ub, w1, w2);
+        for (size_t k = 0; k < n; ++k) {
+            Qx[k] = Qx[k] - sg * w1[k];
+            Qy[k] = Qy[k] - sg * w2[k];
+        }
+        orc_project_alpha(n, Qx, Qy, alpha, P->aniso);
+        for (size_t k = 0; k < n; ++k) Pi[k] = dmin(Pi[k] + sg * Ub[k], Ci[k]);
+    }
+    for (size_t k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < L; ++i) s += ubar[i * n + k];
+        ps[k] = ps[k] - sg * s + sg;
+    }
+    for (int i = 0; i < L; ++i) {
+        double *Ui = u + i * n, *Ub = ubar + i * n;
+        orc_div(H, W, qx + i * n, qy + i * n, w3);
+        for (size_t k = 0; k < n; ++k) {
+            const double u0 = Ui[k];
+            Ui[k] = u0 - tau * (w3[k] + p[i * n + k] - ps[k]);
+            Ub[k] = 2.0 * Ui[k] - u0;
+        }
+    }
+}
+
 int orc_potts_run(int H, int W, int L, const double *C, const double *alpha, const orc_params *P,
                   int n_iter, int cold, double *u, double *qx, double *qy, double *p, double *ps) {
-    if (P->algo < ORC_PADMM || P->algo > ORC_TY || L < 2 || L > 64) return -1;
+    if (P->algo < ORC_PADMM || P->algo > ORC_CP || L < 2 || L > 64) return -1;
     const size_t n = (size_t)H * W;
     if (cold) orc_potts_init(H, W, L, C, P->algo == ORC_RPDRQ, P->tau, u, qx, qy, p, ps);
     double *big = dalloc(n * L);
     double *w1 = dalloc(n), *w2 = dalloc(n), *w3 = dalloc(n), *w4 = dalloc(n), *w5 = dalloc(n),
            *w6 = dalloc(n);
     if (!big || !w1 || !w2 || !w3 || !w4 || !w5 || !w6) return -1;
+    if (P->algo == ORC_CP) potts_cp_ubar(H, W, L, P->tau, u, qx, qy, p, ps, big);
     for (int it = 0; it < n_iter; ++it) {
-        if (P->algo == ORC_RPDRQ)
+        if (P->algo == ORC_CP)
+            potts_cp_step(H, W, L, C, alpha, P, u, qx, qy, p, ps, big, w1, w2, w3);
+        else if (P->algo == ORC_RPDRQ)
             potts_dr_step(H, W, L, C, alpha, P, u, qx, qy, p, ps, big, w1, w2, w3, w4, w6);
         else if (P->algo == ORC_TY)
             potts_ty_step(H, W, L, C, alpha, P, u, qx, qy, p, ps, big, w1, w2, w3, w4, w5);

@@ -11,7 +11,7 @@ import pytest
 
 from paper_2004_11227_gb300 import synth
 
-ALGOS = [0, 1, 2, 3, 4]
+ALGOS = [0, 1, 2, 3, 4, 5]
 
 
 def _converge(orc, inst, algo, tol, max_iter=40000, **kw):
@@ -344,3 +344,50 @@ def test_ty_potts_p_steps_maximise_the_augmented_lagrangian(orc):
             best = minimize_scalar(neg_ps, bounds=(-50, 50), method="bounded",
                                    options={"xatol": 1e-12}).x
             assert abs(st1["ps"][y, x] - best) < 1e-6
+
+
+# --- ALG1: the extrapolated multiplier is recovered from the state ------------------
+
+def test_alg1_split_runs_equal_one_run(orc):
+    """A run recovers ubar^k = 2u^k - u^{k-1} from u^k - tau (div q + p_t -
+    p_s)^k; the explicit recursion inside a run and the recovery at the start
+    of the next must agree, so splitting a run changes nothing (to rounding)."""
+    inst = synth.config2(23, 31)
+    Cs, Ct = inst.costs
+    p = orc.default_params(5, 2)
+    one = orc.binary_run(Cs, Ct, inst.alpha, p, 40)
+    two = orc.binary_run(Cs, Ct, inst.alpha, p, 17)
+    two = orc.binary_run(Cs, Ct, inst.alpha, p, 23, two)
+    for k in one:
+        np.testing.assert_allclose(two[k], one[k], atol=1e-12)
+    instp = synth.config3(14, 17)
+    p = orc.default_params(5, 4)
+    one = orc.potts_run(instp.costs, instp.alpha, p, 30)
+    two = orc.potts_run(instp.costs, instp.alpha, p, 11)
+    two = orc.potts_run(instp.costs, instp.alpha, p, 19, two)
+    for k in one:
+        np.testing.assert_allclose(two[k], one[k], atol=1e-12)
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 8])
+def test_alg1_default_steps_satisfy_cp_condition(orc, L):
+    """sigma tau ||K*K|| < 1 (the convergence condition the Appendix cites)
+    for the default steps, with K*K assembled as a matrix on a small grid:
+    binary K u = (-grad u, u, -u); Potts K*K = Diag(-Lap + I) + Ones(L, L)."""
+    H, W = 5, 6
+    n = H * W
+    D = np.zeros((2 * n, n))
+    for j in range(n):
+        e = np.zeros((H, W))
+        e.flat[j] = 1.0
+        gx, gy = orc.grad(e)
+        D[:n, j] = gx.ravel()
+        D[n:, j] = gy.ravel()
+    lap = -(D.T @ D)
+    if L == 2:
+        KK = -lap + 2.0 * np.eye(n)
+    else:
+        KK = np.kron(np.eye(L), -lap + np.eye(n)) + np.kron(np.ones((L, L)), np.eye(n))
+    p = orc.default_params(5, L)
+    lam = np.linalg.eigvalsh(KK).max()
+    assert p.sigma * p.tau * lam < 1.0, (p.sigma, p.tau, lam)
