@@ -483,7 +483,7 @@ def main():
         return float(np.median(ts)), it
 
     ttg = {}
-    for algo in (0, 1, 2, 3):
+    for algo in (0, 1, 2, 3, 4, 5):
         for impl in (0, 1):
             ms, it = time_to_gap(algo, impl)
             ttg[f"{cmf.ALGO_NAMES[algo]}_{'fused' if impl == 0 else 'plain'}"] = {

@@ -73,10 +73,15 @@ typedef enum {
     CMF_RPADMM_FG = 1,  /* rpADMMI, relaxation r on u (Fortin-Glowinski)     */
     CMF_RPADMM_EB = 2,  /* rpADMMII, relaxation rho (Eckstein-Bertsekas)     */
     CMF_RPDRQ = 3,      /* relaxed preconditioned Douglas-Rachford           */
-    CMF_TY = 4          /* pADMM-TY: the classical multi-block ADMM the paper
+    CMF_TY = 4,         /* pADMM-TY: the classical multi-block ADMM the paper
                            compares against (Eq. ADMM:Tai_yuan / Eq.
                            mADMM:Tai_yuan), sequential p-steps, no relaxation,
                            no convergence guarantee                           */
+    CMF_CP = 5          /* ALG1: the first-order primal-dual (Chambolle-Pock)
+                           method of the paper's Appendix (Eq. iteration:pd:seg
+                           / Eq. alg1:4labels), step sizes sigma, tau with
+                           sigma tau ||K*K|| < 1; fused and plain forms, the
+                           state between calls is (u, q, p)                   */
 } cmf_algo;
 
 typedef enum { CMF_F32 = 0, CMF_F16 = 1, CMF_BF16 = 2 } cmf_dtype;
@@ -89,7 +94,10 @@ typedef enum {
 /* Parameters.  cmf_default_params() fills the paper's values (Sec. 4):
  * c = 0.3, a = 8, a1 = 2 (binary a~), a2 = 2L, rho = 1.9, r = 1.618,
  * rPDRQ sigma = 0.2, tau = 1.0 (binary) or sigma = 5, tau = 0.4 (Potts),
- * one sRBGS sweep, isotropic P_alpha. */
+ * ALG1 sigma = 0.4, tau = 1 / (10 sigma) (binary: ||K*K|| < 10) or
+ * 1 / ((9 + L) sigma) (Potts, L > 2), one sRBGS sweep, isotropic P_alpha.
+ * (L = 2 means the binary model; a two-label Potts ALG1 run needs
+ * tau <= 1 / (11 sigma).) */
 typedef struct {
     int algo;          /* cmf_algo                                             */
     int storage;       /* cmf_dtype of the flow planes                         */

@@ -19,11 +19,11 @@ import torch
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, NOT_CONVERGED = range(6)
-PADMM, RPADMM_FG, RPADMM_EB, RPDRQ, TY = range(5)
+PADMM, RPADMM_FG, RPADMM_EB, RPDRQ, TY, CP = range(6)
 F32, F16, BF16 = range(3)
 FUSED, PLAIN = range(2)
 ALGO_NAMES = {PADMM: "pADMMI", RPADMM_FG: "rpADMMI", RPADMM_EB: "rpADMMII", RPDRQ: "rPDRQ",
-              TY: "pADMM-TY"}
+              TY: "pADMM-TY", CP: "ALG1"}
 _TORCH_DTYPE = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
 
 

@@ -49,7 +49,9 @@ WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool pot
     off += align_up(plane * 4 * nu);
     for (int i = 0; i < nf; ++i) off += align_up(plane * es);
     w.tmp = off;
-    off += align_up(plane * 4 * (size_t)(potts ? L + 2 : 1));
+    // plain forms: g and div q^{k+1} (per label for Potts); the fused kernels
+    // keep everything on chip
+    off += align_up(plane * 4 * (size_t)(p.impl == CMF_PLAIN ? (potts ? 2 * L : 2) : 0));
     w.partials = off;
     off += align_up(sizeof(double) * 3 * (size_t)eval_blocks(H, W));
     w.scalars = off;
@@ -66,7 +68,7 @@ bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
 cmf_status check_params(const cmf_params* p, int L) {
     if (!p) return CMF_EINVAL;
-    if (p->algo < CMF_PADMM || p->algo > CMF_TY) return CMF_EINVAL;
+    if (p->algo < CMF_PADMM || p->algo > CMF_CP) return CMF_EINVAL;
     if (p->storage < CMF_F32 || p->storage > CMF_BF16) return CMF_EINVAL;
     if (p->impl != CMF_FUSED && p->impl != CMF_PLAIN) return CMF_EINVAL;
     if (p->sweeps < 1 || (p->impl == CMF_FUSED && p->sweeps > 4) || p->sweeps > 64)
@@ -571,7 +573,7 @@ cmf_status solve_loop(const cmf_params* p, Run run, Eval eval, Copy copy_back, d
 extern "C" {
 
 cmf_status cmf_default_params(int algo, int L, cmf_params* p) {
-    if (!p || algo < CMF_PADMM || algo > CMF_TY || L < 2) return CMF_EINVAL;
+    if (!p || algo < CMF_PADMM || algo > CMF_CP || L < 2) return CMF_EINVAL;
     memset(p, 0, sizeof(*p));
     p->algo = algo;
     p->storage = CMF_F32;
@@ -590,6 +592,10 @@ cmf_status cmf_default_params(int algo, int L, cmf_params* p) {
     p->r = 1.618;
     p->sigma = L == 2 ? 0.2 : 5.0;
     p->tau = L == 2 ? 1.0 : 0.4;
+    if (algo == CMF_CP) {  // ALG1 (Sec. 4): sigma = 0.4, tau = 1 / (||K*K|| bound x sigma)
+        p->sigma = 0.4;
+        p->tau = 1.0 / ((L == 2 ? 10.0 : 9.0 + L) * 0.4);
+    }
     p->tol_gap = 1e-4;
     return CMF_OK;
 }

@@ -124,7 +124,8 @@ __device__ __forceinline__ void binary_admm_tile(BinProblem P, BinState<S> s0, B
             const float ps0 = St::ld(s0.ps + k), pt0 = St::ld(s0.pt + k);
             const float u0 = __ldg(s0.u + k);
             float ps1, pt1, u1;
-            binary_pu<S>(K, d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1, u1);
+            binary_pu<S>(K, g_s[ly + 1][lx + 1], d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k),
+                         ps1, pt1, u1);
             St::st(s1.ps + k, ps1);
             St::st(s1.pt + k, pt1);
             s1.u[k] = u1;
@@ -191,13 +192,14 @@ __global__ void k_binary_plain_div(BinProblem P, BinState<S> s, float* d) {
 
 // steps a4 + a8: p and u updates, in place
 template <typename S>
-__global__ void k_binary_plain_pu(BinProblem P, BinState<S> s, const float* dbuf, AdmmCoef K) {
+__global__ void k_binary_plain_pu(BinProblem P, BinState<S> s, const float* gbuf,
+                                  const float* dbuf, AdmmCoef K) {
     PIXEL_PROLOGUE
     using St = Store<S>;
     const float d = dbuf[k];
     const float ps0 = St::ldw(s.ps + k), pt0 = St::ldw(s.pt + k), u0 = s.u[k];
     float ps1, pt1, u1;
-    binary_pu<S>(K, d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1, u1);
+    binary_pu<S>(K, gbuf[k], d, ps0, pt0, u0, __ldg(P.Cs + k), __ldg(P.Ct + k), ps1, pt1, u1);
     St::st(s.ps + k, ps1);
     St::st(s.pt + k, pt1);
     s.u[k] = u1;
@@ -502,8 +504,8 @@ static cudaError_t binary_admm_step_t(const BinProblem& P, const BinState<S>& a,
     const dim3 gr = grid_for(P.g, 8), bl(32, 8);
     k_binary_plain_g<S><<<gr, bl, 0, st>>>(P, a, tmp, K);
     k_binary_plain_q<S, ANISO><<<gr, bl, 0, st>>>(P, a, tmp, K);
-    k_binary_plain_div<S><<<gr, bl, 0, st>>>(P, a, tmp);
-    k_binary_plain_pu<S><<<gr, bl, 0, st>>>(P, a, tmp, K);
+    k_binary_plain_div<S><<<gr, bl, 0, st>>>(P, a, tmp + P.g.plane);
+    k_binary_plain_pu<S><<<gr, bl, 0, st>>>(P, a, tmp, tmp + P.g.plane, K);
     return cudaGetLastError();
 }
 

@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(kStripWarps * 32, 8)
                 const float d_o = mxo * tx_o - tx_e + wy * ty_o - qyn_up.y;
                 const float2 ps = PS::f2(a.ps), pt = PS::f2(a.pt);
                 float ps_e, pt_e, u_e, ps_o, pt_o, u_o;
-                binary_pu<S>(K, d_e, ps.x, pt.x, a.u.x, cs_t.x, ct_t.x, ps_e, pt_e, u_e);
-                binary_pu<S>(K, d_o, ps.y, pt.y, a.u.y, cs_t.y, ct_t.y, ps_o, pt_o, u_o);
+                binary_pu<S>(K, g_t.x, d_e, ps.x, pt.x, a.u.x, cs_t.x, ct_t.x, ps_e, pt_e, u_e);
+                binary_pu<S>(K, g_t.y, d_o, ps.y, pt.y, a.u.y, cs_t.y, ct_t.y, ps_o, pt_o, u_o);
                 if (own) {
                     const int o = t * G.pitch + c;
                     PS::st(s1.qx + o, tx_e, tx_o);

@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(256, 4)
                 const float ps0 = bload(sps + so), pt0 = bload(spt + so);
                 const float u0 = su[(ly + 2) * BXU + lx + XO];
                 float ps1, pt1, u1;
-                binary_pu<S>(K, d, ps0, pt0, u0, __ldg(P.Cs + kk), __ldg(P.Ct + kk), ps1, pt1,
-                             u1);
+                binary_pu<S>(K, g_s[(ly + 1) * GW + lx + 1], d, ps0, pt0, u0, __ldg(P.Cs + kk),
+                             __ldg(P.Ct + kk), ps1, pt1, u1);
                 St::st(s1.ps + kk, ps1);
                 St::st(s1.pt + kk, pt1);
                 s1.u[kk] = u1;

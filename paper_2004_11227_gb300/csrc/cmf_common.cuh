@@ -103,18 +103,33 @@ struct AdmmCoef {
     float omr;       // 1 - rho (EB) or 0 (FG, TY)
     float inv_L;     // 1 / L (Potts pADMM-TY)
     int ty;          // 1: pADMM-TY sequential p-steps (Eq. ADMM:Tai_yuan)
+    // ALG1 (Chambolle-Pock, Eq. iteration:pd:seg / Eq. alg1:4labels) runs in
+    // the same kernels: with inv_c = 1/tau the source field g equals
+    // -ubar/tau, where ubar = u - tau (div q + p_t - p_s) = 2u^k - u^{k-1} is
+    // the extrapolated multiplier, so the q-step q - sigma grad ubar is the
+    // ADMM q-step with inv_a = sigma tau; cu = tau.
+    int cp;          // 1: ALG1 dual steps on p with ubar = -tau g
+    float sigma;     // ALG1 dual step size
+    float tau;       // ALG1 primal step size
 };
 
 // Pointwise p / u step of the binary ADMM family, rounded to the storage
 // type.  rpADMMII / rpADMMI (Eq. rpADMMII, Eq. rpADMMI): p_t and p_s both
 // read p^k (Jacobi), then the multiplier update.  pADMM-TY (Eq.
-// ADMM:Tai_yuan): p_s from p_t^k, then p_t from p_s^{k+1}, then u.
+// ADMM:Tai_yuan): p_s from p_t^k, then p_t from p_s^{k+1}, then u.  ALG1
+// (Eq. iteration:pd:seg): p_t, p_s ascend along ubar = -tau g (g: this
+// pixel's source field of the iteration), then u descends.
 template <typename S>
-__device__ __forceinline__ void binary_pu(const AdmmCoef& K, float d, float ps0, float pt0,
-                                          float u0, float cs, float ct, float& ps1, float& pt1,
-                                          float& u1) {
+__device__ __forceinline__ void binary_pu(const AdmmCoef& K, float g, float d, float ps0,
+                                          float pt0, float u0, float cs, float ct, float& ps1,
+                                          float& pt1, float& u1) {
     using St = Store<S>;
-    if (K.ty) {
+    if (K.cp) {
+        const float ub = -K.tau * g;
+        pt1 = St::rt(fminf(pt0 + K.sigma * ub, ct));
+        ps1 = St::rt(fminf(ps0 - K.sigma * ub + K.sigma, cs));
+        u1 = u0 - K.tau * (d + pt1 - ps1);
+    } else if (K.ty) {
         ps1 = St::rt(fminf(pt0 + d - u0 * K.inv_c + K.inv_c, cs));
         pt1 = St::rt(fminf(ps1 - d + u0 * K.inv_c, ct));
         u1 = u0 - K.cu * (pt1 - ps1 + d);
@@ -131,14 +146,20 @@ __device__ __forceinline__ void binary_pu(const AdmmCoef& K, float d, float ps0,
 // Potts, one label of one pixel: p_i^{k+1} (rounded), the label's share of
 // the p_s update (acc_a, acc_b) and v_i with u_i^{k+1} = v_i + cu p_s^{k+1}.
 // rpADMMII / rpADMMI: Eqs. after Thm 2 / Eq. multi:fg:4; pADMM-TY: Eq.
-// mADMM:Tai_yuan with p_s from the new p_i.
+// mADMM:Tai_yuan with p_s from the new p_i; ALG1: Eq. alg1:4labels with
+// ubar_i = -tau g (g: this label's source field at the pixel).
 template <typename S>
-__device__ __forceinline__ float potts_label_pu(const AdmmCoef& K, float d, float p0, float ps0,
-                                                float u0, float cl, float& acc_a, float& acc_b,
-                                                float& v) {
+__device__ __forceinline__ float potts_label_pu(const AdmmCoef& K, float g, float d, float p0,
+                                                float ps0, float u0, float cl, float& acc_a,
+                                                float& acc_b, float& v) {
     using St = Store<S>;
     float p1;
-    if (K.ty) {
+    if (K.cp) {
+        const float ub = -K.tau * g;
+        p1 = St::rt(fminf(p0 + K.sigma * ub, cl));
+        acc_a += ub;
+        v = u0 - K.tau * (d + p1);
+    } else if (K.ty) {
         p1 = St::rt(fminf(ps0 - d + u0 * K.inv_c, cl));
         acc_a += p1 + d - u0 * K.inv_c;
         v = u0 - K.cu * (p1 + d);
@@ -155,6 +176,7 @@ __device__ __forceinline__ float potts_label_pu(const AdmmCoef& K, float d, floa
 template <typename S>
 __device__ __forceinline__ float potts_ps_update(const AdmmCoef& K, float ps0, float acc_a,
                                                  float acc_b) {
+    if (K.cp) return Store<S>::rt(ps0 - K.sigma * (acc_a + acc_b) + K.sigma);
     return K.ty ? Store<S>::rt((acc_a + K.inv_c) * K.inv_L)
                 : Store<S>::rt(ps0 + (acc_a + acc_b + K.inv_c) * K.inv_a2);
 }

@@ -158,8 +158,8 @@ __device__ __forceinline__ void potts_admm_tile(PottsProblem P, PottsState<S> s0
                 const float ps0 = ps_s[ly + 1][lx + 1];
                 const float p0 = St::ld(s0.p + lo + k);
                 const float u0 = __ldg(s0.u + lo + k);
-                const float p1 = potts_label_pu<S>(K, d, p0, ps0, u0, __ldg(P.C + lo + k),
-                                                   accd[j], accp[j], v);
+                const float p1 = potts_label_pu<S>(K, g_s[ly + 1][lx + 1], d, p0, ps0, u0,
+                                                   __ldg(P.C + lo + k), accd[j], accp[j], v);
                 St::st(s1.p + lo + k, p1);
             }
             v_s[(l * TY + ly) * TX + lx] = v;
@@ -243,7 +243,8 @@ __global__ void k_potts_plain_div(PottsProblem P, PottsState<S> s, int l, float*
 }
 
 template <typename S>
-__global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* d, AdmmCoef K) {
+__global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* g, const float* d,
+                                 AdmmCoef K) {
     POTTS_PIXEL_PROLOGUE
     using St = Store<S>;
     const size_t pl = G.plane;
@@ -254,7 +255,7 @@ __global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* d
     for (int l = 0; l < P.L; ++l) {
         const size_t ki = l * pl + k;
         float v;
-        const float p1 = potts_label_pu<S>(K, d[ki], St::ldw(s.p + ki), ps0, s.u[ki],
+        const float p1 = potts_label_pu<S>(K, g[ki], d[ki], St::ldw(s.p + ki), ps0, s.u[ki],
                                            __ldg(P.C + ki), acc_a, acc_b, v);
         St::st(s.p + ki, p1);
         s.u[ki] = v;
@@ -602,14 +603,14 @@ static cudaError_t potts_admm_step_t(const PottsProblem& P, const PottsState<S>&
         return launch_potts_admm_fused<S, ANISO, 1>(P, a, b, K, st);
     }
     const dim3 gr = pgrid(P.g, 8), bl(32, 8);
-    float* g = tmp;                 // one plane
-    float* d = tmp + P.g.plane;     // L planes
+    float* g = tmp;                        // L planes (ALG1 reads them back)
+    float* d = tmp + P.L * P.g.plane;      // L planes
     for (int l = 0; l < P.L; ++l) {
-        k_potts_plain_g<S><<<gr, bl, 0, st>>>(P, a, l, g, K);
-        k_potts_plain_q<S, ANISO><<<gr, bl, 0, st>>>(P, a, l, g, K);
+        k_potts_plain_g<S><<<gr, bl, 0, st>>>(P, a, l, g + l * P.g.plane, K);
+        k_potts_plain_q<S, ANISO><<<gr, bl, 0, st>>>(P, a, l, g + l * P.g.plane, K);
         k_potts_plain_div<S><<<gr, bl, 0, st>>>(P, a, l, d);
     }
-    k_potts_plain_pu<S><<<gr, bl, 0, st>>>(P, a, d, K);
+    k_potts_plain_pu<S><<<gr, bl, 0, st>>>(P, a, g, d, K);
     return cudaGetLastError();
 }
 

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7)
             // d = div q^{k+1} at output row t from the new q of rows t and t-1,
             // then p_i^{k+1}, w_i and this label's share of the p_s update
             auto finish = [&](int t, const QN& q, float2 qy_up, const RowVals<S>& x,
-                              float2 cl) {
+                              float2 cl, float2 g) {
                 const float txl = __shfl_up_sync(full, q.tx_o, 1);  // new q_x at c-1
                 const float wy = row_w(t);
                 const float d_e = q.tx_e - txl + wy * q.ty_e - qy_up.x;
@@ -151,8 +151,10 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7)
                 const float2 pv = PS::f2(x.p), ps = PS::f2(x.ps);
                 const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
                 float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
-                const float p1_e = potts_label_pu<S>(K, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
-                const float p1_o = potts_label_pu<S>(K, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
+                const float p1_e =
+                    potts_label_pu<S>(K, g.x, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
+                const float p1_o =
+                    potts_label_pu<S>(K, g.y, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
                 float2& ac = acc[t - r0][lane];
                 const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
                 if (l == 0) {
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7)
                 }
                 const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);
                 const QN q = q_new(a, g_t, g_n, al_t, t);
-                if (t >= r0) finish(t, q, qyn_up, a, cl_t);
+                if (t >= r0) finish(t, q, qyn_up, a, cl_t, g_t);
                 qyn_up = make_float2(q.ty_e, q.ty_o);
                 a = b;
                 b = nx;

@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
             const bool own = o_k[j] >= 0;
             const float cl = __ldg(C_l + (own ? o_k[j] : 0));
             float v;
-            const float p1 = potts_label_pu<S>(K, d, p0, ps0, u0, cl, accd[j], accp[j], v);
+            const float p1 = potts_label_pu<S>(K, g_s[(ly + 1) * GW + lx + 1], d, p0, ps0, u0, cl,
+                                               accd[j], accp[j], v);
             if (own) St::st(p_out + o_k[j], p1);
             v_s[(l * TY + ly) * TX + lx] = v;
         }

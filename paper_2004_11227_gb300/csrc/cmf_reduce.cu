@@ -60,6 +60,15 @@ AdmmCoef make_admm_coef(const cmf_params& p, int L) {
     k.omr = (float)(eb ? 1.0 - p.rho : 0.0);
     k.inv_L = (float)(1.0 / L);
     k.ty = ty ? 1 : 0;
+    k.cp = 0;
+    k.sigma = (float)p.sigma;
+    k.tau = (float)p.tau;
+    if (p.algo == CMF_CP) {  // g = -ubar / tau; q-step q + sigma tau grad g; u = v + tau p_s
+        k.cp = 1;
+        k.inv_c = (float)(1.0 / p.tau);
+        k.inv_a = (float)(p.sigma * p.tau);
+        k.cu = (float)p.tau;
+    }
     return k;
 }
 

@@ -38,10 +38,12 @@ def _alloc(cmf, inst, p):
     return cmf.alloc_binary(inst, p) if inst.kind == "binary" else cmf.alloc_potts(inst, p)
 
 
-@pytest.mark.parametrize("algo", [1, 2, 3])
+@pytest.mark.parametrize("algo", [1, 2, 3, 5])
 def test_batch_matches_single_solves(cmf, algo):
     insts = _instances()
     kw = dict(tol_gap=1e-4, max_iter=20000, check_every=10, variant=1)
+    if algo == 5:  # one (sigma, tau) for the batch: the 8-label bound (9 + 8) sigma tau <= 1
+        kw["tau"] = 1.0 / (17 * 0.4)
     p = cmf.default_params(algo, 2, **kw)
     items = [_alloc(cmf, i, p) for i in insts]
     status, res = cmf.cmf_solve_batch(items, p)

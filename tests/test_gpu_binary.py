@@ -17,7 +17,7 @@ from paper_2004_11227_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = [0, 1, 2, 3, 4]
+ALGOS = [0, 1, 2, 3, 4, 5]
 TOL_U = 1e-4
 
 
@@ -280,7 +280,7 @@ STRIP_CASES = {
 }
 
 
-@pytest.mark.parametrize("algo", [0, 1, 2, 4])
+@pytest.mark.parametrize("algo", [0, 1, 2, 4, 5])
 @pytest.mark.parametrize("case", list(STRIP_CASES))
 def test_strip_matches_oracle_f32(cmf, case, algo):
     inst, n = STRIP_CASES[case]
