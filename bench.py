@@ -167,6 +167,10 @@ KERNEL_CASES = {
     "binary-admm-1024": ("binary", 2, 1024, 1024, 2, 0, 0),
     "binary-admm-4096": ("binary", 2, 4096, 4096, 2, 0, 0),
     "binary-dr-4096": ("binary", 3, 4096, 4096, 2, 0, 0),
+    "binary-dr-1024": ("binary", 3, 1024, 1024, 2, 0, 0),
+    "binary-dr-plain-1024": ("binary", 3, 1024, 1024, 2, 0, 1),
+    "binary-cp-1024": ("binary", 5, 1024, 1024, 2, 0, 0),
+    "potts4-dr-plain-2048": ("potts", 3, 2048, 2048, 4, 0, 1),
     "binary-plain-4096": ("binary", 2, 4096, 4096, 2, 0, 1),
     "potts4-admm-2048": ("potts", 2, 2048, 2048, 4, 0, 0),
     "potts4-admm-2048-f16": ("potts", 2, 2048, 2048, 4, 1, 0),

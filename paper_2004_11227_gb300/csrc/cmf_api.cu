@@ -180,8 +180,9 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     call.tma = false;
     call.strip = false;
     // automatic choice: warp strips where the layout allows them (as fast as
-    // the persistent TMA kernel at 1024^2, faster on larger grids: measured)
-    if (!call.cfg.dr && !call.cfg.plain && (p->variant == 2 || p->variant == 0)) {
+    // the persistent TMA kernel at 1024^2, faster on larger grids: measured;
+    // rPDRQ: the pipelined red-black sweeps)
+    if (!call.cfg.plain && (p->variant == 2 || p->variant == 0)) {
         const bool ok =
             binary_strip_eligible(call.P.g, p->storage, Cs, Ct, alpha, call.user, call.ws);
         if (!ok && p->variant == 2)
@@ -220,7 +221,9 @@ cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st) {
         } else if (c.strip) {
             const BinStateV& a = cur == 0 ? c.user : c.ws;
             const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st);
+            cudaError_t e =
+                c.cfg.dr ? binary_dr_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.dc, st)
+                         : binary_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         } else if (c.tma) {

@@ -214,21 +214,6 @@ __global__ void k_binary_plain_pu(BinProblem P, BinState<S> s, const float* gbuf
 //   pbar_t += rho (min(2 p_t - pbar_t, C_t) - p_t)
 //   pbar_s += rho (min(2 p_s - pbar_s + tau, C_s) - p_s)
 // ---------------------------------------------------------------------------
-template <typename S, bool ANISO>
-__device__ __forceinline__ void binary_dr_flows(const DrCoef& D, float uc, float gx, float gy,
-                                                float qbx, float qby, float pbs, float pbt,
-                                                float al, float cs, float ct, float& oqx,
-                                                float& oqy, float& ops, float& opt) {
-    const float q1 = qbx - D.tau * gx, q2 = qby - D.tau * gy;
-    float tx = 2.f * q1 - qbx, ty = 2.f * q2 - qby;
-    project_alpha<ANISO>(tx, ty, al);
-    oqx = qbx + D.rho * (tx - q1);
-    oqy = qby + D.rho * (ty - q2);
-    const float pt1 = pbt + D.tau * uc, ps1 = pbs - D.tau * uc;
-    opt = pbt + D.rho * (fminf(2.f * pt1 - pbt, ct) - pt1);
-    ops = pbs + D.rho * (fminf(2.f * ps1 - pbs + D.tau, cs) - ps1);
-}
-
 // Fused: the tile's u after h = 2 sweeps + 1 half-sweeps is needed on rows
 // y0..y0+TY and cols x0..x0+32 (one extra for grad u).  Half-sweep s updates
 // its colour on that region grown by h-1-s, so u^k is staged on the region

@@ -147,6 +147,158 @@ __global__ void __launch_bounds__(kStripWarps * 32, 8)
     }
 }
 
+// ---- rPDRQ by warp strips (Eq. iteration:quadratic:seg) -------------------
+//
+// One iteration: b = -sigma (div qbar + pbar_t - pbar_s); the symmetric
+// red-black Gauss-Seidel sweep(s) for sigma tau (2I - Lap) u = b; the flow
+// steps and reflections.  A warp streams its band top-down as a pipeline of
+// S = 1 + 2 sweeps half-sweep stages: at step m it takes row m in (u^k, b),
+// runs stage s (red, black, red, ...) on row m-1-s, and finishes row m-S-1
+// (flows and reflections from the final u of rows m-S-1 and m-S).  A stage
+// reads the row below at the previous stage's version and the row above at
+// its own stage's version, whose cells of the other colour -- the only ones
+// a half-sweep reads -- are still at the previous stage's version: exactly
+// the red-black order.  Each stage needs one more column of halo, so lanes
+// 0..SW and 31-SW..31 carry the halo and 2 (32 - 2 (SW + 1)) columns are
+// owned per strip.
+template <typename S, bool ANISO, int SW>
+__global__ void __launch_bounds__(kStripWarps * 32)
+    k_binary_dr_strip(BinProblem P, BinState<S> s0, BinState<S> s1, DrCoef D, int R,
+                      int nstrips, int nitems) {
+    constexpr int NS = 1 + 2 * SW;        // half-sweep stages
+    constexpr int HL = SW + 1;            // halo lanes on each side
+    constexpr int OUT = 2 * (32 - 2 * HL);  // owned columns per strip
+    using PS = Pair<S>;
+    using PF = Pair<float>;
+    const int lane = threadIdx.x & 31;
+    const Grid G = P.g;
+    const unsigned full = 0xffffffffu;
+
+    for (int item = blockIdx.x * kStripWarps + (threadIdx.x >> 5); item < nitems;
+         item += gridDim.x * kStripWarps) {
+        const int x0 = (item % nstrips) * OUT;
+        const int r0 = (item / nstrips) * R;
+        const int r1 = min(r0 + R, G.H);
+        const int c = x0 - 2 * HL + 2 * lane;  // even column of the pair (W is even)
+        const bool colin = c >= 0 && c < G.W;
+        const bool own = colin && lane >= HL && lane <= 31 - HL;
+        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;
+        // neighbour counts of the two columns in x
+        const float ncx_e = (c > 0 ? 1.f : 0.f) + (c < G.W - 1 ? 1.f : 0.f);
+        const float ncx_o = 1.f + mxo;
+        auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
+        auto ld_s = [&](const S* base, int r) {
+            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
+        };
+        auto ld_f = [&](const float* base, int r) {
+            return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
+        };
+        auto ld_al = [&](int r) {
+            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+            return ld_f(P.alpha.plane, r);
+        };
+
+        float2 V[NS + 2];   // V[k]: u of row m-k (stage k-1 applied; k >= NS: final)
+        float2 Bh[NS + 1];  // Bh[k]: b of row m-k
+#pragma unroll
+        for (int k = 0; k < NS + 2; ++k) V[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < NS + 1; ++k) Bh[k] = make_float2(0.f, 0.f);
+        float2 qby_up = ld_s(s0.qy, r0 - NS - 1);  // qbar_y of the row above the ingested one
+
+        // prefetched inputs of the next ingested row and the next finished row
+        const int m_first = r0 - NS, m_last = r1 + NS;
+        float2 in_u = ld_f(s0.u, m_first), in_qx = ld_s(s0.qx, m_first);
+        float2 in_qy = ld_s(s0.qy, m_first), in_ps = ld_s(s0.ps, m_first);
+        float2 in_pt = ld_s(s0.pt, m_first);
+        const int t_first = m_first - NS - 1;
+        float2 f_qx = ld_s(s0.qx, t_first), f_qy = ld_s(s0.qy, t_first);
+        float2 f_ps = ld_s(s0.ps, t_first), f_pt = ld_s(s0.pt, t_first);
+        float2 f_cs = ld_f(P.Cs, t_first), f_ct = ld_f(P.Ct, t_first), f_al = ld_al(t_first);
+
+#pragma unroll 1
+        for (int m = m_first; m <= m_last; ++m) {
+            // shift the pipeline: row m enters
+#pragma unroll
+            for (int k = NS + 1; k > 0; --k) V[k] = V[k - 1];
+#pragma unroll
+            for (int k = NS; k > 0; --k) Bh[k] = Bh[k - 1];
+            // b of row m (zero outside the grid)
+            {
+                const float qxl = __shfl_up_sync(full, in_qx.y, 1);
+                const float wy = m < G.H - 1 ? 1.f : 0.f;
+                float2 b;
+                b.x = -D.sigma * (in_qx.x - qxl + wy * in_qy.x - qby_up.x + in_pt.x - in_ps.x);
+                b.y = -D.sigma * (mxo * in_qx.y - in_qx.x + wy * in_qy.y - qby_up.y + in_pt.y -
+                                  in_ps.y);
+                const bool ok = ok_row(m);
+                Bh[0] = ok ? b : make_float2(0.f, 0.f);
+                V[0] = in_u;  // zero outside the grid
+                qby_up = in_qy;
+            }
+            if (m < m_last) {  // next ingested row
+                const int r = m + 1;
+                in_u = ld_f(s0.u, r);
+                in_qx = ld_s(s0.qx, r);
+                in_qy = ld_s(s0.qy, r);
+                in_ps = ld_s(s0.ps, r);
+                in_pt = ld_s(s0.pt, r);
+            }
+            // half-sweep stages on rows m-1 .. m-NS
+#pragma unroll
+            for (int st = 0; st < NS; ++st) {
+                const int j = m - 1 - st;
+                const bool red = (st & 1) == 0;          // red: (row + col) even
+                const bool act_e = ((j & 1) == 0) == red;  // the pair's even column is active
+                const float2 cur = V[st + 1], up = V[st + 2], dn = V[st];
+                const float left = __shfl_up_sync(full, cur.y, 1);   // u(j, c-1)
+                const float right = __shfl_down_sync(full, cur.x, 1);  // u(j, c+2)
+                const float ncy = (j > 0 ? 1.f : 0.f) + (j < G.H - 1 ? 1.f : 0.f);
+                const float2 bj = Bh[st + 1];
+                if (ok_row(j)) {
+                    if (act_e) {
+                        const float sum = left + cur.y + up.x + dn.x;
+                        V[st + 1].x = (bj.x * D.inv_st + sum) / (D.kappa + ncx_e + ncy);
+                    } else {
+                        const float sum = cur.x + right + up.y + dn.y;
+                        V[st + 1].y = (bj.y * D.inv_st + sum) / (D.kappa + ncx_o + ncy);
+                    }
+                }
+            }
+            // finish row t = m - NS - 1: flows, reflections, outputs
+            const int t = m - NS - 1;
+            const float2 uc = V[NS + 1], ud = V[NS];
+            const float u_right = __shfl_down_sync(full, uc.x, 1);
+            if (t >= r0 && t < r1 && own) {
+                const float wy = t < G.H - 1 ? 1.f : 0.f;
+                const float gx_e = uc.y - uc.x, gx_o = mxo * (u_right - uc.y);
+                const float gy_e = wy * (ud.x - uc.x), gy_o = wy * (ud.y - uc.y);
+                float qx_e, qy_e, ps_e, pt_e, qx_o, qy_o, ps_o, pt_o;
+                binary_dr_flows<S, ANISO>(D, uc.x, gx_e, gy_e, f_qx.x, f_qy.x, f_ps.x, f_pt.x,
+                                          f_al.x, f_cs.x, f_ct.x, qx_e, qy_e, ps_e, pt_e);
+                binary_dr_flows<S, ANISO>(D, uc.y, gx_o, gy_o, f_qx.y, f_qy.y, f_ps.y, f_pt.y,
+                                          f_al.y, f_cs.y, f_ct.y, qx_o, qy_o, ps_o, pt_o);
+                const int o = t * G.pitch + c;
+                PF::st(s1.u + o, uc.x, uc.y);
+                PS::st(s1.qx + o, qx_e, qx_o);
+                PS::st(s1.qy + o, qy_e, qy_o);
+                PS::st(s1.ps + o, ps_e, ps_o);
+                PS::st(s1.pt + o, pt_e, pt_o);
+            }
+            if (m < m_last) {  // inputs of the next finished row
+                const int r = t + 1;
+                f_qx = ld_s(s0.qx, r);
+                f_qy = ld_s(s0.qy, r);
+                f_ps = ld_s(s0.ps, r);
+                f_pt = ld_s(s0.pt, r);
+                f_cs = ld_f(P.Cs, r);
+                f_ct = ld_f(P.Ct, r);
+                f_al = ld_al(r);
+            }
+        }
+    }
+}
+
 // ---- host side -------------------------------------------------------------
 
 bool binary_strip_eligible(const Grid& G, int storage, const float* Cs, const float* Ct,
@@ -205,6 +357,63 @@ cudaError_t binary_strip_step(int storage, const BinProblem& P, const BinStateV&
         case CMF_F32: return bin_strip_s<float>(P, a, b, aniso, K, st);
         case CMF_F16: return bin_strip_s<__half>(P, a, b, aniso, K, st);
         default: return bin_strip_s<__nv_bfloat16>(P, a, b, aniso, K, st);
+    }
+}
+
+template <typename S, bool ANISO, int SW>
+static cudaError_t launch_bin_dr_strip(const BinProblem& P, const BinState<S>& a,
+                                       const BinState<S>& b, const DrCoef& D, cudaStream_t st) {
+    auto kern = k_binary_dr_strip<S, ANISO, SW>;
+    static int resident = 0;  // warps resident on the whole device
+    if (!resident) {
+        int dev = 0, sms = 0, blocks = 0;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
+                                                                0)) != cudaSuccess)
+            return e;
+        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    }
+    const Grid& G = P.g;
+    constexpr int OUT = 2 * (32 - 2 * (SW + 1));
+    const int nstrips = (G.W + OUT - 1) / OUT;
+    const int R = strip::choose_rows(G.H, nstrips, resident, 8, 64, 2 * (1 + 2 * SW) + 1);
+    const int nitems = nstrips * ((G.H + R - 1) / R);
+    const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
+    const int grid = blocks < resident / kStripWarps ? blocks : resident / kStripWarps;
+    kern<<<grid, kStripWarps * 32, 0, st>>>(P, a, b, D, R, nstrips, nitems);
+    return cudaGetLastError();
+}
+
+template <typename S, bool ANISO>
+static cudaError_t bin_dr_strip_sw(const BinProblem& P, const BinState<S>& A,
+                                   const BinState<S>& B, const DrCoef& D, cudaStream_t st) {
+    switch (D.sweeps) {
+        case 1: return launch_bin_dr_strip<S, ANISO, 1>(P, A, B, D, st);
+        case 2: return launch_bin_dr_strip<S, ANISO, 2>(P, A, B, D, st);
+        case 3: return launch_bin_dr_strip<S, ANISO, 3>(P, A, B, D, st);
+        default: return launch_bin_dr_strip<S, ANISO, 4>(P, A, B, D, st);
+    }
+}
+
+template <typename S>
+static cudaError_t bin_dr_strip_s(const BinProblem& P, const BinStateV& a, const BinStateV& b,
+                                  bool aniso, const DrCoef& D, cudaStream_t st) {
+    const BinState<S> A = a.as<S>(), B = b.as<S>();
+    return aniso ? bin_dr_strip_sw<S, true>(P, A, B, D, st)
+                 : bin_dr_strip_sw<S, false>(P, A, B, D, st);
+}
+
+cudaError_t binary_dr_strip_step(int storage, const BinProblem& P, const BinStateV& a,
+                                 const BinStateV& b, bool aniso, const DrCoef& D,
+                                 cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32: return bin_dr_strip_s<float>(P, a, b, aniso, D, st);
+        case CMF_F16: return bin_dr_strip_s<__half>(P, a, b, aniso, D, st);
+        default: return bin_dr_strip_s<__nv_bfloat16>(P, a, b, aniso, D, st);
     }
 }
 

@@ -190,6 +190,26 @@ struct DrCoef {
     int sweeps;
 };
 
+// rPDRQ flow steps and reflections of one pixel (Eq. iteration:quadratic:seg):
+// q = qbar - tau grad u, p_t = pbar_t + tau u, p_s = pbar_s - tau u, then
+// qbar += rho (P_alpha(2q - qbar) - q), pbar_t += rho (min(2p_t - pbar_t, C_t)
+// - p_t), pbar_s += rho (min(2p_s - pbar_s + tau, C_s) - p_s).
+template <typename S, bool ANISO>
+__device__ __forceinline__ void binary_dr_flows(const DrCoef& D, float uc, float gx, float gy,
+                                                float qbx, float qby, float pbs, float pbt,
+                                                float al, float cs, float ct, float& oqx,
+                                                float& oqy, float& ops, float& opt) {
+    const float q1 = qbx - D.tau * gx, q2 = qby - D.tau * gy;
+    float tx = 2.f * q1 - qbx, ty = 2.f * q2 - qby;
+    project_alpha<ANISO>(tx, ty, al);
+    oqx = qbx + D.rho * (tx - q1);
+    oqy = qby + D.rho * (ty - q2);
+    const float pt1 = pbt + D.tau * uc, ps1 = pbs - D.tau * uc;
+    opt = pbt + D.rho * (fminf(2.f * pt1 - pbt, ct) - pt1);
+    ops = pbs + D.rho * (fminf(2.f * ps1 - pbs + D.tau, cs) - ps1);
+}
+
+
 AdmmCoef make_admm_coef(const cmf_params& p, int L);
 DrCoef make_dr_coef(const cmf_params& p, int L, bool potts);
 

@@ -144,6 +144,10 @@ bool binary_strip_eligible(const Grid& G, int storage, const float* Cs, const fl
 cudaError_t binary_strip_step(int storage, const BinProblem& P, const BinStateV& a,
                               const BinStateV& b, bool aniso, const AdmmCoef& K,
                               cudaStream_t st);
+// rPDRQ iteration a -> b with the pipelined red-black sweeps.
+cudaError_t binary_dr_strip_step(int storage, const BinProblem& P, const BinStateV& a,
+                                 const BinStateV& b, bool aniso, const DrCoef& D,
+                                 cudaStream_t st);
 // Certificates of a strip-eligible state into eval_blocks(H, W) partials.
 cudaError_t binary_eval_strip(int storage, const BinProblem& P, const BinStateV& s, bool aniso,
                               bool dr, float tau, double* partials, cudaStream_t st);

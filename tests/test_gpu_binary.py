@@ -280,7 +280,7 @@ STRIP_CASES = {
 }
 
 
-@pytest.mark.parametrize("algo", [0, 1, 2, 4, 5])
+@pytest.mark.parametrize("algo", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("case", list(STRIP_CASES))
 def test_strip_matches_oracle_f32(cmf, case, algo):
     inst, n = STRIP_CASES[case]
@@ -304,7 +304,7 @@ def test_strip_anisotropic(cmf, algo):
 @pytest.mark.parametrize("shape", [(70, 98), (5, 130), (130, 6)])
 def test_strip_matches_smem_tiles_half(cmf, storage, shape):
     inst = synth.random_binary(*shape, seed=91, alpha=0.3, field_alpha=True)
-    for algo in (0, 2):
+    for algo in (0, 2, 3):
         a = _gpu_run(cmf, inst, algo, 9, storage=storage, variant=1).state()
         b = _gpu_run(cmf, inst, algo, 9, storage=storage, variant=2).state()
         for k in a:
@@ -372,3 +372,17 @@ def test_strip_certificates_full_size(cmf, aniso):
     assert abs(E - Eo) <= 1e-6 * abs(Eo)
     assert abs(D - Do) <= 1e-6 * abs(Eo)
     assert abs(res - reso) <= 1e-5 * reso + 1e-6
+
+
+@pytest.mark.parametrize("sweeps", [1, 2, 3, 4])
+@pytest.mark.parametrize("aniso", [0, 1])
+def test_strip_dr_sweeps(cmf, sweeps, aniso):
+    """rPDRQ with 1..4 symmetric red-black sweeps per iteration through the
+    pipelined strip kernel (1 + 2 sweeps half-sweep stages) against the
+    oracle; the grid spans several strips and bands."""
+    inst = synth.random_binary(150, 130, seed=92, alpha=0.35, field_alpha=True)
+    b = _gpu_run(cmf, inst, 3, 21, variant=2, sweeps=sweeps, aniso=aniso)
+    ref, _ = _oracle_run(inst, 3, 21, aniso=aniso, sweeps=sweeps)
+    got = b.state()
+    for k in ("u", "qx", "qy", "ps", "pt"):
+        assert np.abs(got[k] - ref[k]).max() <= TOL_U, k
