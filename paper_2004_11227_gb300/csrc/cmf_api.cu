@@ -350,7 +350,7 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.strip = false;
     // automatic choice: warp strips where the layout allows them (fastest on
     // every measured Potts case), else TMA tiles, else shared-memory tiles
-    if (!call.cfg.dr && !call.cfg.plain && (p->variant == 2 || p->variant == 0)) {
+    if (!call.cfg.plain && (p->variant == 2 || p->variant == 0)) {
         const bool ok = potts_strip_eligible(call.P.g, p->storage, C, alpha, call.user, call.ws);
         if (!ok && p->variant == 2)
             return CMF_EINVAL;  // warp strips requested but the layout does not allow them
@@ -382,6 +382,12 @@ cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st) {
             cudaError_t e = potts_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur = 0;
+        } else if (c.strip && c.cfg.dr) {
+            const PottsStateV& a = cur == 0 ? c.user : c.ws;
+            const PottsStateV& b = cur == 0 ? c.ws : c.user;
+            cudaError_t e = potts_dr_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.dc, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
         } else if (c.strip) {
             const PottsStateV& a = cur == 0 ? c.user : c.ws;
             const PottsStateV& b = cur == 0 ? c.ws : c.user;

@@ -164,6 +164,10 @@ cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStat
 // Certificates of a strip-eligible state into eval_blocks(H, W) partials.
 cudaError_t potts_eval_strip(int storage, const PottsProblem& P, const PottsStateV& s,
                              bool aniso, bool dr, float tau, double* partials, cudaStream_t st);
+// rPDRQ iteration a -> b with the pipelined red-black sweeps (all labels).
+cudaError_t potts_dr_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
+                                const PottsStateV& b, bool aniso, const DrCoef& D,
+                                cudaStream_t st);
 // s.u_i += cu * s.p_s on every label (w back to u).
 cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const PottsStateV& s,
                                  float cu, cudaStream_t st);
