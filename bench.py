@@ -246,6 +246,43 @@ def potts_workloads(cmf, synth, flush) -> dict:
     return out
 
 
+def batch_workload(cmf, synth, flush) -> dict:
+    """256 instances of uneven size (64^2..1024^2) and label count (2, 3, 4,
+    8) solved as one batch (one graph, per-instance convergence masks) to the
+    1e-4 gap with fused float32 rpADMMII: the time of the whole batch and the
+    aggregate pixel*label*iterations/s (each instance counted to its own
+    stopping iteration)."""
+    import torch
+
+    insts = synth.batch_instances()
+    p = cmf.default_params(2, 2, tol_gap=1e-4, max_iter=5000, check_every=10)
+    items = [cmf.alloc_binary(i, p) if i.kind == "binary" else cmf.alloc_potts(i, p)
+             for i in insts]
+    for it in items:  # the single-solve workspaces are not used by the batch
+        it.ws = torch.empty(0, dtype=torch.uint8, device=it.u.device)
+    torch.cuda.empty_cache()
+    batch = cmf.Batch(items, p)
+    batch.solve()  # warm (graph instantiation, module load)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, res = batch.solve()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    units = sum(i.H * i.W * i.L * r["iters"] for i, r in zip(insts, res))
+    iters = [r["iters"] for r in res]
+    out = {"instances": len(insts), "time_ms": round(ms, 2), "px_label_it_per_s": units / ms * 1e3,
+           "converged": sum(1 for r in res if r["status"] == cmf.OK),
+           "iters_min": min(iters), "iters_median": int(np.median(iters)), "iters_max": max(iters),
+           "label_pixels": sum(i.H * i.W * i.L for i in insts)}
+    del batch, items
+    torch.cuda.empty_cache()
+    return out
+
+
 def precision_study(size: int, max_iter: int):
     """Convergence of the 16-label Voronoi workload (edge-weighted alpha) at
     size x size under float32, float16 and bfloat16 flow storage: one JSON
@@ -496,6 +533,7 @@ def main():
     plain_ms = ttg["rpADMMII_plain"]["ms"]
 
     potts = potts_workloads(cmf, synth, flush) if rank == 0 and not args.skip_potts else {}
+    batch = batch_workload(cmf, synth, flush) if rank == 0 and not args.skip_potts else {}
 
     if rank == 0:
         rate, dt = cpu_oracle_rate(inst, 150)
@@ -523,6 +561,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "px*label*it/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "potts_workloads": potts,
+            "batch_workload": batch,
             "gpu_launches": launches,
             "clocks": clocks,
         }

@@ -338,41 +338,50 @@ def cmf_solve_potts(s: Potts, hist_cap: int = 4096, stream=None):
     return st, iters.value, hist[:n]
 
 
+class Batch:
+    """The C instance table, the stacked binary costs and the workspace of a
+    batch, built once so that repeated solves call only the library."""
+
+    def __init__(self, items, params: Params):
+        n = len(items)
+        self.items, self.params = items, params
+        self.insts = (Instance * n)()
+        self.keep = []
+        for i, it in enumerate(items):
+            d = self.insts[i]
+            if isinstance(it, Binary):
+                cost = torch.stack([it.Cs, it.Ct]).contiguous()
+                self.keep.append(cost)
+                d.model, d.L = 0, 2
+                d.d_p, d.d_ps = _ptr(it.pt), _ptr(it.ps)
+            else:
+                cost = it.C
+                d.model, d.L = 1, it.L
+                d.d_p, d.d_ps = _ptr(it.p), _ptr(it.ps)
+            d.H, d.W, d.pitch = it.H, it.W, it.pitch
+            d.d_cost = _ptr(cost)
+            d.d_alpha = _ptr(it.alpha)
+            d.alpha0 = it.alpha0
+            d.d_u, d.d_qx, d.d_qy = _ptr(it.u), _ptr(it.qx), _ptr(it.qy)
+        nb = int(lib().cmf_batch_workspace_bytes(self.insts, n, ctypes.byref(params)))
+        if nb == 0:
+            raise CmfError("cmf_batch_workspace_bytes: invalid batch or parameters")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=items[0].u.device)
+
+    def solve(self, stream=None):
+        st = _check(lib().cmf_solve_batch(self.insts, len(self.items), ctypes.byref(self.params),
+                                          _ptr(self.ws), self.ws.numel(), _stream(stream)),
+                    "cmf_solve_batch", allow=(OK, NOT_CONVERGED))
+        res = [dict(iters=d.iters, status=d.status, energy=d.energy, dual=d.dual, gap=d.gap,
+                    res=d.res) for d in self.insts]
+        return st, res
+
+
 def cmf_solve_batch(items, params: Params, stream=None):
     """Solve a list of Binary / Potts containers as one batch.  Returns
     (status, [per-instance result dicts]); the containers' state tensors hold
     the solutions."""
-    n = len(items)
-    insts = (Instance * n)()
-    keep = []
-    for i, it in enumerate(items):
-        d = insts[i]
-        if isinstance(it, Binary):
-            cost = torch.stack([it.Cs, it.Ct]).contiguous()
-            keep.append(cost)
-            d.model, d.L = 0, 2
-            d.d_p, d.d_ps = _ptr(it.pt), _ptr(it.ps)
-        else:
-            cost = it.C
-            d.model, d.L = 1, it.L
-            d.d_p, d.d_ps = _ptr(it.p), _ptr(it.ps)
-        d.H, d.W, d.pitch = it.H, it.W, it.pitch
-        d.d_cost = _ptr(cost)
-        d.d_alpha = _ptr(it.alpha)
-        d.alpha0 = it.alpha0
-        d.d_u, d.d_qx, d.d_qy = _ptr(it.u), _ptr(it.qx), _ptr(it.qy)
-    nb = int(lib().cmf_batch_workspace_bytes(insts, n, ctypes.byref(params)))
-    if nb == 0:
-        raise CmfError("cmf_batch_workspace_bytes: invalid batch or parameters")
-    dev = items[0].u.device
-    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
-    st = _check(lib().cmf_solve_batch(insts, n, ctypes.byref(params), _ptr(ws), nb,
-                                      _stream(stream)),
-                "cmf_solve_batch", allow=(OK, NOT_CONVERGED))
-    res = [dict(iters=d.iters, status=d.status, energy=d.energy, dual=d.dual, gap=d.gap,
-                res=d.res) for d in insts]
-    del keep
-    return st, res
+    return Batch(items, params).solve(stream)
 
 
 def cmf_autotune_binary(b: Binary, stream=None):
