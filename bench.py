@@ -181,12 +181,15 @@ KERNEL_CASES = {
 }
 
 
-def algorithmic_bytes_per_px(model: str, L: int, storage: int, alpha_field: bool) -> int:
-    """State read + written once, costs and alpha read once (halos excluded)."""
+def algorithmic_bytes_per_px(model: str, L: int, storage: int, alpha_field: bool,
+                             levels: bool = False) -> int:
+    """State read + written once, costs and alpha read once (halos excluded);
+    with levels the L cost planes are replaced by one image plane."""
     s = 4 if storage == 0 else 2
     if model == "binary":
         return 4 * 2 + 4 * s * 2 + 8 + (4 if alpha_field else 0)
-    return L * (4 * 2 + 3 * s * 2 + 4) + 2 * s + (4 if alpha_field else 0)
+    costs = 4 if levels else 4 * L
+    return L * (4 * 2 + 3 * s * 2) + costs + 2 * s + (4 if alpha_field else 0)
 
 
 def potts_workloads(cmf, synth, flush) -> dict:
@@ -233,12 +236,30 @@ def potts_workloads(cmf, synth, flush) -> dict:
         st, iters, hist = cmf.cmf_solve_potts(s)
         e1.record()
         e1.synchronize()
+        ttg_ms = e0.elapsed_time(e1)
+        # the same iteration with the costs computed from (I, levels) in the kernels
+        p_lev = cmf.default_params(2, inst.L, storage=storage)
+        s_lev = cmf.alloc_potts_levels(inst.image.astype(np.float32),
+                                       np.asarray(inst.levels, np.float32), inst.alpha, p_lev)
+        cmf.cmf_init_potts(s_lev)
+        cmf.cmf_iterate_potts(s_lev, 10)
+        torch.cuda.synchronize()
+        e0.record()
+        cmf.cmf_iterate_potts(s_lev, n)
+        e1.record()
+        e1.synchronize()
+        ms_lev = e0.elapsed_time(e1) / n
+        nb_lev = algorithmic_bytes_per_px("potts", inst.L, storage,
+                                          isinstance(inst.alpha, np.ndarray), True) * inst.H * inst.W
+        del s_lev
         out[name] = {
+            "ms_per_iter_costs_from_levels": round(ms_lev, 4),
+            "algorithmic_GBps_costs_from_levels": nb_lev / ms_lev / 1e6,
             "ms_per_iter": round(ms, 4),
             "px_label_it_per_s": inst.H * inst.W * inst.L / ms * 1e3,
             "algorithmic_GBps": nb / ms / 1e6, "hbm_frac_of_measured": nb / ms / 1e6 / peak,
             "bytes_per_px": nb // (inst.H * inst.W),
-            "time_to_gap_ms": round(e0.elapsed_time(e1), 2), "iterations": iters,
+            "time_to_gap_ms": round(ttg_ms, 2), "iterations": iters,
             "converged": st == cmf.OK, "final_gap": float(hist[-1, 3]),
         }
         del s

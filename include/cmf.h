@@ -131,6 +131,12 @@ typedef struct {
     double sigma;      /* rPDRQ step sizes                                     */
     double tau;
     double tol_gap;    /* cmf_solve_*: stop when the relative gap <= tol_gap   */
+    int costs;         /* Potts cost input: 0 = L cost planes [L][H][pitch] at
+                          d_C; 1 = computed where read (no counterpart in the
+                          paper's statement, which takes the costs as given):
+                          d_C holds one image plane I [H][pitch] followed by the
+                          L levels c_i (floats), and C_i(x) = (I(x) - c_i)^2.
+                          Binary calls and batches need 0.                    */
 } cmf_params;
 
 /* Fill *p with the paper's defaults for `algo` and L labels (L = 2 for the

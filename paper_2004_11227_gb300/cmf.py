@@ -41,6 +41,7 @@ class Params(ctypes.Structure):
         ("c", ctypes.c_double), ("a", ctypes.c_double), ("a1", ctypes.c_double),
         ("a2", ctypes.c_double), ("rho", ctypes.c_double), ("r", ctypes.c_double),
         ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("tol_gap", ctypes.c_double),
+        ("costs", ctypes.c_int),
     ]
 
 
@@ -265,6 +266,24 @@ def alloc_binary(inst, params: Params, device="cuda") -> Binary:
 
 def alloc_potts(inst, params: Params, device="cuda") -> Potts:
     return Potts(inst.costs, inst.alpha, params, device)
+
+
+def alloc_potts_levels(I, levels, alpha, params: Params, device="cuda") -> Potts:
+    """A Potts problem whose costs C_i = (I - levels[i])^2 the kernels compute
+    where they read them (params.costs = 1): the cost buffer holds the image
+    plane followed by the levels."""
+    I = np.asarray(I, dtype=np.float32)
+    lev = np.asarray(levels, dtype=np.float32)
+    H, W = I.shape
+    params.costs = 1
+    # shape the container as an L-label problem, then replace its cost buffer
+    pot = Potts(np.zeros((len(lev), H, W), np.float32), alpha, params, device)
+    pitch = pot.pitch
+    buf = torch.zeros(H * pitch + len(lev), dtype=torch.float32, device=device)
+    buf[:H * pitch].view(H, pitch)[:, :W] = torch.as_tensor(I, device=device)
+    buf[H * pitch:] = torch.as_tensor(lev, device=device)
+    pot.C = buf
+    return pot
 
 
 # --- C-ABI calls (same names as include/cmf.h) --------------------------------------

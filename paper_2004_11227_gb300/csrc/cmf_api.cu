@@ -80,6 +80,7 @@ cmf_status check_params(const cmf_params* p, int L) {
     if (p->variant != 0 && p->variant != 1 && p->variant != 2 && p->variant != 8 &&
         p->variant != 16 && p->variant != 32)
         return CMF_EINVAL;
+    if (p->costs != 0 && p->costs != 1) return CMF_EINVAL;
     (void)L;
     return CMF_OK;
 }
@@ -159,6 +160,7 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
                           BinaryCall& call) {
     cmf_status s;
     if ((s = check_params(p, 2)) != CMF_OK) return s;
+    if (p->costs != 0) return CMF_EINVAL;  // binary costs are planes
     if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
     if (!Cs || !Ct || !u || !qx || !qy || !ps || !pt || !ws) return CMF_EINVAL;
     if (!alpha && !(alpha0 >= 0.0f && isfinite(alpha0))) return CMF_EINVAL;
@@ -339,7 +341,9 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     if (!aligned(ws, kAlign)) return CMF_EINVAL;
     call.w = ws_layout(H, W, L, pitch, *p, true);
     if (ws_bytes < call.w.total) return CMF_ENOMEM;
-    call.P = PottsProblem{C, L, make_alpha(alpha, alpha0), make_grid(H, W, pitch)};
+    // costs == 1: d_C holds the image plane followed by the L levels
+    call.P = PottsProblem{C, L, make_alpha(alpha, alpha0), make_grid(H, W, pitch),
+                          p->costs == 1 ? C + (size_t)H * (size_t)pitch : nullptr};
     call.user = PottsStateV{u, qx, qy, pp, ps};
     call.wsbase = (char*)ws;
     call.ws = ws_potts_state(call.wsbase, call.w, call.P.g, L, p->storage);
@@ -718,7 +722,8 @@ cmf_status cmf_init_potts(const float* d_C, int L, int H, int W, int pitch, cons
     if ((s = check_params(p, L)) != CMF_OK) return s;
     if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
     if (!d_C || !d_u || !d_qx || !d_qy || !d_p || !d_ps) return CMF_EINVAL;
-    PottsProblem P{d_C, L, make_alpha(nullptr, 0.f), make_grid(H, W, pitch)};
+    PottsProblem P{d_C, L, make_alpha(nullptr, 0.f), make_grid(H, W, pitch),
+                   p->costs == 1 ? d_C + (size_t)H * (size_t)pitch : nullptr};
     PottsStateV st{d_u, d_qx, d_qy, d_p, d_ps};
     CMF_CUDA_TRY(potts_init(p->storage, P, st, p->algo == CMF_RPDRQ, (float)p->tau,
                             (cudaStream_t)stream));

@@ -177,6 +177,7 @@ cmf_status check_instance(const cmf_instance& in, const cmf_params& p) {
 cmf_status check_batch_params(const cmf_params* p) {
     if (!p) return CMF_EINVAL;
     if (p->algo < CMF_PADMM || p->algo > CMF_CP) return CMF_EINVAL;
+    if (p->costs != 0) return CMF_EINVAL;  // batches take cost planes
     if (p->storage < CMF_F32 || p->storage > CMF_BF16) return CMF_EINVAL;
     if (p->impl != CMF_FUSED) return CMF_EINVAL;  // the batch runs the fused kernels
     if (p->sweeps != 1) return CMF_EINVAL;  // batched rPDRQ runs one sRBGS sweep
@@ -259,7 +260,7 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
             for (int t = 0; t < ntx * ((in.H + 31) / 32); ++t) tb.push_back(i);
             for (int t = 0; t < D.ev_count; ++t) eb.push_back(i);
         } else {
-            D.pp = PottsProblem{in.d_cost, in.L, A, G};
+            D.pp = PottsProblem{in.d_cost, in.L, A, G, nullptr};
             D.pu = PottsStateV{in.d_u, in.d_qx, in.d_qy, in.d_p, in.d_ps};
             char* b = sbase;
             D.pw.u = (float*)b;

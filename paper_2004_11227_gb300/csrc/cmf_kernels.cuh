@@ -41,13 +41,24 @@ struct BinStateV {
     }
 };
 
-// Potts problem data: L cost planes.
+// Potts problem data: L cost planes, or (lev != NULL) one image plane I in C
+// and L levels with C_i(x) = (I(x) - lev[i])^2 computed where it is read.
 struct PottsProblem {
     const float* C;
     int L;
     Alpha alpha;
     Grid g;
+    const float* lev;
 };
+
+// Cost of label l at plane offset k.
+__device__ __forceinline__ float potts_cost(const PottsProblem& P, int l, size_t k) {
+    if (P.lev) {
+        const float d = __ldg(P.C + k) - __ldg(P.lev + l);
+        return d * d;
+    }
+    return __ldg(P.C + (size_t)l * P.g.plane + k);
+}
 
 template <typename S>
 struct PottsState {

@@ -17,12 +17,11 @@ namespace cmf {
     const size_t k = G.idx(r, c);
 
 // First cheapest label at plane offset k (ties to the lowest index).
-__device__ __forceinline__ int argmin_label(const float* C, size_t plane, int L, size_t k,
-                                            float& m) {
+__device__ __forceinline__ int argmin_label(const PottsProblem& P, size_t k, float& m) {
     int best = 0;
-    m = __ldg(C + k);
-    for (int i = 1; i < L; ++i) {
-        const float v = __ldg(C + i * plane + k);
+    m = potts_cost(P, 0, k);
+    for (int i = 1; i < P.L; ++i) {
+        const float v = potts_cost(P, i, k);
         if (v < m) {
             m = v;
             best = i;
@@ -42,10 +41,10 @@ __global__ void k_potts_init(PottsProblem P, PottsState<S> s, float tau) {
     using St = Store<S>;
     const size_t pl = G.plane;
     float m, mr, md;
-    const int best = argmin_label(P.C, pl, P.L, k, m);
+    const int best = argmin_label(P, k, m);
     int bestr = -1, bestd = -1;
-    if (DR && c < G.W - 1) bestr = argmin_label(P.C, pl, P.L, k + 1, mr);
-    if (DR && r < G.H - 1) bestd = argmin_label(P.C, pl, P.L, k + G.pitch, md);
+    if (DR && c < G.W - 1) bestr = argmin_label(P, k + 1, mr);
+    if (DR && r < G.H - 1) bestd = argmin_label(P, k + G.pitch, md);
     for (int i = 0; i < P.L; ++i) {
         const size_t ki = i * pl + k;
         const float u = i == best ? 1.f : 0.f;
@@ -159,7 +158,7 @@ __device__ __forceinline__ void potts_admm_tile(PottsProblem P, PottsState<S> s0
                 const float p0 = St::ld(s0.p + lo + k);
                 const float u0 = __ldg(s0.u + lo + k);
                 const float p1 = potts_label_pu<S>(K, g_s[ly + 1][lx + 1], d, p0, ps0, u0,
-                                                   __ldg(P.C + lo + k), accd[j], accp[j], v);
+                                                   potts_cost(P, l, k), accd[j], accp[j], v);
                 St::st(s1.p + lo + k, p1);
             }
             v_s[(l * TY + ly) * TX + lx] = v;
@@ -256,7 +255,7 @@ __global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* g
         const size_t ki = l * pl + k;
         float v;
         const float p1 = potts_label_pu<S>(K, g[ki], d[ki], St::ldw(s.p + ki), ps0, s.u[ki],
-                                           __ldg(P.C + ki), acc_a, acc_b, v);
+                                           potts_cost(P, l, k), acc_a, acc_b, v);
         St::st(s.p + ki, p1);
         s.u[ki] = v;
     }
@@ -375,7 +374,7 @@ __device__ __forceinline__ void potts_dr_tile(PottsProblem P, PottsState<S> s0, 
                 s1.u[lo + k] = uc;
                 St::st(s1.qx + lo + k, qbx + D.rho * (tx - q1));
                 St::st(s1.qy + lo + k, qby + D.rho * (ty - q2));
-                St::st(s1.p + lo + k, pb + D.rho * (fminf(2.f * p1 - pb, __ldg(P.C + lo + k)) - p1));
+                St::st(s1.p + lo + k, pb + D.rho * (fminf(2.f * p1 - pb, potts_cost(P, l, k)) - p1));
                 usum[j] += uc;
             }
         }
@@ -434,7 +433,7 @@ __global__ void k_potts_plain_dr_flows(PottsProblem P, PottsState<S> s, int l, D
     St::st(s.qy + lo + k, qby + D.rho * (ty - q2));
     const float pb = St::ldw(s.p + lo + k);
     const float p1 = pb + D.tau * uc;
-    St::st(s.p + lo + k, pb + D.rho * (fminf(2.f * p1 - pb, __ldg(P.C + lo + k)) - p1));
+    St::st(s.p + lo + k, pb + D.rho * (fminf(2.f * p1 - pb, potts_cost(P, l, k)) - p1));
 }
 
 template <typename S>
@@ -519,7 +518,7 @@ __device__ __forceinline__ void potts_eval_tile(PottsProblem P, PottsState<S> s,
             const float gx = c < G.W - 1 ? fmaxf(s.u[lo + k + 1] - thr, 0.f) - ub : 0.f;
             const float gy = r < G.H - 1 ? fmaxf(s.u[lo + k + G.pitch] - thd, 0.f) - ub : 0.f;
             const float tv = ANISO ? fabsf(gx) + fabsf(gy) : sqrtf(gx * gx + gy * gy);
-            const float Cl = __ldg(P.C + lo + k);
+            const float Cl = potts_cost(P, l, k);
             e += ub * Cl + al * tv;
             float fx, fy, fxl = 0.f, fyl = 0.f, fxu = 0.f, fyu = 0.f;
             potts_flow_at<S, DR>(P, s, tau, lo, r, c, fx, fy);

@@ -44,7 +44,9 @@ struct RowVals {
 
 }  // namespace
 
-template <typename S, bool ANISO>
+// LEV: the costs come from (I, levels) (P.lev set); a separate instantiation
+// keeps the cost-plane kernel free of the extra registers and branches.
+template <typename S, bool ANISO, bool LEV>
 __global__ void __launch_bounds__(kStripWarps * 32, 7)
     k_potts_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, float cu_in,
                   int R, int nstrips, int nitems) {
@@ -126,14 +128,22 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7)
             const S* qy0 = s0.qy + lo;
             const S* p0 = s0.p + lo;
             const float* w0 = s0.u + lo;
-            const float* Cl = P.C + lo;
+            // costs of label l: its plane, or (I - c_l)^2 from the image plane
+            const float* Cb = LEV ? P.C : P.C + lo;
+            const float lev_l = LEV ? __ldg(P.lev + l) : 0.f;
             S* qx1 = s1.qx + lo;
             S* qy1 = s1.qy + lo;
             S* p1o = s1.p + lo;
             float* w1 = s1.u + lo;
             auto row = [&](int r, RowVals<S>& x) { load_row(qx0, qy0, p0, w0, r, x); };
             auto ld_c = [&](int r) {
-                return (colin && r >= 0 && r < G.H) ? PF::ld(Cl + r * G.pitch + c) : PF::zero();
+                float2 v =
+                    (colin && r >= 0 && r < G.H) ? PF::ld(Cb + r * G.pitch + c) : PF::zero();
+                if (LEV) {  // (zero outside the grid is never used)
+                    v.x = (v.x - lev_l) * (v.x - lev_l);
+                    v.y = (v.y - lev_l) * (v.y - lev_l);
+                }
+                return v;
             };
             auto ld_al = [&](int r) {
                 if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
@@ -299,7 +309,18 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             float2 in_ps = ld_s(s0.ps, m_first);
             const int t_first = m_first - NS - 1;
             float2 f_qx = ld_s(qx0, t_first), f_qy = ld_s(qy0, t_first);
-            float2 f_p = ld_s(p0, t_first), f_c = ld_f(P.C + lo, t_first), f_al = ld_al(t_first);
+            // costs of label l: its plane, or (I - c_l)^2 from the image plane
+            const float* Cb = P.lev ? P.C : P.C + lo;
+            const float lev_l = P.lev ? __ldg(P.lev + l) : 0.f;
+            auto ld_cost = [&](int r) {
+                float2 v = ld_f(Cb, r);
+                if (P.lev && ok_row(r)) {
+                    v.x = (v.x - lev_l) * (v.x - lev_l);
+                    v.y = (v.y - lev_l) * (v.y - lev_l);
+                }
+                return v;
+            };
+            float2 f_p = ld_s(p0, t_first), f_c = ld_cost(t_first), f_al = ld_al(t_first);
 #pragma unroll 1
             for (int m = m_first; m <= m_last; ++m) {
 #pragma unroll
@@ -384,7 +405,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                     f_qx = ld_s(qx0, r);
                     f_qy = ld_s(qy0, r);
                     f_p = ld_s(p0, r);
-                    f_c = ld_f(P.C + lo, r);
+                    f_c = ld_cost(r);
                     f_al = ld_al(r);
                 }
             }
@@ -433,11 +454,11 @@ bool potts_strip_eligible(const Grid& G, int storage, const float* C, const floa
     return true;
 }
 
-template <typename S, bool ANISO>
+template <typename S, bool ANISO, bool LEV>
 static cudaError_t launch_strip(const PottsProblem& P, const PottsState<S>& a,
                                 const PottsState<S>& b, const AdmmCoef& K, float cu_in,
                                 cudaStream_t st) {
-    auto kern = k_potts_strip<S, ANISO>;
+    auto kern = k_potts_strip<S, ANISO, LEV>;
     static int resident = 0;  // warps resident on the whole device
     if (!resident) {
         int dev = 0, sms = 0, blocks = 0;
@@ -468,8 +489,11 @@ static cudaError_t strip_step_s(const PottsProblem& P, const PottsStateV& a,
                                 const PottsStateV& b, bool aniso, const AdmmCoef& K,
                                 float cu_in, cudaStream_t st) {
     const PottsState<S> A = a.as<S>(), B = b.as<S>();
-    return aniso ? launch_strip<S, true>(P, A, B, K, cu_in, st)
-                 : launch_strip<S, false>(P, A, B, K, cu_in, st);
+    if (P.lev)
+        return aniso ? launch_strip<S, true, true>(P, A, B, K, cu_in, st)
+                     : launch_strip<S, false, true>(P, A, B, K, cu_in, st);
+    return aniso ? launch_strip<S, true, false>(P, A, B, K, cu_in, st)
+                 : launch_strip<S, false, false>(P, A, B, K, cu_in, st);
 }
 
 cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
@@ -676,6 +700,8 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             const float* ul = s.u + lo;
             const S* qxl = s.qx + lo;
             const S* qyl = s.qy + lo;
+            const float* Cb = P.lev ? P.C : P.C + lo;
+            const float lev_l = P.lev ? __ldg(P.lev + l) : 0.f;
             // flows y of row r (zero outside the grid); every lane shuffles
             auto flows = [&](int r, float2 u_r, float2 u_d, float2& f_x, float2& f_y) {
                 f_x = ld_s(qxl, r);
@@ -703,7 +729,11 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             for (int t = r0; t < r1; ++t) {
                 u_n = ld_f(ul, t + 1);
                 const float2 th_n = th_s[wib][t + 1 - r0][lane];
-                const float2 Cl = ld_f(P.C + lo, t);
+                float2 Cl = ld_f(Cb, t);
+                if (P.lev && ok_row(t)) {
+                    Cl.x = (Cl.x - lev_l) * (Cl.x - lev_l);
+                    Cl.y = (Cl.y - lev_l) * (Cl.y - lev_l);
+                }
                 float2 fp = ld_s(s.p + lo, t), fs = ld_s(s.ps, t);
                 al = ld_al(t);
                 flows(t, u_t, u_n, fx, fy);

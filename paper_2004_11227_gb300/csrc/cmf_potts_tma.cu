@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
         S* qx_out = s1.qx + lo;
         S* qy_out = s1.qy + lo;
         S* p_out = s1.p + lo;
-        const float* C_l = P.C + lo;
 
         // g_l = div q_l + p_l - p_s - u_l / c (zero-filled outside the grid)
 #pragma unroll
@@ -227,7 +226,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
             const float p0 = sload(sp + so);
             const float u0 = su[(ly + 2) * BXU + lx + XO];
             const bool own = o_k[j] >= 0;
-            const float cl = __ldg(C_l + (own ? o_k[j] : 0));
+            const float cl = potts_cost(P, l, own ? (size_t)o_k[j] : 0);
             float v;
             const float p1 = potts_label_pu<S>(K, g_s[(ly + 1) * GW + lx + 1], d, p0, ps0, u0, cl,
                                                accd[j], accp[j], v);

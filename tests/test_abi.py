@@ -84,12 +84,18 @@ def test_bad_arguments_rejected_without_launch(cmf):
     assert lib.cmf_iterate_binary(ptr, ptr, None, 0.5, 8, 8, 8, P, 1, None, ptr, ptr, ptr, ptr,
                                   ptr, 1 << 20, None) == cmf.EINVAL
     for bad in [dict(algo=9), dict(storage=5), dict(impl=3), dict(sweeps=0), dict(c=0.0),
-                dict(rho=2.0), dict(rho=0.0), dict(check_every=0), dict(sweeps=5)]:
+                dict(rho=2.0), dict(rho=0.0), dict(check_every=0), dict(sweeps=5),
+                dict(costs=1), dict(costs=2)]:
         q = cmf.default_params(cmf.RPADMM_EB, 2)
         for k, v in bad.items():
             setattr(q, k, v)
         assert lib.cmf_iterate_binary(ptr, ptr, None, 0.5, 8, 8, 8, ctypes.byref(q), 1, ptr,
                                       ptr, ptr, ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL, bad
+    # Potts: unknown cost input
+    pc = cmf.default_params(cmf.RPADMM_EB, 4)
+    pc.costs = 2
+    assert lib.cmf_iterate_potts(ptr, 4, None, 0.5, 8, 8, 8, ctypes.byref(pc), 1, ptr, ptr, ptr,
+                                 ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL
     # Potts: L out of range
     pp = cmf.default_params(cmf.RPADMM_EB, 4)
     assert lib.cmf_iterate_potts(ptr, 1, None, 0.5, 8, 8, 8, ctypes.byref(pp), 1, ptr, ptr, ptr,

@@ -374,3 +374,64 @@ def test_strip_dr_full_size_2048_L4_windows(cmf):
     inst = synth.config3()
     wins = [(0, 0, 40, 40), (2048 - 37, 2048 - 45, 37, 45), (1000, 1500, 64, 64)]
     _window_step_check(cmf, inst, 3, 23, wins, variant=2)
+
+
+# ---- costs computed from (I, levels) where they are read (params.costs = 1) ---------
+
+def _levels_inputs(inst):
+    """float32 image and levels, and the float32 cost planes the kernels
+    compute from them: (I - c_i)^2 with one rounding per operation."""
+    I = inst.image.astype(np.float32)
+    lev = np.asarray(inst.levels, dtype=np.float32)
+    C = np.stack([(I - c) * (I - c) for c in lev]).astype(np.float32)
+    return I, lev, C
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("shape", [(48, 40), (45, 71), (1, 64)])
+def test_levels_costs_match_oracle(cmf, algo, shape):
+    """Costs from the image and the levels (strip kernels for even widths,
+    TMA or tile kernels for odd ones) against the oracle given the same
+    float32 cost planes; certificates too."""
+    inst = synth.config3(*shape)
+    I, lev, C = _levels_inputs(inst)
+    p = cmf.default_params(algo, 4)
+    s = cmf.alloc_potts_levels(I, lev, inst.alpha, p)
+    cmf.cmf_init_potts(s)
+    cmf.cmf_iterate_potts(s, 27)
+    got = s.state()
+    ref = O.potts_run(C, inst.alpha, O.default_params(algo, 4), 27)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        assert np.abs(got[k] - ref[k]).max() <= TOL_U, k
+    E, D, gap, res = cmf.cmf_eval_potts(s)
+    Eo, Do, gapo, reso = O.potts_eval(C, inst.alpha, got, O.default_params(algo, 4))
+    assert abs(E - Eo) <= 1e-5 * abs(Eo) and abs(D - Do) <= 1e-5 * abs(Eo)
+
+
+@pytest.mark.parametrize("algo,storage", [(2, 0), (2, 1), (3, 0)])
+def test_levels_equal_planes_full_size(cmf, algo, storage):
+    """Full-size 16-label recipe at 2048^2: computing the costs in the
+    kernels gives the iterates of reading the same float32 cost planes."""
+    inst = synth.config5(2048, 2048)
+    I, lev, C = _levels_inputs(inst)
+    p = cmf.default_params(algo, 16, storage=storage)
+    a = cmf.alloc_potts_levels(I, lev, inst.alpha, p)
+    cmf.cmf_init_potts(a)
+    cmf.cmf_iterate_potts(a, 6)
+    b = cmf.Potts(C, inst.alpha, cmf.default_params(algo, 16, storage=storage))
+    cmf.cmf_init_potts(b)
+    cmf.cmf_iterate_potts(b, 6)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        err = (getattr(a, k).float() - getattr(b, k).float()).abs().max().item()
+        assert err <= 1e-6, (k, err)
+
+
+def test_levels_solve_certified(cmf):
+    inst = synth.config3(96, 80)
+    I, lev, C = _levels_inputs(inst)
+    p = cmf.default_params(2, 4, tol_gap=1e-4, max_iter=30000, check_every=10)
+    s = cmf.alloc_potts_levels(I, lev, inst.alpha, p)
+    status, iters, hist = cmf.cmf_solve_potts(s)
+    assert status == cmf.OK and hist[-1, 3] <= 1e-4
+    E, D, gap, res = O.potts_eval(C, inst.alpha, s.state(), O.default_params(2, 4))
+    assert gap <= 1.01e-4
