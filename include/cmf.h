@@ -137,6 +137,21 @@ typedef struct {
                           d_C holds one image plane I [H][pitch] followed by the
                           L levels c_i (floats), and C_i(x) = (I(x) - c_i)^2.
                           Binary calls and batches need 0.                    */
+    const double *rho_schedule; /* relaxation sequence {rho_k} of rpADMMII and
+                          rPDRQ (Thm 1 and Thm 2 assume a non-decreasing
+                          sequence in (0, 2); Sec. 4 takes rho_k = 1.9 for all
+                          k).  Iteration k, counted from 0 at the first
+                          iteration of a cmf_iterate_* or cmf_solve_* call
+                          (warm starts included), uses rho_schedule[k] for
+                          k < rho_schedule_len and rho from then on.  Host
+                          array, read during the call only; NULL with length
+                          0 (the default) means rho_k = rho.  CMF_EINVAL unless
+                          every entry is in (0, 2), the entries do not
+                          decrease, the last is <= rho and algo is rpADMMII or
+                          rPDRQ; batches need length 0.  A solve runs the
+                          scheduled iterations from the host, one launch per
+                          iteration, and the rest as usual.              */
+    int rho_schedule_len;
 } cmf_params;
 
 /* Fill *p with the paper's defaults for `algo` and L labels (L = 2 for the

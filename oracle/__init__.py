@@ -151,9 +151,31 @@ def simplex(v):
 
 
 
-def binary_run(Cs, Ct, alpha, params: Params, n_iter: int, state=None) -> dict:
+def _run_scheduled(run, args, params: Params, n_iter: int, state, rho_schedule, k0: int):
+    """Relaxed iterations with a sequence {rho_k} (the rho_k of Eq.
+    update:two:sun:lag, Eq. rpADMMII and the relaxed Douglas-Rachford step,
+    which Thm 1 and Thm 2 take non-decreasing in (0, 2)): iteration k0 + i uses
+    rho_schedule[k0 + i] while the sequence covers it, params.rho after."""
+    sched = np.asarray(rho_schedule, dtype=np.float64).ravel()
+    i = 0
+    while i < n_iter and k0 + i < sched.size:
+        q = Params.from_buffer_copy(params)
+        q.rho = float(sched[k0 + i])
+        state = run(*args, q, 1, state)
+        i += 1
+    if i < n_iter or state is None:
+        state = run(*args, params, n_iter - i, state)
+    return state
+
+
+def binary_run(Cs, Ct, alpha, params: Params, n_iter: int, state=None, rho_schedule=None,
+               k0: int = 0) -> dict:
     """Run n_iter iterations.  state=None: cold start.  Returns the state dict
-    (u, qx, qy, ps, pt); for rPDRQ the flow entries hold (qbar, pbar)."""
+    (u, qx, qy, ps, pt); for rPDRQ the flow entries hold (qbar, pbar).
+    rho_schedule: see _run_scheduled (k0 = index of the first iteration)."""
+    if rho_schedule is not None:
+        return _run_scheduled(binary_run, (Cs, Ct, alpha), params, n_iter, state,
+                              rho_schedule, k0)
     Cs, Ct = _f64(Cs), _f64(Ct)
     H, W = Cs.shape
     al = _alpha_field(alpha, H, W)
@@ -182,8 +204,12 @@ def binary_eval(Cs, Ct, alpha, state, params: Params):
 
 # --- Potts model --------------------------------------------------------------
 
-def potts_run(C, alpha, params: Params, n_iter: int, state=None) -> dict:
-    """State dict: u, qx, qy, p of shape (L, H, W) and ps of shape (H, W)."""
+def potts_run(C, alpha, params: Params, n_iter: int, state=None, rho_schedule=None,
+              k0: int = 0) -> dict:
+    """State dict: u, qx, qy, p of shape (L, H, W) and ps of shape (H, W).
+    rho_schedule: see _run_scheduled (k0 = index of the first iteration)."""
+    if rho_schedule is not None:
+        return _run_scheduled(potts_run, (C, alpha), params, n_iter, state, rho_schedule, k0)
     C = _f64(C)
     L, H, W = C.shape
     al = _alpha_field(alpha, H, W)
@@ -224,7 +250,7 @@ def potts_labels(u) -> np.ndarray:
 
 
 def solve(inst, algo: int, tol: float = 1e-4, max_iter: int = 20000, check_every: int = 10,
-          params: Params | None = None):
+          params: Params | None = None, rho_schedule=None):
     """Iterate until the relative primal-dual gap is <= tol (checked every
     check_every iterations).  Returns (state, iterations, history)."""
     if params is None:
@@ -235,10 +261,11 @@ def solve(inst, algo: int, tol: float = 1e-4, max_iter: int = 20000, check_every
     while it < max_iter:
         k = min(check_every, max_iter - it)
         if inst.kind == "binary":
-            state = binary_run(inst.costs[0], inst.costs[1], inst.alpha, params, k, state)
+            state = binary_run(inst.costs[0], inst.costs[1], inst.alpha, params, k, state,
+                               rho_schedule, it)
             ev = binary_eval(inst.costs[0], inst.costs[1], inst.alpha, state, params)
         else:
-            state = potts_run(inst.costs, inst.alpha, params, k, state)
+            state = potts_run(inst.costs, inst.alpha, params, k, state, rho_schedule, it)
             ev = potts_eval(inst.costs, inst.alpha, state, params)
         it += k
         hist.append((it,) + ev)

@@ -42,7 +42,21 @@ class Params(ctypes.Structure):
         ("a2", ctypes.c_double), ("rho", ctypes.c_double), ("r", ctypes.c_double),
         ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("tol_gap", ctypes.c_double),
         ("costs", ctypes.c_int),
+        ("rho_schedule", ctypes.POINTER(ctypes.c_double)), ("rho_schedule_len", ctypes.c_int),
     ]
+
+    def set_rho_schedule(self, rhos) -> "Params":
+        """Relaxation sequence rho_0, rho_1, ... for the first len(rhos)
+        iterations of each iterate / solve call (rpADMMII, rPDRQ); rho after.
+        The array is kept alive by this object."""
+        arr = np.ascontiguousarray(np.asarray(rhos, dtype=np.float64).ravel())
+        self._rho_keep = arr
+        if arr.size == 0:
+            self.rho_schedule = None
+        else:
+            self.rho_schedule = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self.rho_schedule_len = int(arr.size)
+        return self
 
 
 class Instance(ctypes.Structure):
@@ -143,6 +157,9 @@ def default_params(algo: int, L: int = 2, **kw) -> Params:
     p = Params()
     _check(lib().cmf_default_params(algo, L, ctypes.byref(p)), "cmf_default_params")
     for k, v in kw.items():
+        if k == "rho_schedule":
+            p.set_rho_schedule(v)
+            continue
         if not hasattr(p, k):
             raise AttributeError(k)
         setattr(p, k, v)
@@ -410,6 +427,7 @@ def cmf_autotune_binary(b: Binary, stream=None):
     _check(lib().cmf_autotune_binary(*b._common(), *b._state_ptrs(), _ptr(b.ws), b.ws.numel(),
                                      ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
            "cmf_autotune_binary")
+    best._rho_keep = getattr(b.params, "_rho_keep", None)  # the copied schedule pointer
     return best, ms.value
 
 
@@ -419,6 +437,7 @@ def cmf_autotune_potts(s: Potts, stream=None):
     _check(lib().cmf_autotune_potts(*s._common(), *s._state_ptrs(), _ptr(s.ws), s.ws.numel(),
                                     ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
            "cmf_autotune_potts")
+    best._rho_keep = getattr(s.params, "_rho_keep", None)  # the copied schedule pointer
     return best, ms.value
 
 
@@ -442,6 +461,7 @@ def tuned_params(problem, cache_path: str | None = None) -> Params:
         cache = {}
     q = Params()
     ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(Params))
+    q._rho_keep = getattr(p, "_rho_keep", None)  # the copied schedule pointer
     if key in cache:
         q.variant, q.sweeps = cache[key]["variant"], cache[key]["sweeps"]
         return q

@@ -81,6 +81,20 @@ cmf_status check_params(const cmf_params* p, int L) {
         p->variant != 16 && p->variant != 32)
         return CMF_EINVAL;
     if (p->costs != 0 && p->costs != 1) return CMF_EINVAL;
+    // relaxation schedule {rho_k}: non-decreasing in (0, 2) (Thm 1, Thm 2),
+    // continued by rho, for the two relaxed algorithms only
+    if (p->rho_schedule_len < 0) return CMF_EINVAL;
+    if (p->rho_schedule_len > 0) {
+        if (!p->rho_schedule) return CMF_EINVAL;
+        if (p->algo != CMF_RPADMM_EB && p->algo != CMF_RPDRQ) return CMF_EINVAL;
+        double prev = 0.0;
+        for (int k = 0; k < p->rho_schedule_len; ++k) {
+            const double r = p->rho_schedule[k];
+            if (!(r > 0) || !(r < 2) || !(r >= prev)) return CMF_EINVAL;
+            prev = r;
+        }
+        if (!(prev <= p->rho)) return CMF_EINVAL;
+    }
     (void)L;
     return CMF_OK;
 }
@@ -105,6 +119,15 @@ StepConfig make_step(const cmf_params& p, int L, bool potts) {
     s.ac = make_admm_coef(p, L);
     s.dc = make_dr_coef(p, L, potts);
     return s;
+}
+
+// Coefficients of iteration k (counted from the start of the call): the
+// scheduled rho_k where the schedule covers k, else the call's own.
+StepConfig step_at(const StepConfig& base, const cmf_params& p, int L, bool potts, int k) {
+    if (k >= p.rho_schedule_len) return base;
+    cmf_params q = p;
+    q.rho = p.rho_schedule[k];
+    return make_step(q, L, potts);
 }
 
 // ---- binary ---------------------------------------------------------------
@@ -147,6 +170,7 @@ struct BinaryCall {
     WsLayout w;
     char* wsbase;
     StepConfig cfg;
+    cmf_params prm;         // the call's parameters (rho schedule)
     int storage;
     bool tma;               // fused ADMM through the persistent TMA kernel
     bool strip;             // fused ADMM by warp strips
@@ -177,6 +201,7 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     call.wsbase = (char*)ws;
     call.ws = ws_binary_state(call.wsbase, call.w, call.P.g, p->storage);
     call.cfg = make_step(*p, 2, false);
+    call.prm = *p;
     call.storage = p->storage;
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
@@ -212,32 +237,34 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
 }
 
 // Run n iterations starting from `cur` (0 = user buffers, 1 = workspace);
-// returns the index of the buffer set holding the result.
-cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st) {
+// returns the index of the buffer set holding the result.  k0 is the index of
+// the first of them within the call (for the rho schedule).
+cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, int k0 = 0) {
     float* tmp = (float*)(c.wsbase + c.w.tmp);
     for (int i = 0; i < n; ++i) {
-        if (c.cfg.plain) {
-            cudaError_t e = binary_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
+        const StepConfig cfg = step_at(c.cfg, c.prm, 2, false, k0 + i);
+        if (cfg.plain) {
+            cudaError_t e = binary_step(c.storage, c.P, c.user, c.user, cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur = 0;
         } else if (c.strip) {
             const BinStateV& a = cur == 0 ? c.user : c.ws;
             const BinStateV& b = cur == 0 ? c.ws : c.user;
             cudaError_t e =
-                c.cfg.dr ? binary_dr_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.dc, st)
-                         : binary_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st);
+                cfg.dr ? binary_dr_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.dc, st)
+                       : binary_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.ac, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         } else if (c.tma) {
             const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_admm_tma_step(c.storage, c.P, b, c.cfg.aniso, c.cfg.ac,
+            cudaError_t e = binary_admm_tma_step(c.storage, c.P, b, cfg.aniso, cfg.ac,
                                                  c.maps[cur], c.err, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         } else {
             const BinStateV& a = cur == 0 ? c.user : c.ws;
             const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_step(c.storage, c.P, a, b, c.cfg, tmp, st);
+            cudaError_t e = binary_step(c.storage, c.P, a, b, cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -318,6 +345,7 @@ struct PottsCall {
     WsLayout w;
     char* wsbase;
     StepConfig cfg;
+    cmf_params prm;              // the call's parameters (rho schedule)
     int storage;
     bool tma;                    // fused ADMM through TMA-staged tiles
     bool strip;                  // fused ADMM by warp strips
@@ -348,6 +376,7 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     call.wsbase = (char*)ws;
     call.ws = ws_potts_state(call.wsbase, call.w, call.P.g, L, p->storage);
     call.cfg = make_step(*p, L, true);
+    call.prm = *p;
     call.storage = p->storage;
     call.err = &((SolveCtl*)(call.wsbase + call.w.ctl))->err;
     call.tma = false;
@@ -379,40 +408,42 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     return CMF_OK;
 }
 
-cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st) {
+cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st, int k0 = 0) {
     float* tmp = (float*)(c.wsbase + c.w.tmp);
     for (int i = 0; i < n; ++i) {
-        if (c.cfg.plain) {
-            cudaError_t e = potts_step(c.storage, c.P, c.user, c.user, c.cfg, tmp, st);
+        const StepConfig cfg = step_at(c.cfg, c.prm, c.P.L, true, k0 + i);
+        if (cfg.plain) {
+            cudaError_t e = potts_step(c.storage, c.P, c.user, c.user, cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur = 0;
-        } else if (c.strip && c.cfg.dr) {
+        } else if (c.strip && cfg.dr) {
             const PottsStateV& a = cur == 0 ? c.user : c.ws;
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = potts_dr_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.dc, st);
+            cudaError_t e = potts_dr_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.dc, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         } else if (c.strip) {
             const PottsStateV& a = cur == 0 ? c.user : c.ws;
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
-            // the first iteration reads u itself, later ones the w form
-            cudaError_t e = potts_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac,
-                                             i == 0 ? 0.0f : c.cfg.ac.cu, st);
+            // the first iteration reads u itself, later ones the w form (cu
+            // does not depend on rho, so a schedule keeps it fixed)
+            cudaError_t e = potts_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.ac,
+                                             i == 0 ? 0.0f : cfg.ac.cu, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
             if (i == n - 1 &&
-                (e = potts_strip_finalize(c.storage, c.P, b, c.cfg.ac.cu, st)) != cudaSuccess)
+                (e = potts_strip_finalize(c.storage, c.P, b, cfg.ac.cu, st)) != cudaSuccess)
                 return e;
         } else if (c.tma) {
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = potts_admm_tma_step(c.storage, c.P, b, c.cfg.aniso, c.cfg.ac,
+            cudaError_t e = potts_admm_tma_step(c.storage, c.P, b, cfg.aniso, cfg.ac,
                                                 c.maps[cur], c.err, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         } else {
             const PottsStateV& a = cur == 0 ? c.user : c.ws;
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = potts_step(c.storage, c.P, a, b, c.cfg, tmp, st);
+            cudaError_t e = potts_step(c.storage, c.P, a, b, cfg, tmp, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         }
@@ -429,8 +460,8 @@ cmf_status potts_eval_state(const PottsCall& c, const PottsStateV& s, double* h_
 
 // ---- device-driven solve loop (CUDA graph with a conditional WHILE node) ----
 
-__global__ void k_solve_reset(SolveCtl* ctl) {
-    ctl->it = 0;
+__global__ void k_solve_reset(SolveCtl* ctl, int it0) {
+    ctl->it = it0;
     ctl->checks = 0;
     ctl->stop = 0;
 }
@@ -477,17 +508,18 @@ bool graph_eligible(const cmf_params& p) {
 
 // `chunk(stream)` launches check_every iterations that start and end in the
 // caller's buffers; `certify(stream)` launches the certificate kernel into
-// the partials.
+// the partials.  The loop continues a solve that has already run it0
+// iterations and recorded nh0 history rows on the host.
 template <typename Chunk, typename Certify>
 cmf_status solve_graph(const cmf_params* p, char* wsbase, const WsLayout& w, int nblocks,
                        Chunk chunk, Certify certify, double* h_hist, int hist_cap, int* h_iters,
-                       cudaStream_t st) {
+                       cudaStream_t st, int it0 = 0, int nh0 = 0) {
     SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
     double* dhist = (double*)(wsbase + w.hist);
     const int rows = (int)hist_rows_for(*p);
     double* partials = (double*)(wsbase + w.partials);
     double* scal = (double*)(wsbase + w.scalars);
-    k_solve_reset<<<1, 1, 0, st>>>(ctl);
+    k_solve_reset<<<1, 1, 0, st>>>(ctl, it0);
     CMF_CUDA_TRY(cudaGetLastError());
 
     cudaStream_t cs = nullptr;
@@ -530,9 +562,10 @@ cmf_status solve_graph(const cmf_params* p, char* wsbase, const WsLayout& w, int
             break;
         if (cudaStreamSynchronize(st) != cudaSuccess) break;
         const int n = hc.checks < rows ? hc.checks : rows;
-        const int ncopy = n < hist_cap ? n : hist_cap;
+        const int room = hist_cap > nh0 ? hist_cap - nh0 : 0;
+        const int ncopy = n < room ? n : room;
         if (h_hist && ncopy > 0) {
-            if (cudaMemcpy(h_hist, dhist, sizeof(double) * 5 * (size_t)ncopy,
+            if (cudaMemcpy(h_hist + 5 * (size_t)nh0, dhist, sizeof(double) * 5 * (size_t)ncopy,
                            cudaMemcpyDeviceToHost) != cudaSuccess)
                 break;
         }
@@ -545,37 +578,76 @@ cmf_status solve_graph(const cmf_params* p, char* wsbase, const WsLayout& w, int
     return status;
 }
 
-// Shared solve loop: `run(n, cur)` advances, `eval(cur, out)` certifies.
-template <typename Run, typename Eval, typename Copy>
-cmf_status solve_loop(const cmf_params* p, Run run, Eval eval, Copy copy_back, double* h_hist,
-                      int hist_cap, int* h_iters, cudaStream_t st) {
-    int cur = 0, it = 0, nh = 0;
+// Progress of a host-driven solve loop.
+struct LoopState {
+    int it = 0;    // iterations done
+    int nh = 0;    // certificate checks done
+    int cur = 0;   // buffer set holding the state (0 = caller's)
     bool converged = false;
+};
+
+// Host-driven chunks of check_every iterations, each followed by the
+// certificates, until convergence, max_iter, or it >= it_stop.
+// `run(n, cur, k0)` advances n iterations whose first is iteration k0 of the
+// solve, `eval(cur, out)` certifies.
+template <typename Run, typename Eval>
+cmf_status loop_chunks(const cmf_params* p, int it_stop, Run run, Eval eval, double* h_hist,
+                       int hist_cap, LoopState& ls) {
     double out[4];
-    while (it < p->max_iter) {
-        const int k = p->check_every < p->max_iter - it ? p->check_every : p->max_iter - it;
-        CMF_CUDA_TRY(run(k, cur));
-        it += k;
-        cmf_status s = eval(cur, out);
+    while (ls.it < p->max_iter && ls.it < it_stop) {
+        const int k =
+            p->check_every < p->max_iter - ls.it ? p->check_every : p->max_iter - ls.it;
+        CMF_CUDA_TRY(run(k, ls.cur, ls.it));
+        ls.it += k;
+        cmf_status s = eval(ls.cur, out);
         if (s != CMF_OK) return s;
-        if (h_hist && nh < hist_cap) {
-            double* row = h_hist + 5 * (size_t)nh;
-            row[0] = it;
+        if (h_hist && ls.nh < hist_cap) {
+            double* row = h_hist + 5 * (size_t)ls.nh;
+            row[0] = ls.it;
             row[1] = out[0];
             row[2] = out[1];
             row[3] = out[2];
             row[4] = out[3];
         }
-        ++nh;
+        ++ls.nh;
         if (out[2] <= p->tol_gap) {
-            converged = true;
+            ls.converged = true;
             break;
         }
     }
-    if (cur != 0) CMF_CUDA_TRY(copy_back());
+    return CMF_OK;
+}
+
+template <typename Copy>
+cmf_status finish_loop(const LoopState& ls, Copy copy_back, int* h_iters, cudaStream_t st) {
+    if (ls.cur != 0) CMF_CUDA_TRY(copy_back());
     CMF_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h_iters) *h_iters = it;
-    return converged ? CMF_OK : CMF_NOT_CONVERGED;
+    if (h_iters) *h_iters = ls.it;
+    return ls.converged ? CMF_OK : CMF_NOT_CONVERGED;
+}
+
+// The solve driver: the iterations a rho schedule covers run host-driven
+// (their coefficients change from launch to launch, a graph's are fixed), the
+// rest in the device-driven graph where it applies, else host-driven.
+template <typename Run, typename Eval, typename Copy, typename Chunk, typename Certify>
+cmf_status solve_driver(const cmf_params* p, char* wsbase, const WsLayout& w, int nblocks,
+                        Run run, Eval eval, Copy copy_back, Chunk chunk, Certify certify,
+                        double* h_hist, int hist_cap, int* h_iters, cudaStream_t st) {
+    LoopState ls;
+    if (!graph_eligible(*p)) {
+        cmf_status s = loop_chunks(p, p->max_iter, run, eval, h_hist, hist_cap, ls);
+        if (s != CMF_OK) return s;
+        return finish_loop(ls, copy_back, h_iters, st);
+    }
+    if (p->rho_schedule_len > 0) {
+        cmf_status s = loop_chunks(p, p->rho_schedule_len, run, eval, h_hist, hist_cap, ls);
+        if (s != CMF_OK) return s;
+        if (ls.cur != 0) CMF_CUDA_TRY(copy_back());  // whole even chunks end at 0
+        ls.cur = 0;
+        if (ls.converged || ls.it >= p->max_iter) return finish_loop(ls, copy_back, h_iters, st);
+    }
+    return solve_graph(p, wsbase, w, nblocks, chunk, certify, h_hist, hist_cap, h_iters, st,
+                       ls.it, ls.nh);
 }
 
 }  // namespace
@@ -692,26 +764,22 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
     CMF_CUDA_TRY(cudaMemsetAsync(&((SolveCtl*)(c.wsbase + c.w.ctl))->err, 0, sizeof(int), st));
     if (!p->warm_start)
         CMF_CUDA_TRY(binary_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
-    if (graph_eligible(*p)) {
-        return solve_graph(
-            p, c.wsbase, c.w, eval_blocks(H, W),
-            [&](cudaStream_t s) {
-                int cur = 0;
-                return binary_run(c, p->check_every, cur, s);
-            },
-            [&](cudaStream_t s) {
-                return binary_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
-                                   (double*)(c.wsbase + c.w.partials), s);
-            },
-            h_hist, hist_cap, h_iters, st);
-    }
-    return solve_loop(
-        p, [&](int n, int& cur) { return binary_run(c, n, cur, st); },
+    return solve_driver(
+        p, c.wsbase, c.w, eval_blocks(H, W),
+        [&](int n, int& cur, int k0) { return binary_run(c, n, cur, st, k0); },
         [&](int cur, double* out) {
             return binary_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
         },
-        [&]() { return copy_binary(c.user, c.ws, c.P.g, c.storage, st); }, h_hist, hist_cap,
-        h_iters, st);
+        [&]() { return copy_binary(c.user, c.ws, c.P.g, c.storage, st); },
+        [&](cudaStream_t s) {  // graph chunks run after the schedule
+            int cur = 0;
+            return binary_run(c, p->check_every, cur, s, p->rho_schedule_len);
+        },
+        [&](cudaStream_t s) {
+            return binary_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                               (double*)(c.wsbase + c.w.partials), s);
+        },
+        h_hist, hist_cap, h_iters, st);
 }
 
 cmf_status cmf_init_potts(const float* d_C, int L, int H, int W, int pitch, const cmf_params* p,
@@ -773,26 +841,22 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
     CMF_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), st));
     if (!p->warm_start)
         CMF_CUDA_TRY(potts_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
-    if (graph_eligible(*p)) {
-        return solve_graph(
-            p, c.wsbase, c.w, eval_blocks(H, W),
-            [&](cudaStream_t s) {
-                int cur = 0;
-                return potts_run(c, p->check_every, cur, s);
-            },
-            [&](cudaStream_t s) {
-                return potts_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
-                                  (double*)(c.wsbase + c.w.partials), s);
-            },
-            h_hist, hist_cap, h_iters, st);
-    }
-    return solve_loop(
-        p, [&](int n, int& cur) { return potts_run(c, n, cur, st); },
+    return solve_driver(
+        p, c.wsbase, c.w, eval_blocks(H, W),
+        [&](int n, int& cur, int k0) { return potts_run(c, n, cur, st, k0); },
         [&](int cur, double* out) {
             return potts_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
         },
-        [&]() { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); }, h_hist, hist_cap,
-        h_iters, st);
+        [&]() { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); },
+        [&](cudaStream_t s) {  // graph chunks run after the schedule
+            int cur = 0;
+            return potts_run(c, p->check_every, cur, s, p->rho_schedule_len);
+        },
+        [&](cudaStream_t s) {
+            return potts_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                              (double*)(c.wsbase + c.w.partials), s);
+        },
+        h_hist, hist_cap, h_iters, st);
 }
 
 }  // extern "C"

@@ -110,6 +110,39 @@ def test_bad_arguments_rejected_without_launch(cmf):
     del keep, out
 
 
+def test_rho_schedule_rejected_without_launch(cmf):
+    """A relaxation schedule must be non-decreasing in (0, 2), end at or below
+    rho, and belong to rpADMMII or rPDRQ; batches take none."""
+    lib = cmf.lib()
+    ptr, keep = _fake()
+
+    def call(algo=cmf.RPADMM_EB, sched=(1.0, 1.5), n=None, null=False, rho=1.9):
+        q = cmf.default_params(algo, 2)
+        q.rho = rho
+        q.set_rho_schedule(sched)
+        if n is not None:
+            q.rho_schedule_len = n
+        if null:
+            q.rho_schedule = None
+        return lib.cmf_iterate_binary(ptr, ptr, None, 0.5, 8, 8, 8, ctypes.byref(q), 1, ptr, ptr,
+                                      ptr, ptr, ptr, ptr, 1 << 20, None)
+
+    for bad in [dict(sched=(1.5, 1.2)), dict(sched=(1.0, 2.0)), dict(sched=(0.0, 1.0)),
+                dict(sched=(1.0, 1.95)), dict(sched=(1.0, float("nan"))),
+                dict(algo=cmf.PADMM), dict(algo=cmf.RPADMM_FG), dict(algo=cmf.TY),
+                dict(algo=cmf.CP), dict(null=True), dict(n=-1)]:
+        assert call(**bad) == cmf.EINVAL, bad
+    q = cmf.default_params(cmf.RPADMM_EB, 4)
+    q.set_rho_schedule([1.2, 1.1])
+    assert lib.cmf_iterate_potts(ptr, 4, None, 0.5, 8, 8, 8, ctypes.byref(q), 1, ptr, ptr, ptr,
+                                 ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL
+    inst = cmf.Instance()
+    q = cmf.default_params(cmf.RPADMM_EB, 2)
+    q.set_rho_schedule([1.0])
+    assert lib.cmf_batch_workspace_bytes(ctypes.byref(inst), 1, ctypes.byref(q)) == 0
+    del keep
+
+
 def test_status_strings(cmf):
     lib = cmf.lib()
     for s in range(6):
