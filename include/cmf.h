@@ -114,13 +114,19 @@ typedef struct {
                           check_every is even), else a host-driven loop        */
     int variant;       /* kernel variant of the fused ADMM algorithms:
                           0 = automatic: warp strips where the layout allows
-                          them, else TMA-staged tiles (Potts, and binary grids
+                          them (binary ADMM: two iterations per launch, as 4),
+                          else TMA-staged tiles (Potts, and binary grids
                           of at most 2^21 pixels) where rows and planes are
                           16-byte aligned, else shared-memory tiles;
                           1 = shared-memory tiles;
                           2 = warp strips (even W and pitch, planes aligned to
                           two elements; for Potts the multipliers are kept as
                           u - cu p_s between the iterations of one call);
+                          4 = binary ADMM: warp strips making two iterations
+                          per launch (the intermediate state stays on chip;
+                          an even number of such launches per call, single
+                          ones for the rest and for scheduled rho_k; same
+                          results as 2); Potts and rPDRQ: as 2;
                           8 / 16 / 32 = TMA tiles of that many rows         */
     double c;          /* ADMM step size                                       */
     double a;          /* q preconditioner N = a c I (a >= 8, Thm 1)           */
@@ -273,7 +279,8 @@ cmf_status cmf_solve_potts(const float *d_C, int L, const float *d_alpha, float 
 /* ------------------------------------------------------------------------ */
 /* Autotuning (no counterpart in the paper: a launch-configuration search).  */
 /* Solves the problem from a cold start once per candidate configuration --  */
-/* the kernel variant (1, 2, 8, 16, 32) of the fused ADMM algorithms, or the */
+/* the kernel variant (1, 2, 4 (binary), 8, 16, 32) of the fused ADMM       */
+/* algorithms, or the                                                        */
 /* sRBGS sweep count (1, 2, 3) of fused rPDRQ -- with everything else taken  */
 /* from *p, and writes the candidate with the shortest time to p->tol_gap    */
 /* (CUDA events on `stream`, best of two runs after a warm-up) to *best and  */

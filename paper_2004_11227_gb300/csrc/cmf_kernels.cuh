@@ -155,6 +155,12 @@ bool binary_strip_eligible(const Grid& G, int storage, const float* Cs, const fl
 cudaError_t binary_strip_step(int storage, const BinProblem& P, const BinStateV& a,
                               const BinStateV& b, bool aniso, const AdmmCoef& K,
                               cudaStream_t st);
+// Two ADMM iterations from a into b in one launch (same result as two
+// binary_strip_step launches through an intermediate state;
+// cmf_binary_strip2.cu).
+cudaError_t binary_strip2_step(int storage, const BinProblem& P, const BinStateV& a,
+                               const BinStateV& b, bool aniso, const AdmmCoef& K,
+                               cudaStream_t st);
 // rPDRQ iteration a -> b with the pipelined red-black sweeps.
 cudaError_t binary_dr_strip_step(int storage, const BinProblem& P, const BinStateV& a,
                                  const BinStateV& b, bool aniso, const DrCoef& D,

@@ -25,6 +25,8 @@ struct Pair<float> {
     static __device__ __forceinline__ void st(float* p, float a, float b) {
         *reinterpret_cast<float2*>(p) = make_float2(a, b);
     }
+    // the pair as a store followed by a load would give it
+    static __device__ __forceinline__ T pk(float a, float b) { return make_float2(a, b); }
 };
 template <>
 struct Pair<__half> {
@@ -37,6 +39,7 @@ struct Pair<__half> {
     static __device__ __forceinline__ void st(__half* p, float a, float b) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
     }
+    static __device__ __forceinline__ T pk(float a, float b) { return __floats2half2_rn(a, b); }
 };
 template <>
 struct Pair<__nv_bfloat16> {
@@ -48,6 +51,9 @@ struct Pair<__nv_bfloat16> {
     static __device__ __forceinline__ float2 f2(T v) { return __bfloat1622float2(v); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+    }
+    static __device__ __forceinline__ T pk(float a, float b) {
+        return __floats2bfloat162_rn(a, b);
     }
 };
 
