@@ -260,7 +260,7 @@ def test_autotune_picks_a_converging_configuration(cmf, tmp_path):
         b = cmf.alloc_binary(inst, p)
         best, ms = cmf.cmf_autotune_binary(b)
         assert ms > 0 and best.algo == algo
-        assert best.variant in (1, 8, 16, 32) if algo != 3 else best.sweeps in (1, 2, 3)
+        assert best.variant in (1, 2, 4, 8, 16, 32) if algo != 3 else best.sweeps in (1, 2, 3)
         q = cmf.tuned_params(b, cache_path=str(tmp_path / "tune.json"))
         assert (tmp_path / "tune.json").exists()
         b2 = cmf.alloc_binary(inst, q)
