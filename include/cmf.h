@@ -31,8 +31,8 @@
  *    written.
  *  - Pointers named d_* are DEVICE pointers owned by the caller; the library
  *    never frees them and never allocates device memory inside a call except
- *    where stated (the CUDA graph objects of cmf_solve_*).  Pointers named h_*
- *    are HOST pointers.
+ *    where stated (the CUDA graph objects of cmf_solve_*, kept for reuse, see
+ *    cmf_release_graphs).  Pointers named h_* are HOST pointers.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Calls are stream-ordered: device outputs are valid once the
  *    stream has been synchronised.  Entry points that return host values
@@ -242,6 +242,23 @@ cmf_status cmf_solve_binary(const float *d_Cs, const float *d_Ct, const float *d
                             float *d_u, void *d_qx, void *d_qy, void *d_ps, void *d_pt,
                             double *h_hist, int hist_cap, int *h_iters, void *d_ws,
                             size_t ws_bytes, void *stream);
+
+/* The device-driven loop of cmf_solve_* (use_graph = 1) is a CUDA graph
+ * whose kernels have the call's pointers, sizes and coefficients baked in.
+ * It is built and instantiated on the first call with a given signature --
+ * the current device, the model, L, H, W, pitch, alpha0, every device
+ * pointer (costs, alpha, state, workspace) and *p apart from warm_start and
+ * the rho schedule -- and replayed by later calls with the same signature
+ * (a solve called in a loop pays the graph construction once).  The
+ * executable graphs of the 8 most recently used signatures are kept, in
+ * device memory the library allocates.  A replay only needs buffers of the
+ * signature's sizes at the signature's addresses, whatever they hold, so
+ * freeing and reallocating buffers never makes a kept graph wrong; a graph
+ * whose buffers are gone is simply never matched again.
+ * cmf_release_graphs() destroys them all, to return their memory.
+ * Thread-safe; graphs still running are freed when they complete.  No
+ * counterpart in the paper. */
+cmf_status cmf_release_graphs(void);
 
 /* ------------------------------------------------------------------------ */
 /* Potts model, L labels (2 <= L <= 64).  d_C: L float32 planes C_1..C_L.   */

@@ -103,6 +103,7 @@ _SIGS = {
     "cmf_autotune_potts": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_float] +
                           [ctypes.c_int] * 3 + [ctypes.c_void_p] * 7 + [ctypes.c_size_t] +
                           [ctypes.c_void_p] * 3,
+    "cmf_release_graphs": [],
     "cmf_batch_workspace_bytes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "cmf_solve_batch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_size_t, ctypes.c_void_p],
@@ -164,6 +165,11 @@ def default_params(algo: int, L: int = 2, **kw) -> Params:
             raise AttributeError(k)
         setattr(p, k, v)
     return p
+
+
+def cmf_release_graphs() -> None:
+    """Destroy the solve graphs kept for reuse by cmf_solve_* (see cmf.h)."""
+    _check(lib().cmf_release_graphs(), "cmf_release_graphs")
 
 
 def cmf_workspace_bytes(H: int, W: int, L: int, pitch: int, p: Params) -> int:

@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <initializer_list>
+#include <mutex>
 #include <vector>
 
 #include "cmf_kernels.cuh"
@@ -535,14 +537,93 @@ bool graph_eligible(const cmf_params& p) {
     return true;
 }
 
+// Everything the kernels of a solve graph are built from: the device, the
+// model, sizes, every device pointer, alpha0 and the parameters (their
+// coefficients, the loop constants).  Calls with equal signatures can replay
+// the same instantiated graph.  Zero-filled before use, compared bytewise.
+struct SolveSig {
+    int dev, model, L, H, W, pitch;
+    float alpha0;
+    const void* ptr[10];
+    cmf_params p;  // rho schedule and warm start cleared: the graph does not depend on them
+};
+
+SolveSig make_sig(int model, int L, int H, int W, int pitch, float alpha0,
+                  std::initializer_list<const void*> ptrs, const cmf_params& p) {
+    SolveSig k;
+    memset(&k, 0, sizeof(k));
+    cudaGetDevice(&k.dev);
+    k.model = model;
+    k.L = L;
+    k.H = H;
+    k.W = W;
+    k.pitch = pitch;
+    k.alpha0 = alpha0;
+    int i = 0;
+    for (const void* q : ptrs)
+        if (i < 10) k.ptr[i++] = q;
+    memcpy(&k.p, &p, sizeof(p));
+    k.p.rho_schedule = nullptr;
+    k.p.rho_schedule_len = 0;
+    k.p.warm_start = 0;
+    return k;
+}
+
+// Instantiated solve graphs, least recently used out.  Graph objects stay
+// alive between calls (until evicted or cmf_release_graphs); an executable
+// graph that is destroyed while in flight is freed when it completes.
+constexpr size_t kGraphCache = 8;
+struct GraphEntry {
+    SolveSig sig;
+    cudaGraph_t g;
+    cudaGraphExec_t ge;
+    unsigned long long used;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry>* g_graphs = new std::vector<GraphEntry>();  // never freed: no
+                                                                     // CUDA calls at exit
+unsigned long long g_graph_tick = 0;
+
+cudaGraphExec_t graph_lookup(const SolveSig& k) {
+    for (GraphEntry& e : *g_graphs)
+        if (memcmp(&e.sig, &k, sizeof(k)) == 0) {
+            e.used = ++g_graph_tick;
+            return e.ge;
+        }
+    return nullptr;
+}
+
+void graph_insert(const SolveSig& k, cudaGraph_t g, cudaGraphExec_t ge) {
+    if (g_graphs->size() >= kGraphCache) {
+        size_t lru = 0;
+        for (size_t i = 1; i < g_graphs->size(); ++i)
+            if ((*g_graphs)[i].used < (*g_graphs)[lru].used) lru = i;
+        cudaGraphExecDestroy((*g_graphs)[lru].ge);
+        cudaGraphDestroy((*g_graphs)[lru].g);
+        g_graphs->erase(g_graphs->begin() + lru);
+    }
+    g_graphs->push_back(GraphEntry{k, g, ge, ++g_graph_tick});
+}
+
+void graph_drop(cudaGraphExec_t ge) {
+    for (size_t i = 0; i < g_graphs->size(); ++i)
+        if ((*g_graphs)[i].ge == ge) {
+            cudaGraphExecDestroy(ge);
+            cudaGraphDestroy((*g_graphs)[i].g);
+            g_graphs->erase(g_graphs->begin() + i);
+            return;
+        }
+}
+
 // `chunk(stream)` launches check_every iterations that start and end in the
 // caller's buffers; `certify(stream)` launches the certificate kernel into
 // the partials.  The loop continues a solve that has already run it0
-// iterations and recorded nh0 history rows on the host.
+// iterations and recorded nh0 history rows on the host.  The graph is built
+// and instantiated on the first call with signature `sig` and replayed after.
 template <typename Chunk, typename Certify>
-cmf_status solve_graph(const cmf_params* p, char* wsbase, const WsLayout& w, int nblocks,
-                       Chunk chunk, Certify certify, double* h_hist, int hist_cap, int* h_iters,
-                       cudaStream_t st, int it0 = 0, int nh0 = 0) {
+cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
+                       int nblocks, Chunk chunk, Certify certify, double* h_hist, int hist_cap,
+                       int* h_iters, cudaStream_t st, int it0 = 0, int nh0 = 0) {
     SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
     double* dhist = (double*)(wsbase + w.hist);
     const int rows = (int)hist_rows_for(*p);
@@ -551,60 +632,68 @@ cmf_status solve_graph(const cmf_params* p, char* wsbase, const WsLayout& w, int
     k_solve_reset<<<1, 1, 0, st>>>(ctl, it0);
     CMF_CUDA_TRY(cudaGetLastError());
 
-    cudaStream_t cs = nullptr;
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    cmf_status status = CMF_ECUDA;
-    do {
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) break;
-        if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
-        cudaGraphConditionalHandle h;
-        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) !=
-            cudaSuccess)
-            break;
-        cudaGraphNodeParams np = {};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        cudaGraphNode_t node;
-        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) break;
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeRelaxed) != cudaSuccess)
-            break;
-        cudaError_t e1 = chunk(cs);
-        cudaError_t e2 = e1 == cudaSuccess ? certify(cs) : e1;
-        cudaError_t e3 = e2 == cudaSuccess ? reduce_partials(partials, nblocks, scal, cs) : e2;
-        if (e3 == cudaSuccess) {
-            k_solve_decide<<<1, 1, 0, cs>>>(scal, ctl, dhist, rows, p->check_every,
-                                            p->max_iter, p->tol_gap, h);
-            e3 = cudaGetLastError();
-        }
-        cudaGraph_t captured = nullptr;
-        cudaError_t e4 = cudaStreamEndCapture(cs, &captured);
-        if (e3 != cudaSuccess || e4 != cudaSuccess) break;
-        if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) break;
-        if (cudaGraphLaunch(ge, st) != cudaSuccess) break;
-        SolveCtl hc;
-        if (cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            break;
-        if (cudaStreamSynchronize(st) != cudaSuccess) break;
-        const int n = hc.checks < rows ? hc.checks : rows;
-        const int room = hist_cap > nh0 ? hist_cap - nh0 : 0;
-        const int ncopy = n < room ? n : room;
-        if (h_hist && ncopy > 0) {
-            if (cudaMemcpy(h_hist + 5 * (size_t)nh0, dhist, sizeof(double) * 5 * (size_t)ncopy,
-                           cudaMemcpyDeviceToHost) != cudaSuccess)
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    cudaGraphExec_t ge = graph_lookup(sig);
+    if (!ge) {
+        cudaStream_t cs = nullptr;
+        cudaGraph_t g = nullptr;
+        bool ok = false;
+        do {
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) break;
+            if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) !=
+                cudaSuccess)
                 break;
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) break;
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed) != cudaSuccess)
+                break;
+            cudaError_t e1 = chunk(cs);
+            cudaError_t e2 = e1 == cudaSuccess ? certify(cs) : e1;
+            cudaError_t e3 =
+                e2 == cudaSuccess ? reduce_partials(partials, nblocks, scal, cs) : e2;
+            if (e3 == cudaSuccess) {
+                k_solve_decide<<<1, 1, 0, cs>>>(scal, ctl, dhist, rows, p->check_every,
+                                                p->max_iter, p->tol_gap, h);
+                e3 = cudaGetLastError();
+            }
+            cudaGraph_t captured = nullptr;
+            cudaError_t e4 = cudaStreamEndCapture(cs, &captured);
+            if (e3 != cudaSuccess || e4 != cudaSuccess) break;
+            if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) break;
+            ok = true;
+        } while (0);
+        if (cs) cudaStreamDestroy(cs);
+        if (!ok) {
+            if (ge) cudaGraphExecDestroy(ge);
+            if (g) cudaGraphDestroy(g);
+            return CMF_ECUDA;
         }
-        if (h_iters) *h_iters = hc.it;
-        status = hc.stop == 1 ? CMF_OK : (hc.stop == 3 ? CMF_ETIMEOUT : CMF_NOT_CONVERGED);
-    } while (0);
-    if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
-    if (cs) cudaStreamDestroy(cs);
-    return status;
+        graph_insert(sig, g, ge);
+    }
+    if (cudaGraphLaunch(ge, st) != cudaSuccess) {
+        graph_drop(ge);
+        return CMF_ECUDA;
+    }
+    SolveCtl hc;
+    CMF_CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CMF_CUDA_TRY(cudaStreamSynchronize(st));
+    const int n = hc.checks < rows ? hc.checks : rows;
+    const int room = hist_cap > nh0 ? hist_cap - nh0 : 0;
+    const int ncopy = n < room ? n : room;
+    if (h_hist && ncopy > 0)
+        CMF_CUDA_TRY(cudaMemcpy(h_hist + 5 * (size_t)nh0, dhist, sizeof(double) * 5 * (size_t)ncopy,
+                                cudaMemcpyDeviceToHost));
+    if (h_iters) *h_iters = hc.it;
+    return hc.stop == 1 ? CMF_OK : (hc.stop == 3 ? CMF_ETIMEOUT : CMF_NOT_CONVERGED);
 }
 
 // Progress of a host-driven solve loop.
@@ -659,9 +748,10 @@ cmf_status finish_loop(const LoopState& ls, Copy copy_back, int* h_iters, cudaSt
 // (their coefficients change from launch to launch, a graph's are fixed), the
 // rest in the device-driven graph where it applies, else host-driven.
 template <typename Run, typename Eval, typename Copy, typename Chunk, typename Certify>
-cmf_status solve_driver(const cmf_params* p, char* wsbase, const WsLayout& w, int nblocks,
-                        Run run, Eval eval, Copy copy_back, Chunk chunk, Certify certify,
-                        double* h_hist, int hist_cap, int* h_iters, cudaStream_t st) {
+cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
+                        int nblocks, Run run, Eval eval, Copy copy_back, Chunk chunk,
+                        Certify certify, double* h_hist, int hist_cap, int* h_iters,
+                        cudaStream_t st) {
     LoopState ls;
     if (!graph_eligible(*p)) {
         cmf_status s = loop_chunks(p, p->max_iter, run, eval, h_hist, hist_cap, ls);
@@ -675,8 +765,8 @@ cmf_status solve_driver(const cmf_params* p, char* wsbase, const WsLayout& w, in
         ls.cur = 0;
         if (ls.converged || ls.it >= p->max_iter) return finish_loop(ls, copy_back, h_iters, st);
     }
-    return solve_graph(p, wsbase, w, nblocks, chunk, certify, h_hist, hist_cap, h_iters, st,
-                       ls.it, ls.nh);
+    return solve_graph(p, sig, wsbase, w, nblocks, chunk, certify, h_hist, hist_cap, h_iters,
+                       st, ls.it, ls.nh);
 }
 
 }  // namespace
@@ -793,8 +883,11 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
     CMF_CUDA_TRY(cudaMemsetAsync(&((SolveCtl*)(c.wsbase + c.w.ctl))->err, 0, sizeof(int), st));
     if (!p->warm_start)
         CMF_CUDA_TRY(binary_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    const SolveSig sig = make_sig(0, 2, H, W, pitch, alpha0,
+                                  {d_Cs, d_Ct, d_alpha, d_u, d_qx, d_qy, d_ps, d_pt, d_ws},
+                                  *p);
     return solve_driver(
-        p, c.wsbase, c.w, eval_blocks(H, W),
+        p, sig, c.wsbase, c.w, eval_blocks(H, W),
         [&](int n, int& cur, int k0) { return binary_run(c, n, cur, st, k0); },
         [&](int cur, double* out) {
             return binary_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
@@ -809,6 +902,16 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
                                (double*)(c.wsbase + c.w.partials), s);
         },
         h_hist, hist_cap, h_iters, st);
+}
+
+cmf_status cmf_release_graphs(void) {
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (GraphEntry& e : *g_graphs) {
+        cudaGraphExecDestroy(e.ge);
+        cudaGraphDestroy(e.g);
+    }
+    g_graphs->clear();
+    return CMF_OK;
 }
 
 cmf_status cmf_init_potts(const float* d_C, int L, int H, int W, int pitch, const cmf_params* p,
@@ -870,8 +973,10 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
     CMF_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), st));
     if (!p->warm_start)
         CMF_CUDA_TRY(potts_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    const SolveSig sig = make_sig(1, L, H, W, pitch, alpha0,
+                                  {d_C, d_alpha, d_u, d_qx, d_qy, d_p, d_ps, d_ws}, *p);
     return solve_driver(
-        p, c.wsbase, c.w, eval_blocks(H, W),
+        p, sig, c.wsbase, c.w, eval_blocks(H, W),
         [&](int n, int& cur, int k0) { return potts_run(c, n, cur, st, k0); },
         [&](int cur, double* out) {
             return potts_eval_state(c, cur == 0 ? c.user : c.ws, out, st);

@@ -143,6 +143,11 @@ def test_rho_schedule_rejected_without_launch(cmf):
     del keep
 
 
+def test_release_graphs_with_nothing_kept(cmf):
+    # no graph was built in this process: nothing to destroy, no CUDA call
+    assert cmf.lib().cmf_release_graphs() == cmf.OK
+
+
 def test_status_strings(cmf):
     lib = cmf.lib()
     for s in range(6):
