@@ -110,8 +110,8 @@ typedef struct {
     int use_graph;     /* cmf_solve_*: 1 = device-driven loop (a CUDA graph whose
                           conditional WHILE node repeats {check_every iterations,
                           certificates, stop test} with no host round trip; used
-                          when max_iter % check_every == 0 and, for CMF_FUSED,
-                          check_every is even), else a host-driven loop        */
+                          when max_iter % check_every == 0), else a host-driven
+                          loop; both give identical results                  */
     int variant;       /* kernel variant of the fused ADMM algorithms:
                           0 = automatic: warp strips where the layout allows
                           them (binary ADMM: two iterations per launch, as 4),

@@ -38,6 +38,7 @@ struct SolveCtl {
     int checks;  // certificate evaluations done
     int stop;    // 0 running, 1 converged, 2 iteration cap, 3 device wait timed out
     int err;     // kErrWaitTimeout: a bounded device-side wait ran out
+    int where;   // buffer set holding the state when the loop stopped (1 = workspace)
 };
 
 WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool potts) {
@@ -247,10 +248,11 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
 // the first of them within the call (for the rho schedule).
 cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, int k0 = 0) {
     float* tmp = (float*)(c.wsbase + c.w.tmp);
-    // Two-iteration launches: an even number of them, after the scheduled
-    // iterations, so the result lands in the same buffer set as n single
-    // launches would leave it (a graph chunk of even length ends in the
-    // caller's buffers).
+    // Two-iteration launches after the scheduled iterations, an even number
+    // of them (so n single launches and this leave the state in the same
+    // buffer set: a chunk of even length ends in the caller's buffers and the
+    // device-driven loop body stays one chunk long, measured faster than five
+    // pairs and a two-chunk body), single launches for the rest.
     int i = 0;
     if (c.pairs) {
         const int sched = c.prm.rho_schedule_len > k0 ? c.prm.rho_schedule_len - k0 : 0;
@@ -495,12 +497,16 @@ __global__ void k_solve_reset(SolveCtl* ctl, int it0) {
     ctl->it = it0;
     ctl->checks = 0;
     ctl->stop = 0;
+    ctl->where = 0;
 }
 
 // One thread: turn the reduced (E, D, res^2) into a history row and decide
-// whether the loop body runs again.
+// whether the loop goes on.  The state it certified is in buffer set `where`.
+// set_h: 1 = h is the loop's condition, 2 = h is the condition of the second
+// half of a two-chunk loop body, 0 = leave the conditions to k_solve_loop_cond.
 __global__ void k_solve_decide(const double* scal, SolveCtl* ctl, double* hist, int hist_rows,
-                               int K, int max_iter, double tol, cudaGraphConditionalHandle h) {
+                               int K, int max_iter, double tol, cudaGraphConditionalHandle h,
+                               int set_h, int where) {
     const double E = scal[0], D = scal[1], R = scal[2];
     const double gap = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
     const int it = ctl->it + K;
@@ -519,7 +525,13 @@ __global__ void k_solve_decide(const double* scal, SolveCtl* ctl, double* hist, 
     const bool failed = ctl->err == kErrWaitTimeout;
     const bool go = !converged && !failed && it + K <= max_iter;
     ctl->stop = go ? 0 : (failed ? 3 : (converged ? 1 : 2));
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (!go) ctl->where = where;
+    if (set_h) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// End of a two-chunk loop body: go on unless either half stopped.
+__global__ void k_solve_loop_cond(const SolveCtl* ctl, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, ctl->stop == 0 ? 1u : 0u);
 }
 
 size_t hist_rows_for(const cmf_params& p) {
@@ -528,12 +540,11 @@ size_t hist_rows_for(const cmf_params& p) {
 }
 
 // Whether the graph path can reproduce the host loop exactly: whole chunks
-// only, and an even chunk for the fused ping-pong so every chunk ends in the
-// caller's buffers.
+// only.  (A chunk that ends in the workspace buffers makes the loop body two
+// chunks long, see solve_graph.)
 bool graph_eligible(const cmf_params& p) {
     if (!p.use_graph || p.max_iter < p.check_every) return false;
     if (p.max_iter % p.check_every != 0) return false;
-    if (p.impl == CMF_FUSED && (p.check_every & 1)) return false;
     return true;
 }
 
@@ -615,15 +626,22 @@ void graph_drop(cudaGraphExec_t ge) {
         }
 }
 
-// `chunk(stream)` launches check_every iterations that start and end in the
-// caller's buffers; `certify(stream)` launches the certificate kernel into
-// the partials.  The loop continues a solve that has already run it0
+// `chunk(stream, from)` launches check_every iterations starting in buffer
+// set `from` (0 = the caller's, 1 = the workspace's) and returns the set they
+// end in through `to`; `certify(stream, set)` launches the certificate kernel
+// for a set into the partials.  A chunk that ends in the caller's buffers
+// makes the loop body {chunk, certificates, decide}; one that ends in the
+// workspace makes it two chunks, the second under a conditional IF node that
+// the first half's decision sets, and a last kernel that sets the loop's
+// condition (so a solve can stop after either half; `copy_back` then brings
+// the state home).  The loop continues a solve that has already run it0
 // iterations and recorded nh0 history rows on the host.  The graph is built
 // and instantiated on the first call with signature `sig` and replayed after.
-template <typename Chunk, typename Certify>
+template <typename Chunk, typename Certify, typename Copy>
 cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
-                       int nblocks, Chunk chunk, Certify certify, double* h_hist, int hist_cap,
-                       int* h_iters, cudaStream_t st, int it0 = 0, int nh0 = 0) {
+                       int nblocks, Chunk chunk, Certify certify, Copy copy_back,
+                       double* h_hist, int hist_cap, int* h_iters, cudaStream_t st, int it0 = 0,
+                       int nh0 = 0) {
     SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
     double* dhist = (double*)(wsbase + w.hist);
     const int rows = (int)hist_rows_for(*p);
@@ -635,11 +653,12 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
     std::lock_guard<std::mutex> lock(g_graph_mu);
     cudaGraphExec_t ge = graph_lookup(sig);
     if (!ge) {
-        cudaStream_t cs = nullptr;
+        cudaStream_t cs = nullptr, cs2 = nullptr;
         cudaGraph_t g = nullptr;
         bool ok = false;
         do {
             if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) break;
+            if (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess) break;
             if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
             cudaGraphConditionalHandle h;
             if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) !=
@@ -656,21 +675,72 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
             if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeRelaxed) != cudaSuccess)
                 break;
-            cudaError_t e1 = chunk(cs);
-            cudaError_t e2 = e1 == cudaSuccess ? certify(cs) : e1;
-            cudaError_t e3 =
-                e2 == cudaSuccess ? reduce_partials(partials, nblocks, scal, cs) : e2;
-            if (e3 == cudaSuccess) {
+            int mid = 0;
+            cudaError_t e = chunk(cs, 0, mid);
+            // the IF node's handle, only when there is a second half (a handle
+            // without its node fails the instantiation)
+            cudaGraphConditionalHandle h_if = 0;
+            if (e == cudaSuccess && mid)
+                e = cudaGraphConditionalHandleCreate(&h_if, body, 0, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess) e = certify(cs, mid);
+            if (e == cudaSuccess) e = reduce_partials(partials, nblocks, scal, cs);
+            if (e == cudaSuccess) {
                 k_solve_decide<<<1, 1, 0, cs>>>(scal, ctl, dhist, rows, p->check_every,
-                                                p->max_iter, p->tol_gap, h);
-                e3 = cudaGetLastError();
+                                                p->max_iter, p->tol_gap, mid ? h_if : h,
+                                                mid ? 2 : 1, mid);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess && mid) {
+                // second half: an IF node on the first half's decision
+                cudaStreamCaptureStatus cst;
+                const cudaGraphNode_t* deps = nullptr;
+                const cudaGraphEdgeData* edges = nullptr;
+                size_t ndeps = 0;
+                cudaGraph_t cg = nullptr;
+                e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &edges, &ndeps);
+                cudaGraphNodeParams ip = {};
+                ip.type = cudaGraphNodeTypeConditional;
+                ip.conditional.handle = h_if;
+                ip.conditional.type = cudaGraphCondTypeIf;
+                ip.conditional.size = 1;
+                cudaGraphNode_t ifnode;
+                if (e == cudaSuccess)
+                    e = cudaGraphAddNode(&ifnode, body, deps, edges, ndeps, &ip);
+                if (e == cudaSuccess)
+                    e = cudaStreamUpdateCaptureDependencies(cs, &ifnode, nullptr, 1,
+                                                            cudaStreamSetCaptureDependencies);
+                if (e == cudaSuccess)
+                    e = cudaStreamBeginCaptureToGraph(cs2, ip.conditional.phGraph_out[0],
+                                                      nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    int end = 1;
+                    cudaError_t f = chunk(cs2, 1, end);
+                    if (f == cudaSuccess && end != 0) f = cudaErrorInvalidValue;
+                    if (f == cudaSuccess) f = certify(cs2, 0);
+                    if (f == cudaSuccess) f = reduce_partials(partials, nblocks, scal, cs2);
+                    if (f == cudaSuccess) {
+                        k_solve_decide<<<1, 1, 0, cs2>>>(scal, ctl, dhist, rows,
+                                                         p->check_every, p->max_iter,
+                                                         p->tol_gap, h, 0, 0);
+                        f = cudaGetLastError();
+                    }
+                    cudaGraph_t cap2 = nullptr;
+                    cudaError_t f2 = cudaStreamEndCapture(cs2, &cap2);
+                    e = f != cudaSuccess ? f : f2;
+                }
+                if (e == cudaSuccess) {
+                    k_solve_loop_cond<<<1, 1, 0, cs>>>(ctl, h);
+                    e = cudaGetLastError();
+                }
             }
             cudaGraph_t captured = nullptr;
             cudaError_t e4 = cudaStreamEndCapture(cs, &captured);
-            if (e3 != cudaSuccess || e4 != cudaSuccess) break;
+            if (e != cudaSuccess || e4 != cudaSuccess) break;
             if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) break;
             ok = true;
         } while (0);
+        if (cs2) cudaStreamDestroy(cs2);
         if (cs) cudaStreamDestroy(cs);
         if (!ok) {
             if (ge) cudaGraphExecDestroy(ge);
@@ -693,6 +763,10 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
         CMF_CUDA_TRY(cudaMemcpy(h_hist + 5 * (size_t)nh0, dhist, sizeof(double) * 5 * (size_t)ncopy,
                                 cudaMemcpyDeviceToHost));
     if (h_iters) *h_iters = hc.it;
+    if (hc.where != 0) {  // stopped after the first half of a two-chunk body
+        CMF_CUDA_TRY(copy_back());
+        CMF_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return hc.stop == 1 ? CMF_OK : (hc.stop == 3 ? CMF_ETIMEOUT : CMF_NOT_CONVERGED);
 }
 
@@ -761,12 +835,12 @@ cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, 
     if (p->rho_schedule_len > 0) {
         cmf_status s = loop_chunks(p, p->rho_schedule_len, run, eval, h_hist, hist_cap, ls);
         if (s != CMF_OK) return s;
-        if (ls.cur != 0) CMF_CUDA_TRY(copy_back());  // whole even chunks end at 0
+        if (ls.cur != 0) CMF_CUDA_TRY(copy_back());  // the graph starts from the caller's set
         ls.cur = 0;
         if (ls.converged || ls.it >= p->max_iter) return finish_loop(ls, copy_back, h_iters, st);
     }
-    return solve_graph(p, sig, wsbase, w, nblocks, chunk, certify, h_hist, hist_cap, h_iters,
-                       st, ls.it, ls.nh);
+    return solve_graph(p, sig, wsbase, w, nblocks, chunk, certify, copy_back, h_hist, hist_cap,
+                       h_iters, st, ls.it, ls.nh);
 }
 
 }  // namespace
@@ -893,13 +967,13 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
             return binary_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
         },
         [&]() { return copy_binary(c.user, c.ws, c.P.g, c.storage, st); },
-        [&](cudaStream_t s) {  // graph chunks run after the schedule
-            int cur = 0;
-            return binary_run(c, p->check_every, cur, s, p->rho_schedule_len);
+        [&](cudaStream_t s, int from, int& to) {  // graph chunks run after the schedule
+            to = from;
+            return binary_run(c, p->check_every, to, s, p->rho_schedule_len);
         },
-        [&](cudaStream_t s) {
-            return binary_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
-                               (double*)(c.wsbase + c.w.partials), s);
+        [&](cudaStream_t s, int set) {
+            return binary_eval(c.storage, c.P, set == 0 ? c.user : c.ws, c.cfg.aniso, c.cfg.dr,
+                               c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s);
         },
         h_hist, hist_cap, h_iters, st);
 }
@@ -982,13 +1056,13 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
             return potts_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
         },
         [&]() { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); },
-        [&](cudaStream_t s) {  // graph chunks run after the schedule
-            int cur = 0;
-            return potts_run(c, p->check_every, cur, s, p->rho_schedule_len);
+        [&](cudaStream_t s, int from, int& to) {  // graph chunks run after the schedule
+            to = from;
+            return potts_run(c, p->check_every, to, s, p->rho_schedule_len);
         },
-        [&](cudaStream_t s) {
-            return potts_eval(c.storage, c.P, c.user, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
-                              (double*)(c.wsbase + c.w.partials), s);
+        [&](cudaStream_t s, int set) {
+            return potts_eval(c.storage, c.P, set == 0 ? c.user : c.ws, c.cfg.aniso, c.cfg.dr,
+                              c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s);
         },
         h_hist, hist_cap, h_iters, st);
 }

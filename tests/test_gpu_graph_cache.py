@@ -104,3 +104,33 @@ def test_potts_repeated_solves(cmf):
         runs.append((st, it, hist.copy(), s.state()))
     for r in runs[1:]:
         _same(runs[0], r)
+
+
+@pytest.mark.parametrize("check_every,max_iter", [(10, 4000), (9, 3996), (7, 3997), (5, 4000),
+                                                  (10, 30), (10, 40), (3, 30), (2, 4000)])
+@pytest.mark.parametrize("model", ["binary", "binary_single", "potts"])
+def test_graph_body_shapes_equal_host_loop(cmf, model, check_every, max_iter):
+    """Chunks that end in the workspace buffers (an odd number of launches:
+    5 pairs, or 4 pairs and a single, or an odd count of single launches)
+    make the loop body two chunks with the second under an IF node; solves
+    that stop after either half, or at max_iter, equal the host loop."""
+    out = []
+    tol = 1e-9 if max_iter < 100 else 1e-4  # the short runs stop at max_iter
+    for use_graph in (1, 0):
+        if model == "potts":
+            inst = synth.config3(48, 64)
+            p = cmf.default_params(2, 4, tol_gap=tol, max_iter=max_iter,
+                                   check_every=check_every, use_graph=use_graph)
+            s = cmf.alloc_potts(inst, p)
+            st, it, hist = cmf.cmf_solve_potts(s)
+            out.append((st, it, hist.copy(), s.state()))
+        else:
+            inst = synth.config2(80, 112)
+            p = cmf.default_params(2, 2, tol_gap=tol, max_iter=max_iter,
+                                   check_every=check_every, use_graph=use_graph,
+                                   variant=2 if model == "binary_single" else 0)
+            b = cmf.alloc_binary(inst, p)
+            out.append(_solve(cmf, b))
+    _same(out[0], out[1])
+    if max_iter < 100:
+        assert out[0][0] == cmf.NOT_CONVERGED and out[0][1] == max_iter
