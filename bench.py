@@ -474,13 +474,14 @@ def main():
     iters = int(np.median(iters_all))
     n_checks = int(np.ceil(iters / CHECK_EVERY))
     # per solve: init, loop reset; per check: the chunk's iteration launches (two
-    # iterations per launch in an even number of launches, single ones for the rest),
-    # certificates, their reduction, the stop decision; a chunk of an odd launch count
-    # makes the loop body two chunks long, closed by one loop-condition kernel
-    pairs = CHECK_EVERY // 4 * 2
-    chunk_launches = pairs + (CHECK_EVERY - 2 * pairs)
-    bodies = (n_checks + 1) // 2 if chunk_launches % 2 else 0
-    launches = args.steps * (2 + n_checks * (chunk_launches + 3) + bodies)
+    # iterations per launch, one single launch for an odd remainder; three buffer sets
+    # let a chunk of two or more launches end in the caller's buffers) and the
+    # certificate launch (its last block reduces and takes the stop decision); a lone
+    # launch per chunk would make the loop body two chunks long, closed by one
+    # loop-condition kernel
+    chunk_launches = CHECK_EVERY // 2 + CHECK_EVERY % 2
+    bodies = (n_checks + 1) // 2 if chunk_launches == 1 else 0
+    launches = args.steps * (2 + n_checks * (chunk_launches + 1) + bodies)
 
     # --- end to end through the C ABI with host buffers -------------------------------
     costs_h = [torch.from_numpy(np.ascontiguousarray(np.pad(

@@ -21,6 +21,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Workspace regions (offsets from the workspace base).
 struct WsLayout {
     size_t state;     // second state buffer set (ping-pong of the fused form)
+    size_t state2;    // third set (binary fused form: routes two-iteration launches)
     size_t tmp;       // float planes used by the plain form
     size_t partials;  // 3 doubles per certificate block
     size_t scalars;   // 4 doubles
@@ -30,16 +31,6 @@ struct WsLayout {
 };
 
 size_t hist_rows_for(const cmf_params& p);
-
-// Control block in the workspace: the device-driven solve loop's counters and
-// the sticky error word that kernels with bounded waits set on a timeout.
-struct SolveCtl {
-    int it;      // iterations done
-    int checks;  // certificate evaluations done
-    int stop;    // 0 running, 1 converged, 2 iteration cap, 3 device wait timed out
-    int err;     // kErrWaitTimeout: a bounded device-side wait ran out
-    int where;   // buffer set holding the state when the loop stopped (1 = workspace)
-};
 
 WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool potts) {
     const size_t plane = (size_t)H * (size_t)pitch;
@@ -51,6 +42,11 @@ WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool pot
     w.state = off;
     off += align_up(plane * 4 * nu);
     for (int i = 0; i < nf; ++i) off += align_up(plane * es);
+    w.state2 = off;
+    if (!potts && p.impl == CMF_FUSED) {
+        off += align_up(plane * 4 * nu);
+        for (int i = 0; i < nf; ++i) off += align_up(plane * es);
+    }
     w.tmp = off;
     // plain forms: g and div q^{k+1} (per label for Potts); the fused kernels
     // keep everything on chip
@@ -135,10 +131,10 @@ StepConfig step_at(const StepConfig& base, const cmf_params& p, int L, bool pott
 
 // ---- binary ---------------------------------------------------------------
 
-BinStateV ws_binary_state(char* ws, const WsLayout& w, const Grid& G, int storage) {
+BinStateV ws_binary_state(char* ws, size_t off, const Grid& G, int storage) {
     const size_t plane = G.plane;
     const size_t es = dtype_size(storage);
-    char* base = ws + w.state;
+    char* base = ws + off;
     BinStateV s;
     s.u = (float*)base;
     base += align_up(plane * 4);
@@ -169,7 +165,7 @@ cudaError_t copy_binary(const BinStateV& dst, const BinStateV& src, const Grid& 
 
 struct BinaryCall {
     BinProblem P;
-    BinStateV user, ws;
+    BinStateV user, ws, ws2;  // buffer sets 0, 1, 2 (set 2: fused form only)
     WsLayout w;
     char* wsbase;
     StepConfig cfg;
@@ -203,7 +199,8 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     call.P = BinProblem{Cs, Ct, make_alpha(alpha, alpha0), make_grid(H, W, pitch)};
     call.user = BinStateV{u, qx, qy, ps, pt};
     call.wsbase = (char*)ws;
-    call.ws = ws_binary_state(call.wsbase, call.w, call.P.g, p->storage);
+    call.ws = ws_binary_state(call.wsbase, call.w.state, call.P.g, p->storage);
+    call.ws2 = ws_binary_state(call.wsbase, call.w.state2, call.P.g, p->storage);
     call.cfg = make_step(*p, 2, false);
     call.prm = *p;
     call.storage = p->storage;
@@ -243,36 +240,49 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     return CMF_OK;
 }
 
-// Run n iterations starting from `cur` (0 = user buffers, 1 = workspace);
+const BinStateV& bset(const BinaryCall& c, int i) {
+    return i == 0 ? c.user : (i == 1 ? c.ws : c.ws2);
+}
+
+// Run n iterations starting from `cur` (0 = user buffers, 1 = workspace,
+// 2 = the workspace's third set, used by the two-iteration launches);
 // returns the index of the buffer set holding the result.  k0 is the index of
 // the first of them within the call (for the rho schedule).
 cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, int k0 = 0) {
     float* tmp = (float*)(c.wsbase + c.w.tmp);
-    // Two-iteration launches after the scheduled iterations, an even number
-    // of them (so n single launches and this leave the state in the same
-    // buffer set: a chunk of even length ends in the caller's buffers and the
-    // device-driven loop body stays one chunk long, measured faster than five
-    // pairs and a two-chunk body), single launches for the rest.
+    // Two-iteration launches after the scheduled iterations (one single
+    // launch for an odd remainder).  With three buffer sets a run of at least
+    // two launches ends in the set it started from: start -> x -> y -> x ...
+    // -> start, x and y the other two sets; a lone launch goes to the
+    // caller's set, or from it to the workspace.
     int i = 0;
     if (c.pairs) {
         const int sched = c.prm.rho_schedule_len > k0 ? c.prm.rho_schedule_len - k0 : 0;
         const int first = sched < n ? sched : n;
         for (; i < first; ++i) {
             const StepConfig cfg = step_at(c.cfg, c.prm, 2, false, k0 + i);
-            const BinStateV& a = cur == 0 ? c.user : c.ws;
-            const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.ac, st);
+            const int dst = cur == 0 ? 1 : 0;
+            cudaError_t e = binary_strip_step(c.storage, c.P, bset(c, cur), bset(c, dst),
+                                              cfg.aniso, cfg.ac, st);
             if (e != cudaSuccess) return e;
-            cur ^= 1;
+            cur = dst;
         }
-        const int npairs = (n - first) / 4 * 2;
-        for (int j = 0; j < npairs; ++j, i += 2) {
-            const BinStateV& a = cur == 0 ? c.user : c.ws;
-            const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_strip2_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st);
+        const int npairs = (n - first) / 2, nsingle = (n - first) % 2;
+        const int nl = npairs + nsingle;
+        const int start = cur;
+        const int x = start == 0 ? 1 : 0, y = start == 2 ? 1 : 2;
+        for (int j = 0; j < nl; ++j) {
+            const int dst = nl == 1 ? (start == 0 ? 1 : 0)
+                                    : (j == nl - 1 ? start : (j % 2 == 0 ? x : y));
+            const BinStateV& a = bset(c, cur);
+            const BinStateV& b = bset(c, dst);
+            cudaError_t e =
+                j < npairs ? binary_strip2_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st)
+                           : binary_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st);
             if (e != cudaSuccess) return e;
-            cur ^= 1;
+            cur = dst;
         }
+        return cudaSuccess;
     }
     for (; i < n; ++i) {
         const StepConfig cfg = step_at(c.cfg, c.prm, 2, false, k0 + i);
@@ -305,11 +315,10 @@ cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, in
     return cudaSuccess;
 }
 
-cmf_status finish_eval(char* wsbase, const WsLayout& w, int nblocks, double* h_out,
-                       cudaStream_t st) {
-    double* partials = (double*)(wsbase + w.partials);
+// The certificate launch has reduced its partials into the scalars (its last
+// block); read them and the error word.
+cmf_status finish_eval(char* wsbase, const WsLayout& w, double* h_out, cudaStream_t st) {
     double* scal = (double*)(wsbase + w.scalars);
-    CMF_CUDA_TRY(reduce_partials(partials, nblocks, scal, st));
     double h[3];
     CMF_CUDA_TRY(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, st));
     int* err = &((SolveCtl*)(wsbase + w.ctl))->err;
@@ -328,11 +337,21 @@ cmf_status finish_eval(char* wsbase, const WsLayout& w, int nblocks, double* h_o
     return CMF_OK;
 }
 
+// The certificate launch with its own reduction (no stop decision).
+EvalTail reduce_tail(char* wsbase, const WsLayout& w) {
+    EvalTail T;
+    T.ctl = (SolveCtl*)(wsbase + w.ctl);
+    T.scal = (double*)(wsbase + w.scalars);
+    return T;
+}
+
 cmf_status binary_eval_state(const BinaryCall& c, const BinStateV& s, double* h_out,
                              cudaStream_t st) {
+    const EvalTail T = reduce_tail(c.wsbase, c.w);
+    CMF_CUDA_TRY(cudaMemsetAsync(&T.ctl->arrive, 0, sizeof(unsigned), st));
     CMF_CUDA_TRY(binary_eval(c.storage, c.P, s, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
-                             (double*)(c.wsbase + c.w.partials), st));
-    return finish_eval(c.wsbase, c.w, eval_blocks(c.P.g.H, c.P.g.W), h_out, st);
+                             (double*)(c.wsbase + c.w.partials), st, T));
+    return finish_eval(c.wsbase, c.w, h_out, st);
 }
 
 // ---- Potts ----------------------------------------------------------------
@@ -486,9 +505,11 @@ cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st, int 
 
 cmf_status potts_eval_state(const PottsCall& c, const PottsStateV& s, double* h_out,
                             cudaStream_t st) {
+    const EvalTail T = reduce_tail(c.wsbase, c.w);
+    CMF_CUDA_TRY(cudaMemsetAsync(&T.ctl->arrive, 0, sizeof(unsigned), st));
     CMF_CUDA_TRY(potts_eval(c.storage, c.P, s, c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
-                            (double*)(c.wsbase + c.w.partials), st));
-    return finish_eval(c.wsbase, c.w, eval_blocks(c.P.g.H, c.P.g.W), h_out, st);
+                            (double*)(c.wsbase + c.w.partials), st, T));
+    return finish_eval(c.wsbase, c.w, h_out, st);
 }
 
 // ---- device-driven solve loop (CUDA graph with a conditional WHILE node) ----
@@ -498,35 +519,7 @@ __global__ void k_solve_reset(SolveCtl* ctl, int it0) {
     ctl->checks = 0;
     ctl->stop = 0;
     ctl->where = 0;
-}
-
-// One thread: turn the reduced (E, D, res^2) into a history row and decide
-// whether the loop goes on.  The state it certified is in buffer set `where`.
-// set_h: 1 = h is the loop's condition, 2 = h is the condition of the second
-// half of a two-chunk loop body, 0 = leave the conditions to k_solve_loop_cond.
-__global__ void k_solve_decide(const double* scal, SolveCtl* ctl, double* hist, int hist_rows,
-                               int K, int max_iter, double tol, cudaGraphConditionalHandle h,
-                               int set_h, int where) {
-    const double E = scal[0], D = scal[1], R = scal[2];
-    const double gap = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
-    const int it = ctl->it + K;
-    const int n = ctl->checks;
-    ctl->it = it;
-    if (n < hist_rows) {
-        double* row = hist + 5 * (size_t)n;
-        row[0] = it;
-        row[1] = E;
-        row[2] = D;
-        row[3] = gap;
-        row[4] = sqrt(R > 0.0 ? R : 0.0);
-    }
-    ctl->checks = n + 1;
-    const bool converged = gap <= tol;
-    const bool failed = ctl->err == kErrWaitTimeout;
-    const bool go = !converged && !failed && it + K <= max_iter;
-    ctl->stop = go ? 0 : (failed ? 3 : (converged ? 1 : 2));
-    if (!go) ctl->where = where;
-    if (set_h) cudaGraphSetConditional(h, go ? 1u : 0u);
+    ctl->arrive = 0;
 }
 
 // End of a two-chunk loop body: go on unless either half stopped.
@@ -639,14 +632,20 @@ void graph_drop(cudaGraphExec_t ge) {
 // and instantiated on the first call with signature `sig` and replayed after.
 template <typename Chunk, typename Certify, typename Copy>
 cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
-                       int nblocks, Chunk chunk, Certify certify, Copy copy_back,
-                       double* h_hist, int hist_cap, int* h_iters, cudaStream_t st, int it0 = 0,
-                       int nh0 = 0) {
+                       Chunk chunk, Certify certify, Copy copy_back, double* h_hist,
+                       int hist_cap, int* h_iters, cudaStream_t st, int it0 = 0, int nh0 = 0) {
     SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
     double* dhist = (double*)(wsbase + w.hist);
     const int rows = (int)hist_rows_for(*p);
-    double* partials = (double*)(wsbase + w.partials);
-    double* scal = (double*)(wsbase + w.scalars);
+    // the certificate launch reduces its partials and takes the stop decision
+    // in its last block: one node per check
+    EvalTail T = reduce_tail(wsbase, w);
+    T.decide = true;
+    T.hist = dhist;
+    T.hist_rows = rows;
+    T.K = p->check_every;
+    T.max_iter = p->max_iter;
+    T.tol = p->tol_gap;
     k_solve_reset<<<1, 1, 0, st>>>(ctl, it0);
     CMF_CUDA_TRY(cudaGetLastError());
 
@@ -682,13 +681,12 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
             cudaGraphConditionalHandle h_if = 0;
             if (e == cudaSuccess && mid)
                 e = cudaGraphConditionalHandleCreate(&h_if, body, 0, cudaGraphCondAssignDefault);
-            if (e == cudaSuccess) e = certify(cs, mid);
-            if (e == cudaSuccess) e = reduce_partials(partials, nblocks, scal, cs);
             if (e == cudaSuccess) {
-                k_solve_decide<<<1, 1, 0, cs>>>(scal, ctl, dhist, rows, p->check_every,
-                                                p->max_iter, p->tol_gap, mid ? h_if : h,
-                                                mid ? 2 : 1, mid);
-                e = cudaGetLastError();
+                EvalTail T1 = T;
+                T1.h = mid ? h_if : h;
+                T1.set_h = mid ? 2 : 1;
+                T1.where = mid;
+                e = certify(cs, mid, T1);
             }
             if (e == cudaSuccess && mid) {
                 // second half: an IF node on the first half's decision
@@ -717,13 +715,9 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
                     int end = 1;
                     cudaError_t f = chunk(cs2, 1, end);
                     if (f == cudaSuccess && end != 0) f = cudaErrorInvalidValue;
-                    if (f == cudaSuccess) f = certify(cs2, 0);
-                    if (f == cudaSuccess) f = reduce_partials(partials, nblocks, scal, cs2);
                     if (f == cudaSuccess) {
-                        k_solve_decide<<<1, 1, 0, cs2>>>(scal, ctl, dhist, rows,
-                                                         p->check_every, p->max_iter,
-                                                         p->tol_gap, h, 0, 0);
-                        f = cudaGetLastError();
+                        EvalTail T2 = T;  // conditions left to k_solve_loop_cond
+                        f = certify(cs2, 0, T2);
                     }
                     cudaGraph_t cap2 = nullptr;
                     cudaError_t f2 = cudaStreamEndCapture(cs2, &cap2);
@@ -764,7 +758,7 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
                                 cudaMemcpyDeviceToHost));
     if (h_iters) *h_iters = hc.it;
     if (hc.where != 0) {  // stopped after the first half of a two-chunk body
-        CMF_CUDA_TRY(copy_back());
+        CMF_CUDA_TRY(copy_back(hc.where));
         CMF_CUDA_TRY(cudaStreamSynchronize(st));
     }
     return hc.stop == 1 ? CMF_OK : (hc.stop == 3 ? CMF_ETIMEOUT : CMF_NOT_CONVERGED);
@@ -812,7 +806,7 @@ cmf_status loop_chunks(const cmf_params* p, int it_stop, Run run, Eval eval, dou
 
 template <typename Copy>
 cmf_status finish_loop(const LoopState& ls, Copy copy_back, int* h_iters, cudaStream_t st) {
-    if (ls.cur != 0) CMF_CUDA_TRY(copy_back());
+    if (ls.cur != 0) CMF_CUDA_TRY(copy_back(ls.cur));
     CMF_CUDA_TRY(cudaStreamSynchronize(st));
     if (h_iters) *h_iters = ls.it;
     return ls.converged ? CMF_OK : CMF_NOT_CONVERGED;
@@ -823,7 +817,7 @@ cmf_status finish_loop(const LoopState& ls, Copy copy_back, int* h_iters, cudaSt
 // rest in the device-driven graph where it applies, else host-driven.
 template <typename Run, typename Eval, typename Copy, typename Chunk, typename Certify>
 cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
-                        int nblocks, Run run, Eval eval, Copy copy_back, Chunk chunk,
+                        Run run, Eval eval, Copy copy_back, Chunk chunk,
                         Certify certify, double* h_hist, int hist_cap, int* h_iters,
                         cudaStream_t st) {
     LoopState ls;
@@ -835,11 +829,11 @@ cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, 
     if (p->rho_schedule_len > 0) {
         cmf_status s = loop_chunks(p, p->rho_schedule_len, run, eval, h_hist, hist_cap, ls);
         if (s != CMF_OK) return s;
-        if (ls.cur != 0) CMF_CUDA_TRY(copy_back());  // the graph starts from the caller's set
+        if (ls.cur != 0) CMF_CUDA_TRY(copy_back(ls.cur));  // the graph starts from set 0
         ls.cur = 0;
         if (ls.converged || ls.it >= p->max_iter) return finish_loop(ls, copy_back, h_iters, st);
     }
-    return solve_graph(p, sig, wsbase, w, nblocks, chunk, certify, copy_back, h_hist, hist_cap,
+    return solve_graph(p, sig, wsbase, w, chunk, certify, copy_back, h_hist, hist_cap,
                        h_iters, st, ls.it, ls.nh);
 }
 
@@ -925,7 +919,7 @@ cmf_status cmf_iterate_binary(const float* d_Cs, const float* d_Ct, const float*
     CMF_CUDA_TRY(cudaMemsetAsync(&((SolveCtl*)(c.wsbase + c.w.ctl))->err, 0, sizeof(int), st));
     int cur = 0;
     CMF_CUDA_TRY(binary_run(c, n_iter, cur, st));
-    if (cur != 0) CMF_CUDA_TRY(copy_binary(c.user, c.ws, c.P.g, c.storage, st));
+    if (cur != 0) CMF_CUDA_TRY(copy_binary(c.user, bset(c, cur), c.P.g, c.storage, st));
     return CMF_OK;
 }
 
@@ -961,19 +955,19 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
                                   {d_Cs, d_Ct, d_alpha, d_u, d_qx, d_qy, d_ps, d_pt, d_ws},
                                   *p);
     return solve_driver(
-        p, sig, c.wsbase, c.w, eval_blocks(H, W),
+        p, sig, c.wsbase, c.w,
         [&](int n, int& cur, int k0) { return binary_run(c, n, cur, st, k0); },
         [&](int cur, double* out) {
-            return binary_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
+            return binary_eval_state(c, bset(c, cur), out, st);
         },
-        [&]() { return copy_binary(c.user, c.ws, c.P.g, c.storage, st); },
+        [&](int from) { return copy_binary(c.user, bset(c, from), c.P.g, c.storage, st); },
         [&](cudaStream_t s, int from, int& to) {  // graph chunks run after the schedule
             to = from;
             return binary_run(c, p->check_every, to, s, p->rho_schedule_len);
         },
-        [&](cudaStream_t s, int set) {
-            return binary_eval(c.storage, c.P, set == 0 ? c.user : c.ws, c.cfg.aniso, c.cfg.dr,
-                               c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s);
+        [&](cudaStream_t s, int set, const EvalTail& T) {
+            return binary_eval(c.storage, c.P, bset(c, set), c.cfg.aniso, c.cfg.dr,
+                               c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s, T);
         },
         h_hist, hist_cap, h_iters, st);
 }
@@ -1050,19 +1044,19 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
     const SolveSig sig = make_sig(1, L, H, W, pitch, alpha0,
                                   {d_C, d_alpha, d_u, d_qx, d_qy, d_p, d_ps, d_ws}, *p);
     return solve_driver(
-        p, sig, c.wsbase, c.w, eval_blocks(H, W),
+        p, sig, c.wsbase, c.w,
         [&](int n, int& cur, int k0) { return potts_run(c, n, cur, st, k0); },
         [&](int cur, double* out) {
             return potts_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
         },
-        [&]() { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); },
+        [&](int) { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); },
         [&](cudaStream_t s, int from, int& to) {  // graph chunks run after the schedule
             to = from;
             return potts_run(c, p->check_every, to, s, p->rho_schedule_len);
         },
-        [&](cudaStream_t s, int set) {
+        [&](cudaStream_t s, int set, const EvalTail& T) {
             return potts_eval(c.storage, c.P, set == 0 ? c.user : c.ws, c.cfg.aniso, c.cfg.dr,
-                              c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s);
+                              c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s, T);
         },
         h_hist, hist_cap, h_iters, st);
 }

@@ -446,8 +446,9 @@ __device__ __forceinline__ void binary_eval_tile(BinProblem P, BinState<S> s, fl
 
 template <typename S, bool ANISO, bool DR>
 __global__ void __launch_bounds__(256)
-    k_binary_eval(BinProblem P, BinState<S> s, float tau, double* partials) {
+    k_binary_eval(BinProblem P, BinState<S> s, float tau, double* partials, EvalTail T) {
     binary_eval_tile<S, ANISO, DR>(P, s, tau, partials + 3 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), blockIdx.x, blockIdx.y);
+    eval_tail(T, partials, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,28 +541,29 @@ cudaError_t binary_step(int storage, const BinProblem& P, const BinStateV& a, co
 
 template <typename S>
 static cudaError_t binary_eval_s(const BinProblem& P, const BinStateV& sv, bool aniso, bool dr,
-                                 float tau, double* partials, cudaStream_t st) {
+                                 float tau, double* partials, cudaStream_t st,
+                                 const EvalTail& T) {
     const BinState<S> s = sv.as<S>();
     const dim3 gr = grid_for(P.g, 8 * EVAL_ROWS), bl(32, 8);
     if (aniso) {
-        if (dr) k_binary_eval<S, true, true><<<gr, bl, 0, st>>>(P, s, tau, partials);
-        else k_binary_eval<S, true, false><<<gr, bl, 0, st>>>(P, s, tau, partials);
+        if (dr) k_binary_eval<S, true, true><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
+        else k_binary_eval<S, true, false><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
     } else {
-        if (dr) k_binary_eval<S, false, true><<<gr, bl, 0, st>>>(P, s, tau, partials);
-        else k_binary_eval<S, false, false><<<gr, bl, 0, st>>>(P, s, tau, partials);
+        if (dr) k_binary_eval<S, false, true><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
+        else k_binary_eval<S, false, false><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
     }
     return cudaGetLastError();
 }
 
 cudaError_t binary_eval(int storage, const BinProblem& P, const BinStateV& s, bool aniso, bool dr,
-                        float tau, double* partials, cudaStream_t st) {
+                        float tau, double* partials, cudaStream_t st, const EvalTail& T) {
     const float* al = P.alpha.plane;
     if (binary_strip_eligible(P.g, storage, P.Cs, P.Ct, al, s, s))
-        return binary_eval_strip(storage, P, s, aniso, dr, tau, partials, st);
+        return binary_eval_strip(storage, P, s, aniso, dr, tau, partials, st, T);
     switch (storage) {
-        case CMF_F32: return binary_eval_s<float>(P, s, aniso, dr, tau, partials, st);
-        case CMF_F16: return binary_eval_s<__half>(P, s, aniso, dr, tau, partials, st);
-        default: return binary_eval_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+        case CMF_F32: return binary_eval_s<float>(P, s, aniso, dr, tau, partials, st, T);
+        case CMF_F16: return binary_eval_s<__half>(P, s, aniso, dr, tau, partials, st, T);
+        default: return binary_eval_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st, T);
     }
 }
 

