@@ -47,8 +47,10 @@
  *    cmf_iterate_* and cmf_solve_* clear the record when they start.
  *  - State storage: u is always float32.  Flows (q, p_s, p_t / p_i) are
  *    stored as cmf_params.storage (float32, float16 or bfloat16); all
- *    arithmetic is float32 and the certificates (energies, gap, residual) are
- *    accumulated in float64.
+ *    arithmetic is float32; the certificates (energies, gap, residual) sum
+ *    float32 per-pixel terms in double-float (two floats kept exact by
+ *    two-sum, about 44 significant bits) within a warp and in float64 above
+ *    it.
  */
 #ifndef CMF_H
 #define CMF_H

@@ -410,7 +410,7 @@ __device__ __forceinline__ void binary_eval_tile(BinProblem P, BinState<S> s, fl
     }
     __syncthreads();
 
-    double accE = 0.0, accD = 0.0, accR = 0.0;
+    DF accE = {0.f, 0.f}, accD = {0.f, 0.f}, accR = {0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < EVAL_ROWS; ++j) {
         const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
@@ -425,7 +425,7 @@ __device__ __forceinline__ void binary_eval_tile(BinProblem P, BinState<S> s, fl
         const float gx = c < G.W - 1 ? fminf(fmaxf(u_s[ly + 1][lx + 2], 0.f), 1.f) - ub : 0.f;
         const float gy = r < G.H - 1 ? fminf(fmaxf(u_s[ly + 2][lx + 1], 0.f), 1.f) - ub : 0.f;
         const float tv = ANISO ? fabsf(gx) + fabsf(gy) : sqrtf(gx * gx + gy * gy);
-        accE += (double)((1.f - ub) * cs + ub * ct + al * tv);
+        df_add(accE, (1.f - ub) * cs + ub * ct + al * tv);
         // conservation residual of y, and the max-flow value of P_alpha(y);
         // out-of-grid neighbours of the tile hold 0
         float ps = St::ldw(s.ps + k), pt = St::ldw(s.pt + k);
@@ -436,12 +436,12 @@ __device__ __forceinline__ void binary_eval_tile(BinProblem P, BinState<S> s, fl
         const float dv = (c < G.W - 1 ? fx_s[ly + 1][lx + 1] : 0.f) - fx_s[ly + 1][lx] +
                          (r < G.H - 1 ? fy_s[ly + 1][lx + 1] : 0.f) - fy_s[ly][lx + 1];
         const float rr = dv - ps + pt;
-        accR += (double)(rr * rr);
+        df_add(accR, rr * rr);
         const float dp = (c < G.W - 1 ? px_s[ly + 1][lx + 1] : 0.f) - px_s[ly + 1][lx] +
                          (r < G.H - 1 ? py_s[ly + 1][lx + 1] : 0.f) - py_s[ly][lx + 1];
-        accD += (double)fminf(cs, ct + dp);
+        df_add(accD, fminf(cs, ct + dp));
     }
-    block_reduce3_store(accE, accD, accR, out3);
+    block_reduce3_store_df(accE, accD, accR, out3);
 }
 
 template <typename S, bool ANISO, bool DR>

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const Grid G = P.g;
     const unsigned full = 0xffffffffu;
-    double accE = 0.0, accD = 0.0, accR = 0.0;
+    DF accE = {0.f, 0.f}, accD = {0.f, 0.f}, accR = {0.f, 0.f};
 
     for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
          item += gridDim.x * kStripWarps) {
@@ -526,9 +526,9 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             const float dp_e = px - pxl + wy * py - py_up.x;
             const float dp_o = mxo * qx_ - px + wy * qy_ - py_up.y;
             if (own) {
-                accE += (double)(e_e + e_o);
-                accR += (double)(r_e * r_e + r_o * r_o);
-                accD += (double)(fminf(cs.x, ct.x + dp_e) + fminf(cs.y, ct.y + dp_o));
+                df_add(accE, e_e + e_o);
+                df_add(accR, r_e * r_e + r_o * r_o);
+                df_add(accD, fminf(cs.x, ct.x + dp_e) + fminf(cs.y, ct.y + dp_o));
             }
             fy_up = fy;
             py_up = make_float2(py, qy_);
@@ -537,13 +537,13 @@ __global__ void __launch_bounds__(kStripWarps * 32)
     }
     // block sums, fixed order
     __shared__ double red[3][kStripWarps];
-    accE = warp_sum(accE);
-    accD = warp_sum(accD);
-    accR = warp_sum(accR);
+    accE = df_warp_sum(accE);
+    accD = df_warp_sum(accD);
+    accR = df_warp_sum(accR);
     if (lane == 0) {
-        red[0][wib] = accE;
-        red[1][wib] = accD;
-        red[2][wib] = accR;
+        red[0][wib] = df_value(accE);
+        red[1][wib] = df_value(accD);
+        red[2][wib] = df_value(accR);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

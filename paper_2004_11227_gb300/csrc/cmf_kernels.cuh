@@ -127,6 +127,74 @@ __device__ __forceinline__ void block_reduce3_store(double a, double b, double c
     }
 }
 
+// Double-float accumulator for the certificate sums: the unevaluated sum
+// hi + lo of two floats, each addition made exact by Knuth's two-sum (the
+// rounding error of hi goes to lo), about 44 significant bits.  GB300 runs
+// FP64 arithmetic and conversions at a small fraction of its FP32 rate, so
+// per-pixel terms (float32) are summed this way per lane and per warp and
+// turn into FP64 once per warp; warps and blocks are summed in FP64.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(DF& a, float x) {
+    const float s = a.hi + x;
+    const float v = s - a.hi;
+    const float err = (a.hi - (s - v)) + (x - v);
+    a.hi = s;
+    a.lo += err;
+}
+
+__device__ __forceinline__ void df_add(DF& a, const DF& b) {
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    const float err = (a.hi - (s - v)) + (b.hi - v);
+    a.hi = s;
+    a.lo = a.lo + b.lo + err;
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF b;
+        b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+        b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+        df_add(a, b);
+    }
+    return a;
+}
+
+__device__ __forceinline__ double df_value(const DF& a) { return (double)a.hi + (double)a.lo; }
+
+// Block-level reduction of three double-float accumulators: per-warp sums in
+// double-float, then FP64 across warps in a fixed order; thread 0 stores the
+// block's triple at out3[0..2].
+__device__ __forceinline__ void block_reduce3_store_df(DF a, DF b, DF c, double* out3) {
+    __shared__ double red_df[3][32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
+    a = df_warp_sum(a);
+    b = df_warp_sum(b);
+    c = df_warp_sum(c);
+    if ((tid & 31) == 0) {
+        red_df[0][tid >> 5] = df_value(a);
+        red_df[1][tid >> 5] = df_value(b);
+        red_df[2][tid >> 5] = df_value(c);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double x = 0.0, y = 0.0, z = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            x += red_df[0][w];
+            y += red_df[1][w];
+            z += red_df[2][w];
+        }
+        out3[0] = x;
+        out3[1] = y;
+        out3[2] = z;
+    }
+}
+
 // Value a kernel stores in the workspace error word when a bounded wait runs
 // out (a distinctive value, so an uninitialised workspace is not mistaken for
 // a report).

@@ -498,7 +498,7 @@ __device__ __forceinline__ void potts_eval_tile(PottsProblem P, PottsState<S> s,
     const Grid G = P.g;
     const size_t pl = G.plane;
     const int c = bx_ * 32 + threadIdx.x;
-    double accE = 0.0, accD = 0.0, accR = 0.0;
+    DF accE = {0.f, 0.f}, accD = {0.f, 0.f}, accR = {0.f, 0.f};
     for (int j = 0; j < EVAL_ROWS; ++j) {
         const int r = (by_ * 8 + threadIdx.y) * EVAL_ROWS + j;
         if (r >= G.H || c >= G.W) continue;
@@ -535,11 +535,11 @@ __device__ __forceinline__ void potts_eval_tile(PottsProblem P, PottsState<S> s,
             const float dp = (c < G.W - 1 ? fx : 0.f) - fxl + (r < G.H - 1 ? fy : 0.f) - fyu;
             dmin = fminf(dmin, Cl + dp);
         }
-        accE += (double)e;
-        accD += (double)dmin;
-        accR += (double)rr2;
+        df_add(accE, e);
+        df_add(accD, dmin);
+        df_add(accR, rr2);
     }
-    block_reduce3_store(accE, accD, accR, out3);
+    block_reduce3_store_df(accE, accD, accR, out3);
 }
 
 template <typename S, bool ANISO, bool DR>

@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
     const Grid G = P.g;
     const int L = P.L;
     const unsigned full = 0xffffffffu;
-    double accE = 0.0, accD = 0.0, accR = 0.0;
+    DF accE = {0.f, 0.f}, accD = {0.f, 0.f}, accR = {0.f, 0.f};
 
     for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
          item += gridDim.x * kStripWarps) {
@@ -772,8 +772,8 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                 const float2 cand = make_float2(Cl.x + dp_e, Cl.y + dp_o);
                 dm = l == 0 ? cand : make_float2(fminf(dm.x, cand.x), fminf(dm.y, cand.y));
                 if (own) {
-                    accE += (double)e;
-                    accR += (double)(r_e * r_e + r_o * r_o);
+                    df_add(accE, e);
+                    df_add(accR, r_e * r_e + r_o * r_o);
                 }
                 fy_up = fy;
                 py_up = make_float2(py, qy_);
@@ -784,18 +784,18 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         if (own)
             for (int t = r0; t < r1; ++t) {
                 const float2 dm = dm_s[wib][t - r0][lane];
-                accD += (double)(dm.x + dm.y);
+                df_add(accD, dm.x + dm.y);
             }
         __syncwarp();
     }
     __shared__ double red[3][kStripWarps];
-    accE = warp_sum(accE);
-    accD = warp_sum(accD);
-    accR = warp_sum(accR);
+    accE = df_warp_sum(accE);
+    accD = df_warp_sum(accD);
+    accR = df_warp_sum(accR);
     if (lane == 0) {
-        red[0][wib] = accE;
-        red[1][wib] = accD;
-        red[2][wib] = accR;
+        red[0][wib] = df_value(accE);
+        red[1][wib] = df_value(accD);
+        red[2][wib] = df_value(accR);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
