@@ -52,7 +52,13 @@ WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool pot
     // keep everything on chip
     off += align_up(plane * 4 * (size_t)(p.impl == CMF_PLAIN ? (potts ? 2 * L : 2) : 0));
     w.partials = off;
-    off += align_up(sizeof(double) * 3 * (size_t)eval_blocks(H, W));
+    {
+        // one triple per certificate block: the certificate kernels' grid, or
+        // the two-iteration launch that certifies its result
+        const size_t nb = (size_t)eval_blocks(H, W);
+        const size_t nc = (!potts && p.impl == CMF_FUSED) ? (size_t)binary_cert_max_blocks() : 0;
+        off += align_up(sizeof(double) * 3 * (nb > nc ? nb : nc));
+    }
     w.scalars = off;
     off += align_up(sizeof(double) * 4);
     w.ctl = off;
@@ -247,9 +253,15 @@ const BinStateV& bset(const BinaryCall& c, int i) {
 // Run n iterations starting from `cur` (0 = user buffers, 1 = workspace,
 // 2 = the workspace's third set, used by the two-iteration launches);
 // returns the index of the buffer set holding the result.  k0 is the index of
-// the first of them within the call (for the rho schedule).
-cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, int k0 = 0) {
+// the first of them within the call (for the rho schedule).  cert != nullptr:
+// also certify the result with that tail (in the last two-iteration launch
+// when there is one, else with the certificate kernel).  dry: launch
+// nothing, only follow the buffer sets.
+cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, int k0 = 0,
+                       const EvalTail* cert = nullptr, bool dry = false) {
     float* tmp = (float*)(c.wsbase + c.w.tmp);
+    double* partials = (double*)(c.wsbase + c.w.partials);
+    bool certified = false;
     // Two-iteration launches after the scheduled iterations (one single
     // launch for an odd remainder).  With three buffer sets a run of at least
     // two launches ends in the set it started from: start -> x -> y -> x ...
@@ -262,9 +274,11 @@ cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, in
         for (; i < first; ++i) {
             const StepConfig cfg = step_at(c.cfg, c.prm, 2, false, k0 + i);
             const int dst = cur == 0 ? 1 : 0;
-            cudaError_t e = binary_strip_step(c.storage, c.P, bset(c, cur), bset(c, dst),
-                                              cfg.aniso, cfg.ac, st);
-            if (e != cudaSuccess) return e;
+            if (!dry) {
+                cudaError_t e = binary_strip_step(c.storage, c.P, bset(c, cur), bset(c, dst),
+                                                  cfg.aniso, cfg.ac, st);
+                if (e != cudaSuccess) return e;
+            }
             cur = dst;
         }
         const int npairs = (n - first) / 2, nsingle = (n - first) % 2;
@@ -274,44 +288,62 @@ cudaError_t binary_run(const BinaryCall& c, int n, int& cur, cudaStream_t st, in
         for (int j = 0; j < nl; ++j) {
             const int dst = nl == 1 ? (start == 0 ? 1 : 0)
                                     : (j == nl - 1 ? start : (j % 2 == 0 ? x : y));
-            const BinStateV& a = bset(c, cur);
-            const BinStateV& b = bset(c, dst);
-            cudaError_t e =
-                j < npairs ? binary_strip2_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st)
-                           : binary_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac, st);
-            if (e != cudaSuccess) return e;
+            // the last pair launch carries the certificates when no single follows it
+            const bool cj = cert && j == npairs - 1 && nsingle == 0;
+            if (!dry) {
+                const BinStateV& a = bset(c, cur);
+                const BinStateV& b = bset(c, dst);
+                cudaError_t e =
+                    j < npairs ? binary_strip2_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac,
+                                                    st, cj ? cert : nullptr, partials)
+                               : binary_strip_step(c.storage, c.P, a, b, c.cfg.aniso, c.cfg.ac,
+                                                   st);
+                if (e != cudaSuccess) return e;
+            }
+            certified = certified || cj;
             cur = dst;
         }
-        return cudaSuccess;
+        i = n;
     }
     for (; i < n; ++i) {
         const StepConfig cfg = step_at(c.cfg, c.prm, 2, false, k0 + i);
         if (cfg.plain) {
-            cudaError_t e = binary_step(c.storage, c.P, c.user, c.user, cfg, tmp, st);
-            if (e != cudaSuccess) return e;
+            if (!dry) {
+                cudaError_t e = binary_step(c.storage, c.P, c.user, c.user, cfg, tmp, st);
+                if (e != cudaSuccess) return e;
+            }
             cur = 0;
         } else if (c.strip) {
             const BinStateV& a = cur == 0 ? c.user : c.ws;
             const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e =
-                cfg.dr ? binary_dr_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.dc, st)
-                       : binary_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.ac, st);
-            if (e != cudaSuccess) return e;
+            if (!dry) {
+                cudaError_t e =
+                    cfg.dr ? binary_dr_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.dc, st)
+                           : binary_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.ac, st);
+                if (e != cudaSuccess) return e;
+            }
             cur ^= 1;
         } else if (c.tma) {
             const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_admm_tma_step(c.storage, c.P, b, cfg.aniso, cfg.ac,
-                                                 c.maps[cur], c.err, st);
-            if (e != cudaSuccess) return e;
+            if (!dry) {
+                cudaError_t e = binary_admm_tma_step(c.storage, c.P, b, cfg.aniso, cfg.ac,
+                                                     c.maps[cur], c.err, st);
+                if (e != cudaSuccess) return e;
+            }
             cur ^= 1;
         } else {
             const BinStateV& a = cur == 0 ? c.user : c.ws;
             const BinStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = binary_step(c.storage, c.P, a, b, cfg, tmp, st);
-            if (e != cudaSuccess) return e;
+            if (!dry) {
+                cudaError_t e = binary_step(c.storage, c.P, a, b, cfg, tmp, st);
+                if (e != cudaSuccess) return e;
+            }
             cur ^= 1;
         }
     }
+    if (cert && !certified && !dry)
+        return binary_eval(c.storage, c.P, bset(c, cur), c.cfg.aniso, c.cfg.dr, c.cfg.dc.tau,
+                           partials, st, *cert);
     return cudaSuccess;
 }
 
@@ -460,7 +492,14 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     return CMF_OK;
 }
 
-cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st, int k0 = 0) {
+// As binary_run: n iterations from buffer set `cur` (0 or 1); cert: certify
+// the result with that tail; dry: only follow the buffer sets.
+cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st, int k0 = 0,
+                      const EvalTail* cert = nullptr, bool dry = false) {
+    if (dry) {
+        if (n > 0) cur = c.cfg.plain ? 0 : (n % 2 ? cur ^ 1 : cur);
+        return cudaSuccess;
+    }
     float* tmp = (float*)(c.wsbase + c.w.tmp);
     for (int i = 0; i < n; ++i) {
         const StepConfig cfg = step_at(c.cfg, c.prm, c.P.L, true, k0 + i);
@@ -500,6 +539,9 @@ cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st, int 
             cur ^= 1;
         }
     }
+    if (cert)
+        return potts_eval(c.storage, c.P, cur == 0 ? c.user : c.ws, c.cfg.aniso, c.cfg.dr,
+                          c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), st, *cert);
     return cudaSuccess;
 }
 
@@ -630,9 +672,9 @@ void graph_drop(cudaGraphExec_t ge) {
 // the state home).  The loop continues a solve that has already run it0
 // iterations and recorded nh0 history rows on the host.  The graph is built
 // and instantiated on the first call with signature `sig` and replayed after.
-template <typename Chunk, typename Certify, typename Copy>
+template <typename Chunk, typename EndOf, typename Copy>
 cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
-                       Chunk chunk, Certify certify, Copy copy_back, double* h_hist,
+                       Chunk chunk, EndOf end_of, Copy copy_back, double* h_hist,
                        int hist_cap, int* h_iters, cudaStream_t st, int it0 = 0, int nh0 = 0) {
     SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
     double* dhist = (double*)(wsbase + w.hist);
@@ -674,19 +716,21 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
             if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeRelaxed) != cudaSuccess)
                 break;
-            int mid = 0;
-            cudaError_t e = chunk(cs, 0, mid);
+            // the set a chunk from the caller's buffers ends in decides the body
+            const int mid = end_of(0);
             // the IF node's handle, only when there is a second half (a handle
             // without its node fails the instantiation)
+            cudaError_t e = cudaSuccess;
             cudaGraphConditionalHandle h_if = 0;
-            if (e == cudaSuccess && mid)
-                e = cudaGraphConditionalHandleCreate(&h_if, body, 0, cudaGraphCondAssignDefault);
+            if (mid) e = cudaGraphConditionalHandleCreate(&h_if, body, 0, cudaGraphCondAssignDefault);
             if (e == cudaSuccess) {
                 EvalTail T1 = T;
                 T1.h = mid ? h_if : h;
                 T1.set_h = mid ? 2 : 1;
                 T1.where = mid;
-                e = certify(cs, mid, T1);
+                int got = 0;
+                e = chunk(cs, 0, got, T1);  // iterations and their certificates
+                if (e == cudaSuccess && got != mid) e = cudaErrorInvalidValue;
             }
             if (e == cudaSuccess && mid) {
                 // second half: an IF node on the first half's decision
@@ -712,13 +756,10 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
                                                       nullptr, nullptr, 0,
                                                       cudaStreamCaptureModeRelaxed);
                 if (e == cudaSuccess) {
-                    int end = 1;
-                    cudaError_t f = chunk(cs2, 1, end);
+                    int end = mid;
+                    EvalTail T2 = T;  // conditions left to k_solve_loop_cond
+                    cudaError_t f = chunk(cs2, mid, end, T2);
                     if (f == cudaSuccess && end != 0) f = cudaErrorInvalidValue;
-                    if (f == cudaSuccess) {
-                        EvalTail T2 = T;  // conditions left to k_solve_loop_cond
-                        f = certify(cs2, 0, T2);
-                    }
                     cudaGraph_t cap2 = nullptr;
                     cudaError_t f2 = cudaStreamEndCapture(cs2, &cap2);
                     e = f != cudaSuccess ? f : f2;
@@ -772,21 +813,20 @@ struct LoopState {
     bool converged = false;
 };
 
-// Host-driven chunks of check_every iterations, each followed by the
-// certificates, until convergence, max_iter, or it >= it_stop.
-// `run(n, cur, k0)` advances n iterations whose first is iteration k0 of the
-// solve, `eval(cur, out)` certifies.
-template <typename Run, typename Eval>
-cmf_status loop_chunks(const cmf_params* p, int it_stop, Run run, Eval eval, double* h_hist,
+// Host-driven chunks of check_every iterations, each with the certificates
+// of its result, until convergence, max_iter, or it >= it_stop.
+// `run_cert(n, cur, k0, out)` advances n iterations whose first is iteration
+// k0 of the solve and writes the certificates (E, D, gap, res) to out.
+template <typename RunCert>
+cmf_status loop_chunks(const cmf_params* p, int it_stop, RunCert run_cert, double* h_hist,
                        int hist_cap, LoopState& ls) {
     double out[4];
     while (ls.it < p->max_iter && ls.it < it_stop) {
         const int k =
             p->check_every < p->max_iter - ls.it ? p->check_every : p->max_iter - ls.it;
-        CMF_CUDA_TRY(run(k, ls.cur, ls.it));
-        ls.it += k;
-        cmf_status s = eval(ls.cur, out);
+        cmf_status s = run_cert(k, ls.cur, ls.it, out);
         if (s != CMF_OK) return s;
+        ls.it += k;
         if (h_hist && ls.nh < hist_cap) {
             double* row = h_hist + 5 * (size_t)ls.nh;
             row[0] = ls.it;
@@ -815,25 +855,26 @@ cmf_status finish_loop(const LoopState& ls, Copy copy_back, int* h_iters, cudaSt
 // The solve driver: the iterations a rho schedule covers run host-driven
 // (their coefficients change from launch to launch, a graph's are fixed), the
 // rest in the device-driven graph where it applies, else host-driven.
-template <typename Run, typename Eval, typename Copy, typename Chunk, typename Certify>
+// `chunk(stream, from, to, tail)` captures one graph chunk with its
+// certificates, `end_of(from)` tells the set a chunk ends in.
+template <typename RunCert, typename Copy, typename Chunk, typename EndOf>
 cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
-                        Run run, Eval eval, Copy copy_back, Chunk chunk,
-                        Certify certify, double* h_hist, int hist_cap, int* h_iters,
-                        cudaStream_t st) {
+                        RunCert run_cert, Copy copy_back, Chunk chunk, EndOf end_of,
+                        double* h_hist, int hist_cap, int* h_iters, cudaStream_t st) {
     LoopState ls;
     if (!graph_eligible(*p)) {
-        cmf_status s = loop_chunks(p, p->max_iter, run, eval, h_hist, hist_cap, ls);
+        cmf_status s = loop_chunks(p, p->max_iter, run_cert, h_hist, hist_cap, ls);
         if (s != CMF_OK) return s;
         return finish_loop(ls, copy_back, h_iters, st);
     }
     if (p->rho_schedule_len > 0) {
-        cmf_status s = loop_chunks(p, p->rho_schedule_len, run, eval, h_hist, hist_cap, ls);
+        cmf_status s = loop_chunks(p, p->rho_schedule_len, run_cert, h_hist, hist_cap, ls);
         if (s != CMF_OK) return s;
         if (ls.cur != 0) CMF_CUDA_TRY(copy_back(ls.cur));  // the graph starts from set 0
         ls.cur = 0;
         if (ls.converged || ls.it >= p->max_iter) return finish_loop(ls, copy_back, h_iters, st);
     }
-    return solve_graph(p, sig, wsbase, w, chunk, certify, copy_back, h_hist, hist_cap,
+    return solve_graph(p, sig, wsbase, w, chunk, end_of, copy_back, h_hist, hist_cap,
                        h_iters, st, ls.it, ls.nh);
 }
 
@@ -956,18 +997,21 @@ cmf_status cmf_solve_binary(const float* d_Cs, const float* d_Ct, const float* d
                                   *p);
     return solve_driver(
         p, sig, c.wsbase, c.w,
-        [&](int n, int& cur, int k0) { return binary_run(c, n, cur, st, k0); },
-        [&](int cur, double* out) {
-            return binary_eval_state(c, bset(c, cur), out, st);
+        [&](int n, int& cur, int k0, double* out) -> cmf_status {
+            const EvalTail T = reduce_tail(c.wsbase, c.w);
+            CMF_CUDA_TRY(cudaMemsetAsync(&T.ctl->arrive, 0, sizeof(unsigned), st));
+            CMF_CUDA_TRY(binary_run(c, n, cur, st, k0, &T));
+            return finish_eval(c.wsbase, c.w, out, st);
         },
         [&](int from) { return copy_binary(c.user, bset(c, from), c.P.g, c.storage, st); },
-        [&](cudaStream_t s, int from, int& to) {  // graph chunks run after the schedule
+        [&](cudaStream_t s, int from, int& to, const EvalTail& T) {  // after the schedule
             to = from;
-            return binary_run(c, p->check_every, to, s, p->rho_schedule_len);
+            return binary_run(c, p->check_every, to, s, p->rho_schedule_len, &T);
         },
-        [&](cudaStream_t s, int set, const EvalTail& T) {
-            return binary_eval(c.storage, c.P, bset(c, set), c.cfg.aniso, c.cfg.dr,
-                               c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s, T);
+        [&](int from) {
+            int to = from;
+            binary_run(c, p->check_every, to, nullptr, p->rho_schedule_len, nullptr, true);
+            return to;
         },
         h_hist, hist_cap, h_iters, st);
 }
@@ -1045,18 +1089,21 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
                                   {d_C, d_alpha, d_u, d_qx, d_qy, d_p, d_ps, d_ws}, *p);
     return solve_driver(
         p, sig, c.wsbase, c.w,
-        [&](int n, int& cur, int k0) { return potts_run(c, n, cur, st, k0); },
-        [&](int cur, double* out) {
-            return potts_eval_state(c, cur == 0 ? c.user : c.ws, out, st);
+        [&](int n, int& cur, int k0, double* out) -> cmf_status {
+            const EvalTail T = reduce_tail(c.wsbase, c.w);
+            CMF_CUDA_TRY(cudaMemsetAsync(&T.ctl->arrive, 0, sizeof(unsigned), st));
+            CMF_CUDA_TRY(potts_run(c, n, cur, st, k0, &T));
+            return finish_eval(c.wsbase, c.w, out, st);
         },
         [&](int) { return copy_potts(c.user, c.ws, c.P.g, L, c.storage, st); },
-        [&](cudaStream_t s, int from, int& to) {  // graph chunks run after the schedule
+        [&](cudaStream_t s, int from, int& to, const EvalTail& T) {  // after the schedule
             to = from;
-            return potts_run(c, p->check_every, to, s, p->rho_schedule_len);
+            return potts_run(c, p->check_every, to, s, p->rho_schedule_len, &T);
         },
-        [&](cudaStream_t s, int set, const EvalTail& T) {
-            return potts_eval(c.storage, c.P, set == 0 ? c.user : c.ws, c.cfg.aniso, c.cfg.dr,
-                              c.cfg.dc.tau, (double*)(c.wsbase + c.w.partials), s, T);
+        [&](int from) {
+            int to = from;
+            potts_run(c, p->check_every, to, nullptr, p->rho_schedule_len, nullptr, true);
+            return to;
         },
         h_hist, hist_cap, h_iters, st);
 }

@@ -322,10 +322,15 @@ cudaError_t binary_strip_step(int storage, const BinProblem& P, const BinStateV&
                               cudaStream_t st);
 // Two ADMM iterations from a into b in one launch (same result as two
 // binary_strip_step launches through an intermediate state;
-// cmf_binary_strip2.cu).
+// cmf_binary_strip2.cu).  cert != nullptr: the launch also writes the
+// certificates of b, one partial triple per block (at most
+// binary_cert_max_blocks() of them) into `partials`, and finishes with
+// eval_tail(*cert).
 cudaError_t binary_strip2_step(int storage, const BinProblem& P, const BinStateV& a,
                                const BinStateV& b, bool aniso, const AdmmCoef& K,
-                               cudaStream_t st);
+                               cudaStream_t st, const EvalTail* cert = nullptr,
+                               double* partials = nullptr);
+int binary_cert_max_blocks();
 // rPDRQ iteration a -> b with the pipelined red-black sweeps.
 cudaError_t binary_dr_strip_step(int storage, const BinProblem& P, const BinStateV& a,
                                  const BinStateV& b, bool aniso, const DrCoef& D,

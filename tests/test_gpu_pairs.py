@@ -156,3 +156,26 @@ def test_pairs_with_schedule_match_oracle(cmf):
     got = b.state()
     for k in ("u", "qx", "qy", "ps", "pt"):
         assert np.abs(got[k] - ref[k]).max() <= TOL_U, k
+
+
+@pytest.mark.parametrize("aniso", [0, 1])
+@pytest.mark.parametrize("shape,algo", [((1024, 1024), 2), ((70, 98), 2), ((130, 6), 1),
+                                        ((5, 130), 4), ((301, 62), 5), ((64, 64), 0)])
+def test_fused_certificates_match_certificate_kernel(cmf, shape, algo, aniso):
+    """A solve's check runs in the chunk's last two-iteration launch; its
+    history row equals what the certificate kernel and the oracle compute
+    for the state the solve returns (one check: max_iter = check_every)."""
+    inst = synth.random_binary(*shape, seed=77, alpha=0.35, field_alpha=True)
+    for use_graph in (1, 0):
+        p = cmf.default_params(algo, 2, aniso=aniso, tol_gap=1e-12, max_iter=20,
+                               check_every=20, use_graph=use_graph)
+        b = cmf.alloc_binary(inst, p)
+        st, it, hist = cmf.cmf_solve_binary(b)
+        assert st == cmf.NOT_CONVERGED and it == 20 and len(hist) == 1
+        E, D, gap, res = hist[0, 1:]
+        Ek, Dk, gapk, resk = cmf.cmf_eval_binary(b)
+        assert abs(E - Ek) <= 1e-7 * abs(Ek) and abs(D - Dk) <= 1e-7 * abs(Dk) + 1e-9
+        assert abs(gap - gapk) <= 1e-7 and abs(res - resk) <= 1e-5 * resk + 1e-7
+        Eo, Do, gapo, reso = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha,
+                                           b.state(), O.default_params(algo, 2, aniso=aniso))
+        assert abs(E - Eo) <= 1e-5 * abs(Eo) and abs(D - Do) <= 1e-5 * abs(Do) + 1e-6
