@@ -178,6 +178,8 @@ KERNEL_CASES = {
     "potts16-admm-2048-f16": ("potts", 2, 2048, 2048, 16, 1, 0),
     "potts16-admm-4096-f16": ("potts", 2, 4096, 4096, 16, 1, 0),
     "potts4-plain-2048": ("potts", 2, 2048, 2048, 4, 0, 1),
+    # a host-driven solve to gap 1e-4 (use_graph = 0), so a profiler sees every launch
+    "binary-solve-host-1024": ("binary-solve", 2, 1024, 1024, 2, 0, 0),
 }
 
 
@@ -354,6 +356,13 @@ def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int =
     __graft_entry__.build()
     model, algo, h, w, nl, storage, impl = KERNEL_CASES[name]
     p = cmf.default_params(algo, nl, storage=storage, impl=impl, variant=variant)
+    if model == "binary-solve":
+        p.use_graph = 0
+        b = cmf.alloc_binary(synth.config2(h, w), p)
+        for _ in range(max(iters, 1)):
+            print(name, cmf.cmf_solve_binary(b)[:2])
+        torch.cuda.synchronize()
+        return
     if model == "binary":
         inst = synth.config2(h, w)
         st = cmf.alloc_binary(inst, p)

@@ -47,7 +47,7 @@ constexpr int kStrip2OutCert = 54;
 constexpr int kCertMaxBlocks = 2048;  // partial triples the workspace holds
 
 template <typename S, bool ANISO, bool CERT>
-__global__ void __launch_bounds__(kStripWarps * 32, CERT ? 3 : 4)
+__global__ void __launch_bounds__(kStripWarps * 32, 4)
     k_binary_strip2(BinProblem P, BinState<S> s0, BinState<S> s1, AdmmCoef K, int R,
                     int nstrips, int nitems, double* partials, EvalTail T) {
     using St = Store<S>;
