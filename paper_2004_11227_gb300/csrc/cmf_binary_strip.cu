@@ -566,9 +566,14 @@ static cudaError_t launch_bin_eval_strip(const BinProblem& P, const BinState<S>&
                                          double* partials, cudaStream_t st,
                                          const EvalTail& T) {
     const Grid& G = P.g;
+    // the grid is eval_blocks(H, W) blocks (the partial count every
+    // certificate path shares); bands sized for the warps actually resident
     const int blocks = eval_blocks(G.H, G.W);
+    static long long resident = 0;
+    if (!resident) resident = strip::resident_warps(k_binary_eval_strip<S, ANISO, DR>);
+    const long long slots = resident > 0 ? resident : (long long)blocks * kStripWarps;
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
-    const int R = strip::choose_rows(G.H, nstrips, (long long)blocks * kStripWarps, 4, 64, 2);
+    const int R = strip::choose_rows(G.H, nstrips, slots, 4, 64, 2);
     const int nitems = nstrips * ((G.H + R - 1) / R);
     k_binary_eval_strip<S, ANISO, DR>
         <<<blocks, kStripWarps * 32, 0, st>>>(P, s, tau, R, nstrips, nitems, partials, T);

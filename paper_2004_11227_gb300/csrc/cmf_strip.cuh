@@ -73,6 +73,20 @@ __device__ __forceinline__ void project_sel(float& x, float& y, float al) {
     }
 }
 
+// Warps of `kern` (blocks of kStripWarps warps, no dynamic shared memory)
+// resident on the whole current device; 0 when the query fails.
+template <typename Kern>
+inline long long resident_warps(Kern kern) {
+    int dev = 0, sms = 0, blocks = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32, 0) !=
+        cudaSuccess)
+        return 0;
+    return (long long)sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+}
+
 // Band height for a grid: the fewest rounds of work items over the resident
 // warps, each round costing its rows plus `halo` rows; ties go to taller bands.
 inline int choose_rows(int H, int nstrips, long long resident, int rmin, int rmax, int halo) {
