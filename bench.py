@@ -46,6 +46,31 @@ def _dist():
     return ws, rank
 
 
+def job_totals(step_ms, iters, world: int, device):
+    """Whole-job figures from one rank's timed steps: the slowest rank's total
+    time (max over ranks) and the units all ranks processed (H*W*L pixel-labels
+    per iteration, summed over ranks).  Replicas: each rank solves its own
+    instance, so the only communication is this reduction of two scalars."""
+    import torch
+
+    total_ms = float(np.sum(step_ms))
+    units = H * W * L * float(np.sum(iters))
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(u)
+        total_ms, units = float(t.item()), float(u.item())
+    return total_ms, units
+
+
+def job_max_ms(step_ms, world: int, device) -> float:
+    """The slowest rank's total of step_ms (max over ranks)."""
+    return job_totals(step_ms, [0], world, device)[0]
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -469,16 +494,7 @@ def main():
     barrier()
     clocks = sampler.stop()
 
-    total_ms = float(np.sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        it_t = torch.tensor([float(np.sum(iters_all))], device=dev)
-        dist.all_reduce(it_t)
-        total_units = H * W * L * float(it_t.item())
-    else:
-        total_units = H * W * L * float(np.sum(iters_all))
+    total_ms, total_units = job_totals(times, iters_all, world, dev)
     value = total_units / (total_ms / 1000.0)
     iters = int(np.median(iters_all))
     n_checks = int(np.ceil(iters / CHECK_EVERY))
@@ -515,11 +531,7 @@ def main():
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
     barrier()
-    e2e_ms = float(np.sum(e2e_times))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = job_max_ms(e2e_times, world, dev)
     e2e_value = total_units / (e2e_ms / 1000.0)
     h2d = 3 * H * b.pitch * 4
     d2h = H * b.pitch * 4
