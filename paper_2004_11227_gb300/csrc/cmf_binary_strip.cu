@@ -425,9 +425,9 @@ cudaError_t binary_dr_strip_step(int storage, const BinProblem& P, const BinStat
 // the primal energy at clip(u, 0, 1), the conservation residual of the flows
 // y (q for ADMM; q - tau grad u, p_t + tau u, p_s - tau u for rPDRQ) and the
 // max-flow value min(C_s, C_t + div P_alpha(y)).  Each row's pair is added to
-// per-lane FP64 sums; the block's sums go to partials[blockIdx.x].  The grid
-// has exactly eval_blocks(H, W) blocks so the partial count is the tile
-// kernel's.
+// per-lane double-float sums (FP64 from the warp sums on); the block's sums go
+// to partials[blockIdx.x].  The grid has exactly eval_blocks(H, W) blocks so
+// the partial count is the tile kernel's; eval_tail may reduce them.
 namespace cmf {
 
 template <typename S, bool ANISO, bool DR>

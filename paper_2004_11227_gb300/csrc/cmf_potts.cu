@@ -450,28 +450,29 @@ __global__ void k_potts_plain_dr_ps(PottsProblem P, PottsState<S> s, DrCoef D) {
 // ---------------------------------------------------------------------------
 // Certificates.  ub(x) = projection of u(x) onto the simplex:
 // ub_i = max(u_i - theta, 0), theta from Michelot's active-set iteration
-// (remove entries <= theta, recompute theta = (sum_active - 1)/n_active).
+// (drop entries <= theta, recompute theta = (sum_active - 1)/n_active).  The
+// thresholds never decrease, so a dropped entry stays dropped and the active
+// set of a pass is {i : u_i > theta}: each pass sums and counts it afresh (no
+// set bookkeeping) and the iteration stops when the count no longer changes.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float simplex_theta(const float* u, size_t pl, int L, size_t k) {
-    unsigned long long active = L >= 64 ? ~0ull : ((1ull << L) - 1ull);
     float sum = 0.f;
-    int n = L;
     for (int i = 0; i < L; ++i) sum += u[i * pl + k];
+    int n = L;
     float theta = (sum - 1.f) / (float)n;
     for (int it = 0; it < L; ++it) {
-        bool changed = false;
+        float s = 0.f;
+        int m = 0;
         for (int i = 0; i < L; ++i) {
-            if (!((active >> i) & 1ull)) continue;
             const float v = u[i * pl + k];
-            if (v <= theta) {
-                active &= ~(1ull << i);
-                sum -= v;
-                --n;
-                changed = true;
+            if (v > theta) {
+                s += v;
+                ++m;
             }
         }
-        if (!changed || n == 0) break;
-        theta = (sum - 1.f) / (float)n;
+        if (m == n || m == 0) break;
+        n = m;
+        theta = (s - 1.f) / (float)n;
     }
     return theta;
 }

@@ -600,8 +600,9 @@ cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const Potts
 // walks the labels, streaming each label down the band: the primal energy at
 // max(u_i - theta, 0), the conservation residual of the flows y and the
 // running minimum over labels of C_i + div P_alpha(y_i) (shared memory).  Sums
-// are FP64 per lane, then per block into partials[blockIdx.x]; the grid has
-// eval_blocks(H, W) blocks, the tile kernel's partial count.
+// are double-float per lane and per warp, FP64 per block into
+// partials[blockIdx.x]; the grid has eval_blocks(H, W) blocks, the tile
+// kernel's partial count.
 namespace {
 constexpr int kEvalRmax = 15;  // 4 warps x (16 + 15 + 15) rows x 256 B = 46 KB static
 }  // namespace
@@ -656,35 +657,35 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                     sy += v.y;
                 }
                 us = make_float2(sx, sy);
-                // Michelot: drop entries <= theta, theta = (sum_active - 1) / n
-                unsigned long long ax = L >= 64 ? ~0ull : ((1ull << L) - 1ull), ay = ax;
+                // Michelot: theta = (sum_active - 1) / n_active, active = the
+                // entries above theta (the thresholds never decrease, so each
+                // pass sums and counts that set afresh); stop when the counts
+                // no longer change
                 int nx = L, ny = L;
                 float tx = (sx - 1.f) / (float)nx, ty = (sy - 1.f) / (float)ny;
-                bool run_x = true, run_y = true;
-                for (int it = 0; it < L && (run_x || run_y); ++it) {
-                    bool chx = false, chy = false;
+                for (int it = 0; it < L; ++it) {
+                    float ax = 0.f, ay = 0.f;
+                    int mx = 0, my = 0;
                     for (int l = 0; l < L; ++l) {
                         const float2 v = PF::ld(ub + (size_t)l * G.plane);
-                        if (run_x && ((ax >> l) & 1ull) && v.x <= tx) {
-                            ax &= ~(1ull << l);
-                            sx -= v.x;
-                            --nx;
-                            chx = true;
+                        if (v.x > tx) {
+                            ax += v.x;
+                            ++mx;
                         }
-                        if (run_y && ((ay >> l) & 1ull) && v.y <= ty) {
-                            ay &= ~(1ull << l);
-                            sy -= v.y;
-                            --ny;
-                            chy = true;
+                        if (v.y > ty) {
+                            ay += v.y;
+                            ++my;
                         }
                     }
-                    if (run_x) {
-                        if (!chx || nx == 0) run_x = false;
-                        else tx = (sx - 1.f) / (float)nx;
+                    const bool cx = mx != nx && mx > 0, cy = my != ny && my > 0;
+                    if (!cx && !cy) break;
+                    if (cx) {
+                        nx = mx;
+                        tx = (ax - 1.f) / (float)nx;
                     }
-                    if (run_y) {
-                        if (!chy || ny == 0) run_y = false;
-                        else ty = (sy - 1.f) / (float)ny;
+                    if (cy) {
+                        ny = my;
+                        ty = (ay - 1.f) / (float)ny;
                     }
                 }
                 th = make_float2(tx, ty);
