@@ -163,3 +163,16 @@ def test_product_path_does_not_touch_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower() or f == "synth.py", f
+
+
+def test_rho_schedule_binding_keeps_its_array(cmf):
+    import gc
+
+    p = cmf.default_params(cmf.RPADMM_EB, 2, rho_schedule=[0.5, 1.0, 1.5])
+    gc.collect()  # the list is gone; the params object holds its own copy
+    assert p.rho_schedule_len == 3
+    assert [p.rho_schedule[i] for i in range(3)] == [0.5, 1.0, 1.5]
+    p.set_rho_schedule([])
+    assert p.rho_schedule_len == 0 and not p.rho_schedule
+    q = cmf.default_params(cmf.RPDRQ, 4)
+    assert q.rho_schedule_len == 0 and not q.rho_schedule
