@@ -78,6 +78,7 @@ def lib():
         L.orc_project_alpha.argtypes = [ctypes.c_size_t, dp, dp, dp, i]
         L.orc_srbgs.argtypes = [i, i, ctypes.c_double, ctypes.c_double, dp, dp, i]
         L.orc_simplex.argtypes = [i, dp, dp]
+        L.orc_simplex.restype = i
         L.orc_binary_init.argtypes = [i, i, dp, dp, i, ctypes.c_double, dp, dp, dp, dp, dp]
         L.orc_binary_run.argtypes = [i, i, dp, dp, dp, ctypes.POINTER(Params), i, i,
                                      dp, dp, dp, dp, dp]
@@ -90,6 +91,7 @@ def lib():
         L.orc_potts_run.restype = i
         L.orc_potts_eval.argtypes = [i, i, i, dp, dp, i, i, ctypes.c_double,
                                      dp, dp, dp, dp, dp, dp]
+        L.orc_potts_eval.restype = i
     return _lib
 
 
@@ -143,7 +145,8 @@ def srbgs(b, u, kappa: float, st: float, sweeps: int = 1):
 def simplex(v):
     v = _f64(v)
     w = np.empty_like(v)
-    lib().orc_simplex(v.size, _ptr(v), _ptr(w))
+    if lib().orc_simplex(v.size, _ptr(v), _ptr(w)) != 0:
+        raise ValueError("oracle: the simplex projection takes 1 to 64 entries")
     return w
 
 
@@ -231,8 +234,11 @@ def potts_eval(C, alpha, state, params: Params):
     al = _alpha_field(alpha, H, W)
     out = np.zeros(4)
     arrs = [_f64(state[k]) for k in ("u", "qx", "qy", "p", "ps")]
-    lib().orc_potts_eval(H, W, L, _ptr(C), _ptr(al), params.aniso, int(params.algo == RPDRQ),
-                         params.tau, *[_ptr(a) for a in arrs], _ptr(out))
+    rc = lib().orc_potts_eval(H, W, L, _ptr(C), _ptr(al), params.aniso,
+                              int(params.algo == RPDRQ), params.tau, *[_ptr(a) for a in arrs],
+                              _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle: Potts certificates take 2 to 64 labels")
     return tuple(float(x) for x in out)
 
 

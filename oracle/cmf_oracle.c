@@ -162,7 +162,8 @@ static int cmp_desc(const void *a, const void *b) {
     double x = *(const double *)a, y = *(const double *)b;
     return (x < y) - (x > y);
 }
-void orc_simplex(int n, const double *v, double *w) {
+int orc_simplex(int n, const double *v, double *w) {
+    if (n < 1 || n > 64) return -1; /* the sort buffer holds 64 entries */
     double s[64];
     memcpy(s, v, (size_t)n * sizeof(double));
     qsort(s, (size_t)n, sizeof(double), cmp_desc);
@@ -173,6 +174,7 @@ void orc_simplex(int n, const double *v, double *w) {
         if (s[k] - t > 0.0) theta = t;
     }
     for (int k = 0; k < n; ++k) w[k] = v[k] - theta > 0.0 ? v[k] - theta : 0.0;
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -687,9 +689,10 @@ int orc_potts_run(int H, int W, int L, const double *C, const double *alpha, con
  * For rPDRQ the flows are y = ybar + tau K u: q_i = qbar_i - tau grad u_i,
  * p_i = pbar_i + tau u_i, p_s = pbar_s - tau sum_i u_i; the dual uses
  * P_alpha(q_i). */
-void orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, int aniso, int dr,
-                    double tau, const double *u, const double *qx, const double *qy,
-                    const double *p, const double *ps, double *out) {
+int orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, int aniso, int dr,
+                   double tau, const double *u, const double *qx, const double *qy,
+                   const double *p, const double *ps, double *out) {
+    if (L < 2 || L > 64) return -1; /* per-pixel label buffers hold 64 entries */
     const size_t n = (size_t)H * W;
     double *ub = dalloc(n * L), *gx = dalloc(n), *gy = dalloc(n), *fx = dalloc(n * L),
            *fy = dalloc(n * L), *fp = dalloc(n * L), *fs = dalloc(n), *d = dalloc(n),
@@ -748,4 +751,5 @@ void orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, i
     out[2] = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
     out[3] = sqrt(res);
     free(ub); free(gx); free(gy); free(fx); free(fy); free(fp); free(fs); free(d); free(mn);
+    return 0;
 }

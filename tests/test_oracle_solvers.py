@@ -391,3 +391,86 @@ def test_alg1_default_steps_satisfy_cp_condition(orc, L):
     p = orc.default_params(5, L)
     lam = np.linalg.eigvalsh(KK).max()
     assert p.sigma * p.tau * lam < 1.0, (p.sigma, p.tau, lam)
+
+
+# --- Potts cold start ---------------------------------------------------------
+
+def _np_grad(g):
+    """Forward differences with a zero far boundary (unit spacing), written
+    out here independently of the oracle's operator."""
+    gx = np.zeros_like(g)
+    gy = np.zeros_like(g)
+    gx[:, :-1] = g[:, 1:] - g[:, :-1]
+    gy[:-1, :] = g[1:, :] - g[:-1, :]
+    return gx, gy
+
+
+def _tied_potts_costs(L, H, W, seed):
+    """Costs on a coarse grid of values, so many pixels have exact ties for
+    the cheapest label."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(0, 3, size=(L, H, W)) / 4.0).astype(np.float32)
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_potts_cold_start_is_alpha_zero_saddle_point(orc, algo):
+    """The cold start is the alpha = 0 saddle point: u_i = 1 for the FIRST
+    cheapest label (ties included), q_i = 0, p_i = p_s = min_j C_j; rPDRQ
+    stores ybar = y - tau K u of that point (Eq. pdrq:4labels: y is recovered
+    as q_i = qbar_i - tau grad u_i, p_i = pbar_i + tau u_i,
+    p_s = pbar_s - tau sum_i u_i).  With alpha = 0 every algorithm must leave
+    it unchanged."""
+    L, H, W = 5, 6, 7
+    C = _tied_potts_costs(L, H, W, seed=31)
+    first = np.argmin(C, axis=0)  # numpy returns the first minimiser
+    assert (np.sort(C, axis=0)[0] == np.sort(C, axis=0)[1]).sum() > 5  # ties present
+    m = C.astype(np.float64).min(axis=0)
+    p = orc.default_params(algo, L)
+    st0 = orc.potts_run(C, 0.0, p, 0)
+    u_exp = (np.arange(L)[:, None, None] == first[None]).astype(np.float64)
+    np.testing.assert_array_equal(st0["u"], u_exp)
+    qx, qy, pp, ps = (st0[k].copy() for k in ("qx", "qy", "p", "ps"))
+    if algo == 3:
+        for i in range(L):
+            gx, gy = _np_grad(u_exp[i])
+            qx[i] -= p.tau * gx
+            qy[i] -= p.tau * gy
+            pp[i] += p.tau * u_exp[i]
+        ps -= p.tau * u_exp.sum(axis=0)
+    np.testing.assert_allclose(qx, 0.0, atol=1e-15)
+    np.testing.assert_allclose(qy, 0.0, atol=1e-15)
+    np.testing.assert_allclose(pp, np.broadcast_to(m, pp.shape), atol=1e-15)
+    np.testing.assert_allclose(ps, m, atol=1e-15)
+    st = orc.potts_run(C, 0.0, p, 4, st0)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        np.testing.assert_allclose(st[k], st0[k], atol=1e-12, err_msg=k)
+    E, D, gap, res = orc.potts_eval(C, 0.0, st, p)
+    assert abs(E - m.sum()) < 1e-12 and abs(D - m.sum()) < 1e-12 and res < 1e-12
+
+
+def test_potts_conservation_residual_vanishes(orc):
+    """Flow conservation div q_i - p_s + p_i = 0 for every label holds at the
+    limit (Eq. potts-mf)."""
+    inst = synth.config3(16, 14)
+    for algo in (2, 3):
+        p = orc.default_params(algo, 4)
+        st = orc.potts_run(inst.costs, inst.alpha, p, 200)
+        res0 = orc.potts_eval(inst.costs, inst.alpha, st, p)[3]
+        st = orc.potts_run(inst.costs, inst.alpha, p, 20000, st)
+        E, D, gap, res = orc.potts_eval(inst.costs, inst.alpha, st, p)
+        assert res < res0 / 1000 and res < 1e-7 and gap < 1e-8, (algo, res0, res, gap)
+
+
+def test_potts_label_count_guard(orc):
+    """The oracle's per-pixel label buffers hold 64 entries; more labels are
+    refused instead of overrunning them."""
+    C = np.zeros((65, 2, 2), dtype=np.float32)
+    st = {k: np.zeros((65, 2, 2)) for k in ("u", "qx", "qy", "p")}
+    st["ps"] = np.zeros((2, 2))
+    with pytest.raises(ValueError):
+        orc.potts_eval(C, 0.1, st, orc.default_params(2, 65))
+    with pytest.raises(ValueError):
+        orc.potts_run(C, 0.1, orc.default_params(2, 65), 1)
+    with pytest.raises(ValueError):
+        orc.simplex(np.zeros(65))
+    np.testing.assert_allclose(orc.simplex(np.zeros(64)), np.full(64, 1.0 / 64))
