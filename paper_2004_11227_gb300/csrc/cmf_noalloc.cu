@@ -2,13 +2,14 @@
 // caller-provided workspace.
 //
 // Some callers cannot allocate device memory at the point where they want a
-// certificate: code running while a CUDA stream is being captured in global
-// mode (where cudaMalloc is prohibited), plug-ins that receive only a stream
-// and the solver's buffers from a host application that owns every
-// allocation, and real-time loops whose memory budget is fixed up front.  This
-// entry point keeps its scratch (the per-block partial sums and the reduced
-// scalars) in a file-scope __device__ array instead.  The array exists on
-// every GPU that loads the library, for as long as the library stays loaded.
+// certificate: plug-ins that receive only a stream and the solver's buffers
+// from a host application that owns every allocation, and real-time loops
+// whose memory budget is fixed up front.  This entry point keeps its scratch
+// (the per-block partial sums and the reduced scalars) in a file-scope
+// __device__ array instead.  The array exists on every GPU that loads the
+// library, for as long as the library stays loaded.  The call synchronises
+// its stream and copies the result to the host, so it refuses to run on a
+// stream that is being captured into a CUDA graph.
 #include <math.h>
 
 #include "cmf_kernels.cuh"
@@ -23,24 +24,16 @@ constexpr int kScratchDoubles = 3 * kMaxBlocks + 4;
 
 static __device__ __align__(256) double g_eval_scratch[kScratchDoubles];
 
-// Device address of g_eval_scratch, looked up once per device.  In host code
-// the name g_eval_scratch is only a host-side stand-in; kernels must be given
-// the address cudaGetSymbolAddress returns.
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-
+// Device address of g_eval_scratch on the current device.  In host code the
+// name g_eval_scratch is only a host-side stand-in; kernels must be given the
+// address cudaGetSymbolAddress returns.  It is looked up on every call (after
+// the capture check, so never during a capture): a table cached across calls
+// would keep a dead address after cudaDeviceReset reloads the module.
 cudaError_t scratch_for_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_eval_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_eval_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = (double*)p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = (double*)p;
     return cudaSuccess;
 }
 
@@ -56,18 +49,25 @@ extern "C" cmf_status cmf_eval_binary_noalloc(const float* d_Cs, const float* d_
     if (!p || !h_out || !d_Cs || !d_Ct || !d_u || !d_qx || !d_qy || !d_ps || !d_pt)
         return CMF_EINVAL;
     if (H < 1 || W < 1 || pitch < W) return CMF_EINVAL;
-    if (p->algo < CMF_PADMM || p->algo > CMF_RPDRQ) return CMF_EINVAL;
+    if (p->algo < CMF_PADMM || p->algo > CMF_CP) return CMF_EINVAL;
     if (p->storage < CMF_F32 || p->storage > CMF_BF16) return CMF_EINVAL;
     if (!(p->tau > 0)) return CMF_EINVAL;
     if (!d_alpha && !(alpha0 >= 0.0f && isfinite(alpha0))) return CMF_EINVAL;
     const int nblocks = eval_blocks(H, W);
     if (nblocks > kMaxBlocks) return CMF_EINVAL;  // grid larger than the static scratch
 
+    cudaStream_t st = (cudaStream_t)stream;
+    // the call ends with a device-to-host copy and a stream synchronisation,
+    // neither of which a stream capture allows: refuse before any launch
+    // (the query itself is allowed during a capture and leaves it valid)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return CMF_EINVAL;
+
     double* scratch = nullptr;
     CMF_CUDA_TRY(scratch_for_current_device(&scratch));
     double* partials = scratch;
     double* scal = scratch + 3 * kMaxBlocks;
-    cudaStream_t st = (cudaStream_t)stream;
 
     BinProblem P{d_Cs, d_Ct, Alpha{d_alpha, alpha0},
                  Grid{H, W, pitch, (size_t)H * (size_t)pitch}};
