@@ -319,18 +319,11 @@ template <typename S, bool ANISO>
 static cudaError_t launch_bin_strip(const BinProblem& P, const BinState<S>& a,
                                     const BinState<S>& b, const AdmmCoef& K, cudaStream_t st) {
     auto kern = k_binary_strip<S, ANISO>;
-    static int resident = 0;  // warps resident on the whole device
-    if (!resident) {
-        int dev = 0, sms = 0, blocks = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
-                                                                0)) != cudaSuccess)
-            return e;
-        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    long long resident = 0;
+    {
+        const cudaError_t e = strip::device_resident_warps(memo, kern, 0, resident);
+        if (e != cudaSuccess) return e;
     }
     const Grid& G = P.g;
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
@@ -364,18 +357,11 @@ template <typename S, bool ANISO, int SW>
 static cudaError_t launch_bin_dr_strip(const BinProblem& P, const BinState<S>& a,
                                        const BinState<S>& b, const DrCoef& D, cudaStream_t st) {
     auto kern = k_binary_dr_strip<S, ANISO, SW>;
-    static int resident = 0;  // warps resident on the whole device
-    if (!resident) {
-        int dev = 0, sms = 0, blocks = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
-                                                                0)) != cudaSuccess)
-            return e;
-        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    long long resident = 0;
+    {
+        const cudaError_t e = strip::device_resident_warps(memo, kern, 0, resident);
+        if (e != cudaSuccess) return e;
     }
     const Grid& G = P.g;
     constexpr int OUT = 2 * (32 - 2 * (SW + 1));
@@ -569,8 +555,8 @@ static cudaError_t launch_bin_eval_strip(const BinProblem& P, const BinState<S>&
     // the grid is eval_blocks(H, W) blocks (the partial count every
     // certificate path shares); bands sized for the warps actually resident
     const int blocks = eval_blocks(G.H, G.W);
-    static long long resident = 0;
-    if (!resident) resident = strip::resident_warps(k_binary_eval_strip<S, ANISO, DR>);
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    const long long resident = strip::resident_warps(memo, k_binary_eval_strip<S, ANISO, DR>);
     const long long slots = resident > 0 ? resident : (long long)blocks * kStripWarps;
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
     const int R = strip::choose_rows(G.H, nstrips, slots, 4, 64, 2);

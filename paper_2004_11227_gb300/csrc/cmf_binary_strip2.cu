@@ -262,18 +262,11 @@ static cudaError_t launch_bin_strip2(const BinProblem& P, const BinState<S>& a,
                                      const BinState<S>& b, const AdmmCoef& K, double* partials,
                                      const EvalTail& T, cudaStream_t st) {
     auto kern = k_binary_strip2<S, ANISO, CERT>;
-    static int resident = 0;  // warps resident on the whole device
-    if (!resident) {
-        int dev = 0, sms = 0, blocks = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
-                                                                0)) != cudaSuccess)
-            return e;
-        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    long long resident = 0;
+    {
+        const cudaError_t e = strip::device_resident_warps(memo, kern, 0, resident);
+        if (e != cudaSuccess) return e;
     }
     const Grid& G = P.g;
     constexpr int OUT = CERT ? kStrip2OutCert : kStrip2Out;

@@ -239,24 +239,31 @@ static cudaError_t launch_bin_tma(const BinProblem& P, const BinState<S>& b, con
                                   const BinTmaMaps& m, int* err, cudaStream_t st) {
     using Lay = BinTmaLayout<S, TY>;
     auto kern = k_binary_admm_tma<S, ANISO, TY>;  // static smem: (NG + 2 NQ) x 256 floats
-    static int blocks_per_sm = 0;
-    static int sms = 0;
-    if (!blocks_per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Lay::DYN);
+    static std::atomic<long long> memo[kMaxDevices];  // resident blocks per device
+    long long resident = 0;
+    {
+        const cudaError_t e = per_device(
+            memo,
+            [&](int dev, long long& v) -> cudaError_t {
+                cudaError_t e2 = cudaFuncSetAttribute(
+                    kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::DYN);
+                if (e2 != cudaSuccess) return e2;
+                int sms = 0, blocks_per_sm = 0;
+                if ((e2 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+                    cudaSuccess)
+                    return e2;
+                if ((e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 256,
+                                                                         Lay::DYN)) !=
+                    cudaSuccess)
+                    return e2;
+                v = (long long)sms * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+                return cudaSuccess;
+            },
+            resident);
         if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 256,
-                                                                Lay::DYN)) != cudaSuccess)
-            return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     const int ntiles = ((P.g.W + 31) / 32) * ((P.g.H + TY - 1) / TY);
-    int grid = sms * blocks_per_sm;
+    int grid = (int)resident;
     if (grid > ntiles) grid = ntiles;
     kern<<<grid, dim3(32, 8), Lay::DYN, st>>>(P, b, K, m.qx, m.qy, m.ps, m.pt, m.u, err);
     return cudaGetLastError();

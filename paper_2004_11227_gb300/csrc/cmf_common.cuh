@@ -8,6 +8,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/cmf.h"
 
 namespace cmf {
@@ -45,6 +48,58 @@ template <> struct Store<__nv_bfloat16> {
 };
 
 inline size_t dtype_size(int storage) { return storage == CMF_F32 ? 4 : 2; }
+
+// ---- per-device memo of launch-configuration queries ----------------------
+// Function attributes (a raised shared-memory limit) and occupancy belong to
+// a device, so a launcher that caches them keeps one entry per device
+// ordinal.  compute(dev, v) runs with that device current and fills v (> 0);
+// entries are atomics, so concurrent host threads at worst compute one twice.
+constexpr int kMaxDevices = 64;
+template <typename F>
+inline cudaError_t per_device(std::atomic<long long> (&memo)[kMaxDevices], F compute,
+                              long long& out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool slot = dev >= 0 && dev < kMaxDevices;
+    if (slot) {
+        const long long v = memo[dev].load(std::memory_order_acquire);
+        if (v > 0) {
+            out = v;
+            return cudaSuccess;
+        }
+    }
+    long long v = 0;
+    if ((e = compute(dev, v)) != cudaSuccess) return e;
+    if (slot && v > 0) memo[dev].store(v, std::memory_order_release);
+    out = v;
+    return cudaSuccess;
+}
+
+// Raise `kern`'s dynamic shared-memory limit on the current device to at
+// least dyn bytes.  memo (the caller's per-kernel table) holds the limit set
+// on each device; one lock orders the raises, so a smaller request never
+// lowers a limit a concurrent call has just raised.
+inline std::mutex& attr_mutex() {
+    static std::mutex m;
+    return m;
+}
+template <typename Kern>
+inline cudaError_t raise_dyn_smem(std::atomic<long long> (&memo)[kMaxDevices], Kern kern,
+                                  size_t dyn) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool slot = dev >= 0 && dev < kMaxDevices;
+    if (slot && memo[dev].load(std::memory_order_acquire) >= (long long)dyn) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(attr_mutex());
+    if (slot && memo[dev].load(std::memory_order_acquire) >= (long long)dyn) return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn)) !=
+        cudaSuccess)
+        return e;
+    if (slot) memo[dev].store((long long)dyn, std::memory_order_release);
+    return cudaSuccess;
+}
 
 // ---- pointwise projections (Eq. projections) -----------------------------
 
@@ -172,13 +227,14 @@ __device__ __forceinline__ float potts_label_pu(const AdmmCoef& K, float g, floa
     return p1;
 }
 
-// p_s^{k+1} from the accumulated label terms (rounded to the storage type).
-template <typename S>
+// p_s^{k+1} from the accumulated label terms.  The Potts p_s plane is stored
+// as float32 whatever the flow storage: one plane per pixel (4 bytes more per
+// pixel and iteration than 16-bit), and its rounding to 16 bits alone holds
+// the certified gap of the 16-label workload near 4e-4.
 __device__ __forceinline__ float potts_ps_update(const AdmmCoef& K, float ps0, float acc_a,
                                                  float acc_b) {
-    if (K.cp) return Store<S>::rt(ps0 - K.sigma * (acc_a + acc_b) + K.sigma);
-    return K.ty ? Store<S>::rt((acc_a + K.inv_c) * K.inv_L)
-                : Store<S>::rt(ps0 + (acc_a + acc_b + K.inv_c) * K.inv_a2);
+    if (K.cp) return ps0 - K.sigma * (acc_a + acc_b) + K.sigma;
+    return K.ty ? (acc_a + K.inv_c) * K.inv_L : ps0 + (acc_a + acc_b + K.inv_c) * K.inv_a2;
 }
 
 // ---- DR coefficients -----------------------------------------------------

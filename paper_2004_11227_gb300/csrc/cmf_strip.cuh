@@ -20,6 +20,13 @@ struct Pair<float> {
     static __device__ __forceinline__ T ld(const float* p) {
         return __ldg(reinterpret_cast<const float2*>(p));
     }
+    // read once in this launch: evict-first in L1 and L2 (ld.global.cs)
+    static __device__ __forceinline__ T ldcs(const float* p) {
+        return __ldcs(reinterpret_cast<const float2*>(p));
+    }
+    static __device__ __forceinline__ void stcs(float* p, float a, float b) {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(a, b));
+    }
     static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
     static __device__ __forceinline__ float2 f2(T v) { return v; }
     static __device__ __forceinline__ void st(float* p, float a, float b) {
@@ -34,6 +41,12 @@ struct Pair<__half> {
     static __device__ __forceinline__ T ld(const __half* p) {
         return __ldg(reinterpret_cast<const __half2*>(p));
     }
+    static __device__ __forceinline__ T ldcs(const __half* p) {
+        return __ldcs(reinterpret_cast<const __half2*>(p));
+    }
+    static __device__ __forceinline__ void stcs(__half* p, float a, float b) {
+        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(a, b));
+    }
     static __device__ __forceinline__ T zero() { return __float2half2_rn(0.f); }
     static __device__ __forceinline__ float2 f2(T v) { return __half22float2(v); }
     static __device__ __forceinline__ void st(__half* p, float a, float b) {
@@ -46,6 +59,12 @@ struct Pair<__nv_bfloat16> {
     using T = __nv_bfloat162;
     static __device__ __forceinline__ T ld(const __nv_bfloat16* p) {
         return __ldg(reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    static __device__ __forceinline__ T ldcs(const __nv_bfloat16* p) {
+        return __ldcs(reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    static __device__ __forceinline__ void stcs(__nv_bfloat16* p, float a, float b) {
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a, b));
     }
     static __device__ __forceinline__ T zero() { return __float2bfloat162_rn(0.f); }
     static __device__ __forceinline__ float2 f2(T v) { return __bfloat1622float2(v); }
@@ -73,18 +92,40 @@ __device__ __forceinline__ void project_sel(float& x, float& y, float al) {
     }
 }
 
-// Warps of `kern` (blocks of kStripWarps warps, no dynamic shared memory)
-// resident on the whole current device; 0 when the query fails.
+// Warps of `kern` resident on the whole current device, for blocks of
+// kStripWarps warps with `dyn` bytes of dynamic shared memory (with dyn > 0
+// the kernel's dynamic shared-memory limit is raised to dyn first).  `memo`
+// is the caller's per-kernel table: the queries run once per device.
 template <typename Kern>
-inline long long resident_warps(Kern kern) {
-    int dev = 0, sms = 0, blocks = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32, 0) !=
-        cudaSuccess)
-        return 0;
-    return (long long)sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+inline cudaError_t device_resident_warps(std::atomic<long long> (&memo)[kMaxDevices], Kern kern,
+                                         size_t dyn, long long& out) {
+    return per_device(
+        memo,
+        [&](int dev, long long& v) -> cudaError_t {
+            cudaError_t e;
+            if (dyn && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)dyn)) != cudaSuccess)
+                return e;
+            int sms = 0, blocks = 0;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+                cudaSuccess)
+                return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern,
+                                                                    kStripWarps * 32, dyn)) !=
+                cudaSuccess)
+                return e;
+            v = (long long)sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+            return cudaSuccess;
+        },
+        out);
+}
+
+// As device_resident_warps without dynamic shared memory; 0 when a query
+// fails (the certificate launchers then size bands for their own grid).
+template <typename Kern>
+inline long long resident_warps(std::atomic<long long> (&memo)[kMaxDevices], Kern kern) {
+    long long v = 0;
+    return device_resident_warps(memo, kern, 0, v) == cudaSuccess ? v : 0;
 }
 
 // Band height for a grid: the fewest rounds of work items over the resident
