@@ -45,8 +45,11 @@
  *    cmf_solve_* report it as CMF_ETIMEOUT; after cmf_iterate_* (which does
  *    not synchronise) the next cmf_eval_* on the same workspace reports it.
  *    cmf_iterate_* and cmf_solve_* clear the record when they start.
- *  - State storage: u is always float32.  Flows (q, p_s, p_t / p_i) are
- *    stored as cmf_params.storage (float32, float16 or bfloat16); all
+ *  - State storage: u is always float32.  Flows (binary q, p_s, p_t; Potts
+ *    q_i, p_i) are stored as cmf_params.storage (float32, float16 or
+ *    bfloat16); the Potts source flow p_s, one plane shared by all labels, is
+ *    always float32 (4 bytes per pixel more than 16 bits; rounded to 16 bits
+ *    it alone holds the certified gap of a 16-label problem near 4e-4); all
  *    arithmetic is float32; the certificates (energies, gap, residual) sum
  *    float32 per-pixel terms in double-float (two floats kept exact by
  *    two-sum, about 44 significant bits) within a warp and in float64 above
@@ -139,11 +142,14 @@ typedef struct {
     double sigma;      /* rPDRQ step sizes                                     */
     double tau;
     double tol_gap;    /* cmf_solve_*: stop when the relative gap <= tol_gap   */
-    int costs;         /* Potts cost input: 0 = L cost planes [L][H][pitch] at
-                          d_C; 1 = computed where read (no counterpart in the
-                          paper's statement, which takes the costs as given):
-                          d_C holds one image plane I [H][pitch] followed by the
-                          L levels c_i (floats), and C_i(x) = (I(x) - c_i)^2.
+    int costs;         /* Potts cost input: 0 = L float32 cost planes
+                          [L][H][pitch] at d_C; 1 = computed where read (no
+                          counterpart in the paper's statement, which takes the
+                          costs as given): d_C holds one image plane I
+                          [H][pitch] followed by the L levels c_i (floats), and
+                          C_i(x) = (I(x) - c_i)^2; 2 = L float16 cost planes
+                          [L][H][pitch] at d_C (the given costs rounded to
+                          float16; every use converts them to float32).
                           Binary calls and batches need 0.                    */
     const double *rho_schedule; /* relaxation sequence {rho_k} of rpADMMII and
                           rPDRQ (Thm 1 and Thm 2 assume a non-decreasing
@@ -178,6 +184,12 @@ const char *cmf_status_str(cmf_status s);
  * size it with the parameters the calls will use (a call whose parameters
  * need more returns CMF_ENOMEM before launching anything). */
 size_t cmf_workspace_bytes(int H, int W, int L, int pitch, const cmf_params *p);
+/* Device memory outside the workspace: the device-driven loop of cmf_solve_*
+ * (use_graph = 1) keeps the instantiated CUDA graphs of the 8 most recently
+ * used call signatures (see cmf_release_graphs).  Their memory is the
+ * driver's (graph nodes and kernel parameters, a few KB to tens of KB per
+ * graph); it is not part of cmf_workspace_bytes and is returned by
+ * cmf_release_graphs. */
 
 /* ------------------------------------------------------------------------ */
 /* Binary model.  Planes: d_Cs, d_Ct (float32, read only); d_alpha (float32  */
@@ -212,19 +224,21 @@ cmf_status cmf_eval_binary(const float *d_Cs, const float *d_Ct, const float *d_
                            const void *d_ps, const void *d_pt, double *h_out, void *d_ws,
                            size_t ws_bytes, void *stream);
 
-/* Certificates of a binary state exactly as cmf_eval_binary computes them,
- * for callers that cannot allocate device memory when they need them (code
- * running while a stream is captured in global mode, where cudaMalloc is
- * prohibited; plug-ins that only receive a stream and the solver's buffers;
+/* Certificates of a binary state exactly as cmf_eval_binary computes them
+ * (every algorithm, every storage type), for callers that cannot allocate
+ * device memory when they need them (plug-ins that only receive a stream and
+ * the solver's buffers from a host application that owns every allocation;
  * loops with a memory budget fixed up front).  It takes no workspace and
  * allocates nothing: its scratch is a static device array inside libcmf of
  * 393,248 bytes (per-block partial sums for up to 16384 blocks of 32 x 32
  * pixels, i.e. grids up to 4096 x 4096 pixels, plus the reduced scalars),
  * present on every GPU that loads the library until the process exits.
  *  - Larger grids (more than 16384 blocks of 32 x 32) return CMF_EINVAL.
- *  - The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress for the current device; make that first call
- *    before any stream capture.
+ *  - Every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress), so calls after cudaDeviceReset stay valid.
+ *  - The call cannot be captured into a CUDA graph: it synchronises `stream`
+ *    and copies to the host.  On a stream that is being captured it returns
+ *    CMF_EINVAL before launching anything, and the capture stays valid.
  *  - All calls share the array: calls whose GPU work overlaps (different
  *    streams, or different host threads on one device) race and give wrong
  *    results.  Nothing in the array has to start at zero; each call
@@ -268,9 +282,10 @@ cmf_status cmf_solve_binary(const float *d_Cs, const float *d_Ct, const float *d
 cmf_status cmf_release_graphs(void);
 
 /* ------------------------------------------------------------------------ */
-/* Potts model, L labels (2 <= L <= 64).  d_C: L float32 planes C_1..C_L.   */
-/* State: d_u (L float32 planes), d_qx, d_qy, d_p (L planes each, storage    */
-/* dtype), d_ps (one plane).  rPDRQ: (qbar_i, pbar_i, pbar_s).              */
+/* Potts model, L labels (2 <= L <= 64).  d_C: L cost planes C_1..C_L      */
+/* (float32, or see cmf_params.costs).  State: d_u (L float32 planes),      */
+/* d_qx, d_qy, d_p (L planes each, storage dtype), d_ps (one float32        */
+/* plane).  rPDRQ: (qbar_i, pbar_i, pbar_s).                                */
 /* ------------------------------------------------------------------------ */
 
 /* Cold start: u_i = 1 for the first cheapest label, q_i = 0,
@@ -295,6 +310,18 @@ cmf_status cmf_eval_potts(const float *d_C, int L, const float *d_alpha, float a
                           const void *d_qx, const void *d_qy, const void *d_p, const void *d_ps,
                           double *h_out, void *d_ws, size_t ws_bytes, void *stream);
 
+/* Solve the Potts model (Eq. potts-mf, dual of Eq. relaxed-potts) to a
+ * relative gap <= p->tol_gap or p->max_iter iterations, as cmf_solve_binary
+ * does for the binary model: cold start (u_i = 1 for the first cheapest
+ * label, q_i = 0, p_i = p_s = min_j C_j) unless p->warm_start, then repeat
+ * {check_every iterations of p->algo (Eq. multi:fg:4, the Eckstein-Bertsekas
+ * equations after Thm 2, Eq. pdrq:4labels, Eq. mADMM:Tai_yuan, Eq.
+ * alg1:4labels); the certificates of cmf_eval_potts}.  h_hist (host, may be
+ * NULL) receives up to hist_cap rows of (iteration, E, D, gap, res); *h_iters
+ * (host, may be NULL) the iterations run.  The state buffers hold the last
+ * iterate (u itself, also for the warp-strip kernels' w form).  Returns
+ * CMF_OK on convergence, CMF_NOT_CONVERGED at max_iter, CMF_ETIMEOUT when a
+ * bounded device wait ran out. */
 cmf_status cmf_solve_potts(const float *d_C, int L, const float *d_alpha, float alpha0, int H,
                            int W, int pitch, const cmf_params *p, float *d_u, void *d_qx,
                            void *d_qy, void *d_p, void *d_ps, double *h_hist, int hist_cap,
@@ -344,7 +371,7 @@ typedef struct {
     float *d_u;             /* binary: 1 plane; Potts: L planes (float32)       */
     void *d_qx, *d_qy;      /* 1 / L planes each, storage dtype                 */
     void *d_p;              /* binary: p_t (1 plane); Potts: p_i (L planes)     */
-    void *d_ps;             /* p_s (1 plane)                                    */
+    void *d_ps;             /* p_s (1 plane; Potts: float32)                    */
     /* results (outputs) */
     int iters;              /* iterations run for this instance                 */
     int status;             /* CMF_OK or CMF_NOT_CONVERGED                      */

@@ -2,6 +2,11 @@
 
 The translation units are compiled in parallel and linked into
 ``paper_2004_11227_gb300/libcmf.so``; objects go to ``paper_2004_11227_gb300/_build``.
+The same batch builds ``libcmf_inject.so``, the fault-injection library of
+the failure-detection tests: the translation units with bounded device waits
+compiled again with CMF_FAULT_INJECTION (a short wait limit and a hook that
+makes a wait run out), linked with the other objects.  Nothing on the product
+path loads it.
 """
 from __future__ import annotations
 
@@ -15,6 +20,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcmf.so")
+LIB_INJECT = os.path.join(PKG, "libcmf_inject.so")
+# translation units with bounded device waits (rebuilt for the injection library)
+INJECT_TUS = ("cmf_binary_tma.cu", "cmf_potts_tma.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -36,9 +44,9 @@ def _deps() -> list:
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB_INJECT):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_INJECT))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -50,12 +58,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     procs = []
     objs = []
+    inj_objs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmd = [nvcc, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE,
                                             stderr=subprocess.STDOUT, text=True)))
+        if os.path.basename(src) in INJECT_TUS:
+            iobj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".inject.o")
+            inj_objs.append((obj, iobj))
+            icmd = [nvcc, *ARCH, *FLAGS, "-DCMF_FAULT_INJECTION", "-I",
+                    os.path.join(ROOT, "include"), "-c", src, "-o", iobj]
+            procs.append((src + " (injection)",
+                          subprocess.Popen(icmd, stdout=subprocess.PIPE,
+                                           stderr=subprocess.STDOUT, text=True)))
     errors = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -68,6 +85,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
+    swap = dict(inj_objs)
+    tmp = LIB_INJECT + ".tmp"
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *[swap.get(o, o) for o in objs]])
+    os.replace(tmp, LIB_INJECT)
     return LIB
 
 

@@ -239,7 +239,9 @@ class Potts:
         self.pitch = pitch_for(self.W)
         self.params = params
         self.device = device
-        self.C = _pitched(C, self.pitch, device)
+        # costs = 2: the cost planes are stored as float16 (rounded once here)
+        cdt = torch.float16 if params.costs == 2 else torch.float32
+        self.C = _pitched(C, self.pitch, device, cdt)
         if np.isscalar(alpha):
             self.alpha, self.alpha0 = None, float(alpha)
         else:
@@ -251,7 +253,9 @@ class Potts:
         self.qx = torch.zeros(shp, dtype=sd, device=device)
         self.qy = torch.zeros(shp, dtype=sd, device=device)
         self.p = torch.zeros(shp, dtype=sd, device=device)
-        self.ps = torch.zeros((self.H, self.pitch), dtype=sd, device=device)
+        # the source flow p_s (one plane shared by the labels) is float32 for
+        # every flow storage
+        self.ps = torch.zeros((self.H, self.pitch), dtype=torch.float32, device=device)
         nb = cmf_workspace_bytes(self.H, self.W, self.L, self.pitch, params)
         self.ws = torch.empty(nb, dtype=torch.uint8, device=device)
 
@@ -276,10 +280,10 @@ class Potts:
         return (_ptr(self.u), _ptr(self.qx), _ptr(self.qy), _ptr(self.p), _ptr(self.ps))
 
 
-def _pitched(a: np.ndarray, pitch: int, device) -> torch.Tensor:
+def _pitched(a: np.ndarray, pitch: int, device, dtype=torch.float32) -> torch.Tensor:
     shp = a.shape[:-1] + (pitch,)
-    t = torch.zeros(shp, dtype=torch.float32, device=device)
-    t[..., :a.shape[-1]] = torch.as_tensor(np.ascontiguousarray(a), device=device)
+    t = torch.zeros(shp, dtype=dtype, device=device)
+    t[..., :a.shape[-1]] = torch.as_tensor(np.ascontiguousarray(a), device=device).to(dtype)
     return t
 
 
@@ -293,11 +297,17 @@ def alloc_potts(inst, params: Params, device="cuda") -> Potts:
 
 def alloc_potts_levels(I, levels, alpha, params: Params, device="cuda") -> Potts:
     """A Potts problem whose costs C_i = (I - levels[i])^2 the kernels compute
-    where they read them (params.costs = 1): the cost buffer holds the image
-    plane followed by the levels."""
+    where they read them: the returned object carries a copy of ``params``
+    with costs = 1, and its cost buffer holds the image plane followed by the
+    levels."""
     I = np.asarray(I, dtype=np.float32)
     lev = np.asarray(levels, dtype=np.float32)
     H, W = I.shape
+    # a copy with costs = 1: the caller's params object is left as it was
+    keep = getattr(params, "_rho_keep", None)
+    params = Params.from_buffer_copy(params)
+    if keep is not None:
+        params._rho_keep = keep
     params.costs = 1
     # shape the container as an L-label problem, then replace its cost buffer
     pot = Potts(np.zeros((len(lev), H, W), np.float32), alpha, params, device)

@@ -35,18 +35,18 @@ size_t hist_rows_for(const cmf_params& p);
 WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool potts) {
     const size_t plane = (size_t)H * (size_t)pitch;
     const size_t es = dtype_size(p.storage);
-    const int nu = potts ? L : 1;           // u planes
-    const int nf = potts ? 3 * L + 1 : 4;   // flow planes
+    // one state set: u planes (float32), flow planes in the storage type, and
+    // for Potts the float32 p_s plane; the Potts per-label planes are packed
+    // [L][H][pitch]
+    const size_t set = potts ? align_up(plane * 4 * L) + 3 * align_up(plane * es * L) +
+                                   align_up(plane * 4)
+                             : align_up(plane * 4) + 4 * align_up(plane * es);
     WsLayout w;
     size_t off = 0;
     w.state = off;
-    off += align_up(plane * 4 * nu);
-    for (int i = 0; i < nf; ++i) off += align_up(plane * es);
+    off += set;
     w.state2 = off;
-    if (!potts && p.impl == CMF_FUSED) {
-        off += align_up(plane * 4 * nu);
-        for (int i = 0; i < nf; ++i) off += align_up(plane * es);
-    }
+    if (!potts && p.impl == CMF_FUSED) off += set;
     w.tmp = off;
     // plain forms: g and div q^{k+1} (per label for Potts); the fused kernels
     // keep everything on chip
@@ -85,7 +85,7 @@ cmf_status check_params(const cmf_params* p, int L) {
     if (p->variant != 0 && p->variant != 1 && p->variant != 2 && p->variant != 4 &&
         p->variant != 8 && p->variant != 16 && p->variant != 32)
         return CMF_EINVAL;
-    if (p->costs != 0 && p->costs != 1) return CMF_EINVAL;
+    if (p->costs < 0 || p->costs > 2) return CMF_EINVAL;
     // relaxation schedule {rho_k}: non-decreasing in (0, 2) (Thm 1, Thm 2),
     // continued by rho, for the two relaxed algorithms only
     if (p->rho_schedule_len < 0) return CMF_EINVAL;
@@ -114,6 +114,16 @@ Alpha make_alpha(const float* d_alpha, float alpha0) { return Alpha{d_alpha, alp
 
 Grid make_grid(int H, int W, int pitch) {
     return Grid{H, W, pitch, (size_t)H * (size_t)pitch};
+}
+
+// The Potts problem as the kernels see it.  costs == 1: d_C holds the image
+// plane followed by the L levels; costs == 2: d_C holds L float16 planes.
+PottsProblem potts_problem(const float* C, int L, const float* alpha, float alpha0, int H,
+                           int W, int pitch, int costs) {
+    PottsProblem P{C, L, make_alpha(alpha, alpha0), make_grid(H, W, pitch), nullptr, nullptr};
+    if (costs == 1) P.lev = C + (size_t)H * (size_t)pitch;
+    if (costs == 2) P.C16 = reinterpret_cast<const __half*>(C);
+    return P;
 }
 
 StepConfig make_step(const cmf_params& p, int L, bool potts) {
@@ -401,7 +411,7 @@ PottsStateV ws_potts_state(char* ws, const WsLayout& w, const Grid& G, int L, in
     base += align_up(plane * es * L);
     s.p = base;
     base += align_up(plane * es * L);
-    s.ps = base;
+    s.ps = (float*)base;
     return s;
 }
 
@@ -420,7 +430,7 @@ cudaError_t copy_potts(const PottsStateV& dst, const PottsStateV& src, const Gri
         if ((e = copy_plane((char*)dst.p + oe, (char*)src.p + oe, G, es, st)) != cudaSuccess)
             return e;
     }
-    return copy_plane(dst.ps, src.ps, G, es, st);
+    return copy_plane(dst.ps, src.ps, G, 4, st);  // p_s: float32
 }
 
 struct PottsCall {
@@ -447,16 +457,15 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     if (!C || !u || !qx || !qy || !pp || !ps || !ws) return CMF_EINVAL;
     if (!alpha && !(alpha0 >= 0.0f && isfinite(alpha0))) return CMF_EINVAL;
     const size_t es = dtype_size(p->storage);
-    if (!aligned(u, 4) || !aligned(C, 4) || (alpha && !aligned(alpha, 4))) return CMF_EINVAL;
-    if (!aligned(qx, es) || !aligned(qy, es) || !aligned(pp, es) || !aligned(ps, es))
+    if (!aligned(u, 4) || !aligned(C, p->costs == 2 ? 2 : 4) || (alpha && !aligned(alpha, 4)))
+        return CMF_EINVAL;
+    if (!aligned(qx, es) || !aligned(qy, es) || !aligned(pp, es) || !aligned(ps, 4))
         return CMF_EINVAL;
     if (!aligned(ws, kAlign)) return CMF_EINVAL;
     call.w = ws_layout(H, W, L, pitch, *p, true);
     if (ws_bytes < call.w.total) return CMF_ENOMEM;
-    // costs == 1: d_C holds the image plane followed by the L levels
-    call.P = PottsProblem{C, L, make_alpha(alpha, alpha0), make_grid(H, W, pitch),
-                          p->costs == 1 ? C + (size_t)H * (size_t)pitch : nullptr};
-    call.user = PottsStateV{u, qx, qy, pp, ps};
+    call.P = potts_problem(C, L, alpha, alpha0, H, W, pitch, p->costs);
+    call.user = PottsStateV{u, qx, qy, pp, (float*)ps};
     call.wsbase = (char*)ws;
     call.ws = ws_potts_state(call.wsbase, call.w, call.P.g, L, p->storage);
     call.cfg = make_step(*p, L, true);
@@ -586,7 +595,8 @@ bool graph_eligible(const cmf_params& p) {
 // Everything the kernels of a solve graph are built from: the device, the
 // model, sizes, every device pointer, alpha0 and the parameters (their
 // coefficients, the loop constants).  Calls with equal signatures can replay
-// the same instantiated graph.  Zero-filled before use, compared bytewise.
+// the same instantiated graph.  Zero-filled before use (padding included) and
+// filled field by field, then compared bytewise.
 struct SolveSig {
     int dev, model, L, H, W, pitch;
     float alpha0;
@@ -608,10 +618,27 @@ SolveSig make_sig(int model, int L, int H, int W, int pitch, float alpha0,
     int i = 0;
     for (const void* q : ptrs)
         if (i < 10) k.ptr[i++] = q;
-    memcpy(&k.p, &p, sizeof(p));
-    k.p.rho_schedule = nullptr;
-    k.p.rho_schedule_len = 0;
-    k.p.warm_start = 0;
+    // field by field: the caller's padding bytes (after `costs`, at the tail)
+    // stay zero, so equal parameters always compare equal
+    k.p.algo = p.algo;
+    k.p.storage = p.storage;
+    k.p.impl = p.impl;
+    k.p.aniso = p.aniso;
+    k.p.sweeps = p.sweeps;
+    k.p.max_iter = p.max_iter;
+    k.p.check_every = p.check_every;
+    k.p.use_graph = p.use_graph;
+    k.p.variant = p.variant;
+    k.p.c = p.c;
+    k.p.a = p.a;
+    k.p.a1 = p.a1;
+    k.p.a2 = p.a2;
+    k.p.rho = p.rho;
+    k.p.r = p.r;
+    k.p.sigma = p.sigma;
+    k.p.tau = p.tau;
+    k.p.tol_gap = p.tol_gap;
+    k.p.costs = p.costs;
     return k;
 }
 
@@ -1034,9 +1061,9 @@ cmf_status cmf_init_potts(const float* d_C, int L, int H, int W, int pitch, cons
     if ((s = check_params(p, L)) != CMF_OK) return s;
     if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
     if (!d_C || !d_u || !d_qx || !d_qy || !d_p || !d_ps) return CMF_EINVAL;
-    PottsProblem P{d_C, L, make_alpha(nullptr, 0.f), make_grid(H, W, pitch),
-                   p->costs == 1 ? d_C + (size_t)H * (size_t)pitch : nullptr};
-    PottsStateV st{d_u, d_qx, d_qy, d_p, d_ps};
+    if (!aligned(d_C, p->costs == 2 ? 2 : 4)) return CMF_EINVAL;
+    const PottsProblem P = potts_problem(d_C, L, nullptr, 0.f, H, W, pitch, p->costs);
+    PottsStateV st{d_u, d_qx, d_qy, d_p, (float*)d_ps};
     CMF_CUDA_TRY(potts_init(p->storage, P, st, p->algo == CMF_RPDRQ, (float)p->tau,
                             (cudaStream_t)stream));
     return CMF_OK;

@@ -33,7 +33,7 @@ size_t state_bytes(const cmf_instance& in, int storage) {
     const size_t plane = (size_t)in.H * (size_t)in.pitch;
     const size_t es = dtype_size(storage);
     if (in.model == 0) return al(plane * 4) + 4 * al(plane * es);
-    return al(plane * 4 * in.L) + 3 * al(plane * es * in.L) + al(plane * es);
+    return al(plane * 4 * in.L) + 3 * al(plane * es * in.L) + al(plane * 4);  // p_s float32
 }
 
 BatchLayout batch_layout(const cmf_instance* inst, int n, const cmf_params& p) {
@@ -169,7 +169,9 @@ cmf_status check_instance(const cmf_instance& in, const cmf_params& p) {
     const size_t es = dtype_size(p.storage);
     auto ok = [](const void* q, size_t a) { return ((uintptr_t)q % a) == 0; };
     if (!ok(in.d_cost, 4) || !ok(in.d_u, 4) || (in.d_alpha && !ok(in.d_alpha, 4))) return CMF_EINVAL;
-    if (!ok(in.d_qx, es) || !ok(in.d_qy, es) || !ok(in.d_p, es) || !ok(in.d_ps, es))
+    // the Potts p_s plane is float32 for every flow storage
+    const size_t es_ps = in.model == 1 ? 4 : es;
+    if (!ok(in.d_qx, es) || !ok(in.d_qy, es) || !ok(in.d_p, es) || !ok(in.d_ps, es_ps))
         return CMF_EINVAL;
     return CMF_OK;
 }
@@ -262,7 +264,7 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
             for (int t = 0; t < D.ev_count; ++t) eb.push_back(i);
         } else {
             D.pp = PottsProblem{in.d_cost, in.L, A, G, nullptr};
-            D.pu = PottsStateV{in.d_u, in.d_qx, in.d_qy, in.d_p, in.d_ps};
+            D.pu = PottsStateV{in.d_u, in.d_qx, in.d_qy, in.d_p, (float*)in.d_ps};
             char* b = sbase;
             D.pw.u = (float*)b;
             b += al(plane * 4 * in.L);
@@ -272,7 +274,7 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
             b += al(plane * es * in.L);
             D.pw.p = b;
             b += al(plane * es * in.L);
-            D.pw.ps = b;
+            D.pw.ps = (float*)b;
             D.tile_base = (int)tp.size();
             D.ev_tab = (int)ep.size();
             for (int t = 0; t < ntx * ((in.H + pty - 1) / pty); ++t) tp.push_back(i);

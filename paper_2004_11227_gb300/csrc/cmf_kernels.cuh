@@ -41,15 +41,25 @@ struct BinStateV {
     }
 };
 
-// Potts problem data: L cost planes, or (lev != NULL) one image plane I in C
-// and L levels with C_i(x) = (I(x) - lev[i])^2 computed where it is read.
+// Potts problem data: L float32 cost planes at C; or (lev != NULL) one image
+// plane I at C and L levels with C_i(x) = (I(x) - lev[i])^2 computed where it
+// is read; or (C16 != NULL) L float16 cost planes at C16 (C then holds the
+// same address, never read as float32).
 struct PottsProblem {
     const float* C;
     int L;
     Alpha alpha;
     Grid g;
     const float* lev;
+    const __half* C16;
 };
+
+// Cost source of a Potts problem, as the warp-strip kernels take it as a
+// template parameter.
+enum CostSrc { kCostF32 = 0, kCostLevels = 1, kCostF16 = 2 };
+inline int cost_src(const PottsProblem& P) {
+    return P.lev ? kCostLevels : (P.C16 ? kCostF16 : kCostF32);
+}
 
 // Cost of label l at plane offset k.
 __device__ __forceinline__ float potts_cost(const PottsProblem& P, int l, size_t k) {
@@ -57,16 +67,19 @@ __device__ __forceinline__ float potts_cost(const PottsProblem& P, int l, size_t
         const float d = __ldg(P.C + k) - __ldg(P.lev + l);
         return d * d;
     }
+    if (P.C16) return __half2float(__ldg(P.C16 + (size_t)l * P.g.plane + k));
     return __ldg(P.C + (size_t)l * P.g.plane + k);
 }
 
+// Potts state: the per-label flows in the storage type S; u and the one
+// p_s plane in float32.
 template <typename S>
 struct PottsState {
     float* u;   // L planes
     S* qx;      // L planes
     S* qy;      // L planes
     S* p;       // L planes
-    S* ps;      // one plane
+    float* ps;  // one plane
 };
 
 struct PottsStateV {
@@ -74,10 +87,10 @@ struct PottsStateV {
     void* qx;
     void* qy;
     void* p;
-    void* ps;
+    float* ps;
     template <typename S>
     __host__ __device__ PottsState<S> as() const {
-        return PottsState<S>{u, (S*)qx, (S*)qy, (S*)p, (S*)ps};
+        return PottsState<S>{u, (S*)qx, (S*)qy, (S*)p, ps};
     }
 };
 

@@ -59,7 +59,7 @@ __global__ void k_potts_init(PottsProblem P, PottsState<S> s, float tau) {
         St::st(s.qy + ki, qy);
         St::st(s.p + ki, p);
     }
-    St::st(s.ps + k, DR ? m + tau : m);
+    s.ps[k] = DR ? m + tau : m;
 }
 
 // ---------------------------------------------------------------------------
@@ -92,7 +92,7 @@ __device__ __forceinline__ void potts_admm_tile(PottsProblem P, PottsState<S> s0
     for (int i = tid; i < GX * GY; i += 256) {
         const int ly = i / GX, lx = i - ly * GX;
         const int r = y0 - 1 + ly, c = x0 - 1 + lx;
-        ps_s[ly][lx] = (r >= 0 && r < G.H && c >= 0 && c < G.W) ? St::ld(s0.ps + G.idx(r, c))
+        ps_s[ly][lx] = (r >= 0 && r < G.H && c >= 0 && c < G.W) ? __ldg(s0.ps + G.idx(r, c))
                                                                  : 0.f;
     }
     float accd[ROWS], accp[ROWS];
@@ -173,8 +173,8 @@ __device__ __forceinline__ void potts_admm_tile(PottsProblem P, PottsState<S> s0
         ps1[j] = 0.f;
         if (r < G.H && c < G.W) {
             const float ps0 = ps_s[ly + 1][lx + 1];
-            ps1[j] = potts_ps_update<S>(K, ps0, accd[j], accp[j]);
-            St::st(s1.ps + G.idx(r, c), ps1[j]);
+            ps1[j] = potts_ps_update(K, ps0, accd[j], accp[j]);
+            s1.ps[G.idx(r, c)] = ps1[j];
         }
     }
 #pragma unroll 1
@@ -217,7 +217,7 @@ __global__ void k_potts_plain_g(PottsProblem P, PottsState<S> s, int l, float* g
     using St = Store<S>;
     const size_t lo = (size_t)l * G.plane;
     g[k] = div_plane(G, s.qx + lo, s.qy + lo, r, c, k) + St::ldw(s.p + lo + k) -
-           St::ldw(s.ps + k) - s.u[lo + k] * K.inv_c;
+           s.ps[k] - s.u[lo + k] * K.inv_c;
 }
 
 template <typename S, bool ANISO>
@@ -247,7 +247,7 @@ __global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* g
     POTTS_PIXEL_PROLOGUE
     using St = Store<S>;
     const size_t pl = G.plane;
-    const float ps0 = St::ldw(s.ps + k);
+    const float ps0 = s.ps[k];
     // p_i^{k+1} and v_i per label (v_i parked in u_i), then p_s^{k+1}, then
     // u_i^{k+1} = v_i + cu p_s^{k+1}
     float acc_a = 0.f, acc_b = 0.f;
@@ -259,9 +259,9 @@ __global__ void k_potts_plain_pu(PottsProblem P, PottsState<S> s, const float* g
         St::st(s.p + ki, p1);
         s.u[ki] = v;
     }
-    const float ps1 = potts_ps_update<S>(K, ps0, acc_a, acc_b);
+    const float ps1 = potts_ps_update(K, ps0, acc_a, acc_b);
     for (int l = 0; l < P.L; ++l) s.u[l * pl + k] += K.cu * ps1;
-    St::st(s.ps + k, ps1);
+    s.ps[k] = ps1;
 }
 
 // ---------------------------------------------------------------------------
@@ -298,7 +298,7 @@ __device__ __forceinline__ void potts_dr_tile(PottsProblem P, PottsState<S> s0, 
         if (r >= 0 && r < G.H && c >= 0 && c < G.W) {
             const size_t k = G.idx(r, c);
             for (int l = 0; l < P.L; ++l) U += __ldg(s0.u + (size_t)l * pl + k);
-            pbs = St::ld(s0.ps + k);
+            pbs = __ldg(s0.ps + k);
         }
         U_s[ly][lx] = U;
         pbs_s[ly][lx] = pbs;
@@ -386,7 +386,7 @@ __device__ __forceinline__ void potts_dr_tile(PottsProblem P, PottsState<S> s0, 
         if (r < G.H && c < G.W) {
             const float pbs = pbs_s[ly + NH - 1][lx + NH - 1];
             const float ps1 = pbs - D.tau * usum[j];
-            St::st(s1.ps + G.idx(r, c), pbs + D.rho * ((2.f * ps1 - pbs + D.tau) - ps1));
+            s1.ps[G.idx(r, c)] = pbs + D.rho * ((2.f * ps1 - pbs + D.tau) - ps1);
         }
     }
 }
@@ -413,7 +413,7 @@ __global__ void k_potts_plain_dr_b(PottsProblem P, PottsState<S> s, int l, const
     using St = Store<S>;
     const size_t lo = (size_t)l * G.plane;
     b[k] = -D.sigma * (div_plane(G, s.qx + lo, s.qy + lo, r, c, k) + St::ldw(s.p + lo + k) -
-                       St::ldw(s.ps + k)) +
+                       s.ps[k]) +
            D.sigma * D.tau * ((float)P.L * s.u[lo + k] - U[k]);
 }
 
@@ -442,9 +442,9 @@ __global__ void k_potts_plain_dr_ps(PottsProblem P, PottsState<S> s, DrCoef D) {
     using St = Store<S>;
     float a = 0.f;
     for (int l = 0; l < P.L; ++l) a += s.u[(size_t)l * G.plane + k];
-    const float pbs = St::ldw(s.ps + k);
+    const float pbs = s.ps[k];
     const float ps1 = pbs - D.tau * a;
-    St::st(s.ps + k, pbs + D.rho * ((2.f * ps1 - pbs + D.tau) - ps1));
+    s.ps[k] = pbs + D.rho * ((2.f * ps1 - pbs + D.tau) - ps1);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,7 +510,7 @@ __device__ __forceinline__ void potts_eval_tile(PottsProblem P, PottsState<S> s,
         const float thd = r < G.H - 1 ? simplex_theta(s.u, pl, P.L, k + G.pitch) : 0.f;
         float usum = 0.f;
         for (int l = 0; l < P.L; ++l) usum += s.u[(size_t)l * pl + k];
-        float fs = St::ldw(s.ps + k);
+        float fs = s.ps[k];
         if (DR) fs -= tau * usum;
         float e = 0.f, rr2 = 0.f, dmin = 3.402823466e38f;
         for (int l = 0; l < P.L; ++l) {
@@ -582,13 +582,11 @@ static cudaError_t launch_potts_admm_fused(const PottsProblem& P, const PottsSta
     const size_t dyn = (size_t)P.L * (8 * ROWS) * 32 * sizeof(float);
     auto kern = k_potts_admm_fused<S, ANISO, ROWS>;
     // static + dynamic shared memory above 48 KB needs the opt-in; raise the
-    // limit once per instantiation to the largest request seen so far
-    static size_t configured = 0;
-    if (dyn > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
+    // limit per device to the largest request seen so far
+    static std::atomic<long long> memo[kMaxDevices];
+    {
+        const cudaError_t e = raise_dyn_smem(memo, kern, dyn);
         if (e != cudaSuccess) return e;
-        configured = dyn;
     }
     kern<<<pgrid(P.g, 8 * ROWS), dim3(32, 8), dyn, st>>>(P, a, b, K);
     return cudaGetLastError();
@@ -738,12 +736,10 @@ static cudaError_t launch_batch_potts_admm(int maxL, const BatchDesc* desc, cons
                                            int ntiles, int parity, cudaStream_t st) {
     const size_t dyn = (size_t)maxL * (8 * ROWS) * 32 * sizeof(float);
     auto kern = k_batch_potts_admm<S, ANISO, ROWS>;
-    static size_t configured = 0;
-    if (dyn > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
+    static std::atomic<long long> memo[kMaxDevices];  // limit set on each device
+    {
+        const cudaError_t e = raise_dyn_smem(memo, kern, dyn);
         if (e != cudaSuccess) return e;
-        configured = dyn;
     }
     kern<<<ntiles, dim3(32, 8), dyn, st>>>(desc, tile_inst, parity);
     return cudaGetLastError();

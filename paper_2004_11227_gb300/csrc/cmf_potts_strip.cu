@@ -35,193 +35,209 @@ namespace {
 constexpr int kStripRmax = 24;  // band rows at most (shared accumulators: 24 KB per
                                 // block, so seven blocks of 72 registers fit an SM)
 
-// State values of one row of one label at this lane's column pair.
+// State values of one row of one label at this lane's column pair (p_s is
+// float32 whatever the flow storage).
 template <typename S>
 struct RowVals {
-    typename Pair<S>::T qx, qy, p, ps;
-    float2 w;
+    typename Pair<S>::T qx, qy, p;
+    float2 ps, w;
 };
 
 }  // namespace
 
-// LEV: the costs come from (I, levels) (P.lev set); a separate instantiation
-// keeps the cost-plane kernel free of the extra registers and branches.
-template <typename S, bool ANISO, bool LEV>
-__global__ void __launch_bounds__(kStripWarps * 32, 7)
-    k_potts_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, float cu_in,
-                  int R, int nstrips, int nitems) {
+// One work item of k_potts_strip: strip `cs`, band rows r0 .. r1-1, all
+// labels.  CS: the cost source (kCostF32 planes, kCostLevels, kCostF16
+// planes), a template parameter so each instantiation carries only its own
+// loads.  p_s is float32 whatever the flow storage S.
+template <typename S, bool ANISO, int CS>
+__device__ __forceinline__ void potts_strip_item(const PottsProblem& P, const PottsState<S>& s0,
+                                                 const PottsState<S>& s1, const AdmmCoef& K,
+                                                 float cu_in, int cs, int r0, int r1,
+                                                 float2 (*acc)[32], int lane) {
     using St = Store<S>;
     using PS = Pair<S>;
     using PF = Pair<float>;
+    using PH = Pair<__half>;
+    const Grid G = P.g;
+    const int L = P.L;
+    const unsigned full = 0xffffffffu;
+    const int c = cs - 2 + 2 * lane;  // even column of the pair (W is even)
+    const bool colin = c >= 0 && c < G.W;
+    const bool own = colin && lane >= 1 && lane <= 30;
+    const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;  // odd column is not the last
+    auto row_ok = [&](int r) { return colin && r >= 0 && r < G.H; };
+    // weight of a row's own y term: row H-1 has no forward difference
+    auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+
+    // one row of state at (r, c..c+1): zero outside the grid
+    auto load_row = [&](const S* qx, const S* qy, const S* pp, const float* w, int r,
+                        RowVals<S>& x) {
+        const bool ok = row_ok(r);
+        const int o = r * G.pitch + c;
+        x.qx = ok ? PS::ld(qx + o) : PS::zero();
+        x.qy = ok ? PS::ld(qy + o) : PS::zero();
+        x.p = ok ? PS::ld(pp + o) : PS::zero();
+        x.ps = ok ? PF::ld(s0.ps + o) : PF::zero();
+        x.w = ok ? PF::ld(w + o) : PF::zero();
+    };
+    // g = div q + p_i - p_s - u_i / c at row r, given the row above's q_y
+    // (outside the grid the loaded values are zero)
+    auto g_of = [&](const RowVals<S>& x, float2 qy_up, int r) {
+        const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy), p = PS::f2(x.p);
+        const float2 ps = x.ps;
+        const float qx_left = __shfl_up_sync(full, qx.y, 1);
+        const float wy = row_w(r);
+        const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
+        float2 g;
+        g.x = qx.x - qx_left + wy * qy.x - qy_up.x + p.x - ps.x - u_e * K.inv_c;
+        g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + p.y - ps.y - u_o * K.inv_c;
+        return g;
+    };
+
+    // q^{k+1} = P_alpha(q + grad g / a) at row t of this pair, from g at
+    // rows t and t+1 (zero outside the grid)
+    struct QN {
+        float tx_e, tx_o, ty_e, ty_o;
+    };
+    auto q_new = [&](const RowVals<S>& x, float2 g_t, float2 g_b, float2 al, int t) {
+        const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
+        const float my = row_w(t) * K.inv_a;
+        const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
+        QN q;
+        q.tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
+        q.tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
+        q.ty_e = qy.x + (g_b.x - g_t.x) * my;
+        q.ty_o = qy.y + (g_b.y - g_t.y) * my;
+        project_sel<ANISO>(q.tx_e, q.ty_e, al.x);
+        project_sel<ANISO>(q.tx_o, q.ty_o, al.y);
+        const bool in = colin && t >= 0 && t < G.H;
+        q.tx_e = in ? St::rt(q.tx_e) : 0.f;
+        q.tx_o = in ? St::rt(q.tx_o) : 0.f;
+        q.ty_e = in ? St::rt(q.ty_e) : 0.f;
+        q.ty_o = in ? St::rt(q.ty_o) : 0.f;
+        return q;
+    };
+
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const size_t lo = (size_t)l * G.plane;
+        const S* qx0 = s0.qx + lo;
+        const S* qy0 = s0.qy + lo;
+        const S* p0 = s0.p + lo;
+        const float* w0 = s0.u + lo;
+        const float lev_l = CS == kCostLevels ? __ldg(P.lev + l) : 0.f;
+        S* qx1 = s1.qx + lo;
+        S* qy1 = s1.qy + lo;
+        S* p1o = s1.p + lo;
+        float* w1 = s1.u + lo;
+        auto row = [&](int r, RowVals<S>& x) { load_row(qx0, qy0, p0, w0, r, x); };
+        // costs of label l at row r: its plane, or (I - c_l)^2 from the image
+        // plane (zero outside the grid; never used there)
+        auto ld_c = [&](int r) {
+            if (!row_ok(r)) return PF::zero();
+            const int o = r * G.pitch + c;
+            if (CS == kCostF16) return PH::f2(PH::ld(P.C16 + lo + o));
+            if (CS == kCostLevels) {
+                float2 v = PF::ld(P.C + o);
+                v.x = (v.x - lev_l) * (v.x - lev_l);
+                v.y = (v.y - lev_l) * (v.y - lev_l);
+                return v;
+            }
+            return PF::ld(P.C + lo + o);
+        };
+        auto ld_al = [&](int r) {
+            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+            return row_ok(r) ? PF::ld(P.alpha.plane + r * G.pitch + c) : PF::zero();
+        };
+        // d = div q^{k+1} at output row t from the new q of rows t and t-1,
+        // then p_i^{k+1}, w_i and this label's share of the p_s update
+        auto finish = [&](int t, const QN& q, float2 qy_up, const RowVals<S>& x, float2 cl,
+                          float2 g) {
+            const float txl = __shfl_up_sync(full, q.tx_o, 1);  // new q_x at c-1
+            const float wy = row_w(t);
+            const float d_e = q.tx_e - txl + wy * q.ty_e - qy_up.x;
+            const float d_o = mxo * q.tx_o - q.tx_e + wy * q.ty_o - qy_up.y;
+            const float2 pv = PS::f2(x.p), ps = x.ps;
+            const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
+            float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
+            const float p1_e =
+                potts_label_pu<S>(K, g.x, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
+            const float p1_o =
+                potts_label_pu<S>(K, g.y, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
+            float2& ac = acc[t - r0][lane];
+            const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
+            if (l == 0) {
+                ac = share;
+            } else {
+                ac.x += share.x;
+                ac.y += share.y;
+            }
+            if (own) {
+                const int o = t * G.pitch + c;
+                PS::st(qx1 + o, q.tx_e, q.tx_o);
+                PS::st(qy1 + o, q.ty_e, q.ty_o);
+                PS::st(p1o + o, p1_e, p1_o);
+                PF::st(w1 + o, v_e, v_o);
+            }
+        };
+
+        // top-down: step t makes q^{k+1} of row t and finishes row t;
+        // row t+2 is loaded during the step
+        RowVals<S> a, b, nx;
+        const int rm2 = r0 - 2;
+        const float2 qy_m2 =
+            PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c) : PS::zero());
+        row(r0 - 1, a);
+        row(r0, b);
+        float2 g_t = g_of(a, qy_m2, r0 - 1);
+        float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
+        float2 al_t = ld_al(r0 - 1), cl_t = PF::zero(), al_n = al_t, cl_n = cl_t;
+#pragma unroll 1
+        for (int t = r0 - 1; t < r1; ++t) {
+            if (t + 2 <= r1) row(t + 2, nx);
+            if (t + 1 < r1) {
+                al_n = ld_al(t + 1);
+                cl_n = ld_c(t + 1);
+            }
+            const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);
+            const QN q = q_new(a, g_t, g_n, al_t, t);
+            if (t >= r0) finish(t, q, qyn_up, a, cl_t, g_t);
+            qyn_up = make_float2(q.ty_e, q.ty_o);
+            a = b;
+            b = nx;
+            g_t = g_n;
+            al_t = al_n;
+            cl_t = cl_n;
+        }
+    }
+
+    // p_s^{k+1} on the band from the summed label shares
+#pragma unroll 1
+    for (int t = r0; t < r1; ++t) {
+        if (!own) continue;
+        const int o = t * G.pitch + c;
+        const float2 ps = PF::ld(s0.ps + o);
+        const float2 ac = acc[t - r0][lane];
+        PF::st(s1.ps + o, potts_ps_update(K, ps.x, ac.x, 0.f), potts_ps_update(K, ps.y, ac.y, 0.f));
+    }
+}
+
+template <typename S, bool ANISO, int CS>
+__global__ void __launch_bounds__(kStripWarps * 32, 7)
+    k_potts_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, float cu_in,
+                  int R, int nstrips, int nitems) {
     __shared__ float2 acc_s[kStripWarps][kStripRmax][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float2(*acc)[32] = acc_s[wib];
     const Grid G = P.g;
-    const int L = P.L;
-    const unsigned full = 0xffffffffu;
 
     for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
          item += gridDim.x * kStripWarps) {
         const int cs = (item % nstrips) * kStripOut;
         const int r0 = (item / nstrips) * R;
         const int r1 = min(r0 + R, G.H);
-        const int c = cs - 2 + 2 * lane;  // even column of the pair (W is even)
-        const bool colin = c >= 0 && c < G.W;
-        const bool own = colin && lane >= 1 && lane <= 30;
-        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;  // odd column is not the last
-
-        // one row of state at (r, c..c+1): zero outside the grid
-        auto load_row = [&](const S* qx, const S* qy, const S* pp, const float* w, int r,
-                            RowVals<S>& x) {
-            const bool ok = colin && r >= 0 && r < G.H;
-            const int o = r * G.pitch + c;
-            x.qx = ok ? PS::ld(qx + o) : PS::zero();
-            x.qy = ok ? PS::ld(qy + o) : PS::zero();
-            x.p = ok ? PS::ld(pp + o) : PS::zero();
-            x.ps = ok ? PS::ld(s0.ps + o) : PS::zero();
-            x.w = ok ? PF::ld(w + o) : PF::zero();
-        };
-        // weight of a row's own y term: row H-1 has no forward difference
-        auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
-        // g = div q + p_i - p_s - u_i / c at row r, given the row above's q_y
-        // (outside the grid the loaded values are zero)
-        auto g_of = [&](const RowVals<S>& x, float2 qy_up, int r) {
-            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy), p = PS::f2(x.p);
-            const float2 ps = PS::f2(x.ps);
-            const float qx_left = __shfl_up_sync(full, qx.y, 1);
-            const float wy = row_w(r);
-            const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
-            float2 g;
-            g.x = qx.x - qx_left + wy * qy.x - qy_up.x + p.x - ps.x - u_e * K.inv_c;
-            g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + p.y - ps.y - u_o * K.inv_c;
-            return g;
-        };
-
-        // q^{k+1} = P_alpha(q + grad g / a) at row t of this pair, from g at
-        // rows t and t+1 (zero outside the grid)
-        struct QN {
-            float tx_e, tx_o, ty_e, ty_o;
-        };
-        auto q_new = [&](const RowVals<S>& x, float2 g_t, float2 g_b, float2 al, int t) {
-            const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
-            const float my = row_w(t) * K.inv_a;
-            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
-            QN q;
-            q.tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
-            q.tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
-            q.ty_e = qy.x + (g_b.x - g_t.x) * my;
-            q.ty_o = qy.y + (g_b.y - g_t.y) * my;
-            project_sel<ANISO>(q.tx_e, q.ty_e, al.x);
-            project_sel<ANISO>(q.tx_o, q.ty_o, al.y);
-            const bool in = colin && t >= 0 && t < G.H;
-            q.tx_e = in ? St::rt(q.tx_e) : 0.f;
-            q.tx_o = in ? St::rt(q.tx_o) : 0.f;
-            q.ty_e = in ? St::rt(q.ty_e) : 0.f;
-            q.ty_o = in ? St::rt(q.ty_o) : 0.f;
-            return q;
-        };
-
-#pragma unroll 1
-        for (int l = 0; l < L; ++l) {
-            const size_t lo = (size_t)l * G.plane;
-            const S* qx0 = s0.qx + lo;
-            const S* qy0 = s0.qy + lo;
-            const S* p0 = s0.p + lo;
-            const float* w0 = s0.u + lo;
-            // costs of label l: its plane, or (I - c_l)^2 from the image plane
-            const float* Cb = LEV ? P.C : P.C + lo;
-            const float lev_l = LEV ? __ldg(P.lev + l) : 0.f;
-            S* qx1 = s1.qx + lo;
-            S* qy1 = s1.qy + lo;
-            S* p1o = s1.p + lo;
-            float* w1 = s1.u + lo;
-            auto row = [&](int r, RowVals<S>& x) { load_row(qx0, qy0, p0, w0, r, x); };
-            auto ld_c = [&](int r) {
-                float2 v =
-                    (colin && r >= 0 && r < G.H) ? PF::ld(Cb + r * G.pitch + c) : PF::zero();
-                if (LEV) {  // (zero outside the grid is never used)
-                    v.x = (v.x - lev_l) * (v.x - lev_l);
-                    v.y = (v.y - lev_l) * (v.y - lev_l);
-                }
-                return v;
-            };
-            auto ld_al = [&](int r) {
-                if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
-                return (colin && r >= 0 && r < G.H) ? PF::ld(P.alpha.plane + r * G.pitch + c)
-                                                    : PF::zero();
-            };
-            // d = div q^{k+1} at output row t from the new q of rows t and t-1,
-            // then p_i^{k+1}, w_i and this label's share of the p_s update
-            auto finish = [&](int t, const QN& q, float2 qy_up, const RowVals<S>& x,
-                              float2 cl, float2 g) {
-                const float txl = __shfl_up_sync(full, q.tx_o, 1);  // new q_x at c-1
-                const float wy = row_w(t);
-                const float d_e = q.tx_e - txl + wy * q.ty_e - qy_up.x;
-                const float d_o = mxo * q.tx_o - q.tx_e + wy * q.ty_o - qy_up.y;
-                const float2 pv = PS::f2(x.p), ps = PS::f2(x.ps);
-                const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
-                float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
-                const float p1_e =
-                    potts_label_pu<S>(K, g.x, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
-                const float p1_o =
-                    potts_label_pu<S>(K, g.y, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
-                float2& ac = acc[t - r0][lane];
-                const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
-                if (l == 0) {
-                    ac = share;
-                } else {
-                    ac.x += share.x;
-                    ac.y += share.y;
-                }
-                if (own) {
-                    const int o = t * G.pitch + c;
-                    PS::st(qx1 + o, q.tx_e, q.tx_o);
-                    PS::st(qy1 + o, q.ty_e, q.ty_o);
-                    PS::st(p1o + o, p1_e, p1_o);
-                    PF::st(w1 + o, v_e, v_o);
-                }
-            };
-
-            // top-down: step t makes q^{k+1} of row t and finishes row t;
-            // row t+2 is loaded during the step
-            RowVals<S> a, b, nx;
-            const int rm2 = r0 - 2;
-            const float2 qy_m2 = PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c)
-                                                            : PS::zero());
-            row(r0 - 1, a);
-            row(r0, b);
-            float2 g_t = g_of(a, qy_m2, r0 - 1);
-            float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
-            float2 al_t = ld_al(r0 - 1), cl_t = PF::zero(), al_n = al_t, cl_n = cl_t;
-#pragma unroll 1
-            for (int t = r0 - 1; t < r1; ++t) {
-                if (t + 2 <= r1) row(t + 2, nx);
-                if (t + 1 < r1) {
-                    al_n = ld_al(t + 1);
-                    cl_n = ld_c(t + 1);
-                }
-                const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);
-                const QN q = q_new(a, g_t, g_n, al_t, t);
-                if (t >= r0) finish(t, q, qyn_up, a, cl_t, g_t);
-                qyn_up = make_float2(q.ty_e, q.ty_o);
-                a = b;
-                b = nx;
-                g_t = g_n;
-                al_t = al_n;
-                cl_t = cl_n;
-            }
-        }
-
-        // p_s^{k+1} on the band from the summed label shares
-#pragma unroll 1
-        for (int t = r0; t < r1; ++t) {
-            if (!own) continue;
-            const int o = t * G.pitch + c;
-            const float2 ps = PS::f2(PS::ld(s0.ps + o));
-            const float2 ac = acc[t - r0][lane];
-            PS::st(s1.ps + o, potts_ps_update<S>(K, ps.x, ac.x, 0.f),
-                   potts_ps_update<S>(K, ps.y, ac.y, 0.f));
-        }
+        potts_strip_item<S, ANISO, CS>(P, s0, s1, K, cu_in, cs, r0, r1, acc, lane);
+        __syncwarp();
     }
 }
 
@@ -306,13 +322,16 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             float2 qby_up = ld_s(qy0, m_first - 1);
             float2 in_u = ld_f(u0, m_first), in_qx = ld_s(qx0, m_first);
             float2 in_qy = ld_s(qy0, m_first), in_p = ld_s(p0, m_first);
-            float2 in_ps = ld_s(s0.ps, m_first);
+            float2 in_ps = ld_f(s0.ps, m_first);
             const int t_first = m_first - NS - 1;
             float2 f_qx = ld_s(qx0, t_first), f_qy = ld_s(qy0, t_first);
             // costs of label l: its plane, or (I - c_l)^2 from the image plane
             const float* Cb = P.lev ? P.C : P.C + lo;
             const float lev_l = P.lev ? __ldg(P.lev + l) : 0.f;
             auto ld_cost = [&](int r) {
+                if (P.C16)
+                    return ok_row(r) ? Pair<__half>::f2(Pair<__half>::ld(P.C16 + lo + r * G.pitch + c))
+                                     : PF::zero();
                 float2 v = ld_f(Cb, r);
                 if (P.lev && ok_row(r)) {
                     v.x = (v.x - lev_l) * (v.x - lev_l);
@@ -347,7 +366,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                     in_qx = ld_s(qx0, r);
                     in_qy = ld_s(qy0, r);
                     in_p = ld_s(p0, r);
-                    in_ps = ld_s(s0.ps, r);
+                    in_ps = ld_f(s0.ps, r);
                 }
 #pragma unroll
                 for (int st = 0; st < NS; ++st) {
@@ -414,10 +433,10 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         // phase 3: p_s reflection on the band
         if (own)
             for (int t = r0; t < r1; ++t) {
-                const float2 pbs = ld_s(s0.ps, t);
+                const float2 pbs = ld_f(s0.ps, t);
                 const float2 us = Ns[(t - r0) * 32 + lane];
                 const float ps1x = pbs.x - D.tau * us.x, ps1y = pbs.y - D.tau * us.y;
-                PS::st(s1.ps + t * G.pitch + c,
+                PF::st(s1.ps + t * G.pitch + c,
                        pbs.x + D.rho * ((2.f * ps1x - pbs.x + D.tau) - ps1x),
                        pbs.y + D.rho * ((2.f * ps1y - pbs.y + D.tau) - ps1y));
             }
@@ -427,13 +446,12 @@ __global__ void __launch_bounds__(kStripWarps * 32)
 
 // u_i = w_i + cu p_s on every label plane (turns the strip kernel's output
 // back into the multipliers themselves).
-template <typename S>
-__global__ void k_potts_strip_finalize(Grid G, int L, float* u, const S* ps, float cu) {
+__global__ void k_potts_strip_finalize(Grid G, int L, float* u, const float* ps, float cu) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (c >= G.W) return;
     const size_t k = G.idx(r, c);
-    const float s = cu * Store<S>::ld(ps + k);
+    const float s = cu * __ldg(ps + k);
 #pragma unroll 4
     for (int l = 0; l < L; ++l) u[(size_t)l * G.plane + k] += s;
 }
@@ -449,28 +467,21 @@ bool potts_strip_eligible(const Grid& G, int storage, const float* C, const floa
     if (!al(C, 8) || (alpha && !al(alpha, 8))) return false;
     for (const PottsStateV* s : {&a, &b})
         if (!al(s->u, 8) || !al(s->qx, es2) || !al(s->qy, es2) || !al(s->p, es2) ||
-            !al(s->ps, es2))
+            !al(s->ps, 8))
             return false;
     return true;
 }
 
-template <typename S, bool ANISO, bool LEV>
+template <typename S, bool ANISO, int CS>
 static cudaError_t launch_strip(const PottsProblem& P, const PottsState<S>& a,
                                 const PottsState<S>& b, const AdmmCoef& K, float cu_in,
                                 cudaStream_t st) {
-    auto kern = k_potts_strip<S, ANISO, LEV>;
-    static int resident = 0;  // warps resident on the whole device
-    if (!resident) {
-        int dev = 0, sms = 0, blocks = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
-                                                                0)) != cudaSuccess)
-            return e;
-        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    auto kern = k_potts_strip<S, ANISO, CS>;
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    long long resident = 0;
+    {
+        const cudaError_t e = strip::device_resident_warps(memo, kern, 0, resident);
+        if (e != cudaSuccess) return e;
     }
     const Grid& G = P.g;
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
@@ -484,16 +495,24 @@ static cudaError_t launch_strip(const PottsProblem& P, const PottsState<S>& a,
     return cudaGetLastError();
 }
 
+template <typename S, int CS>
+static cudaError_t strip_step_cs(const PottsProblem& P, const PottsState<S>& A,
+                                 const PottsState<S>& B, bool aniso, const AdmmCoef& K,
+                                 float cu_in, cudaStream_t st) {
+    return aniso ? launch_strip<S, true, CS>(P, A, B, K, cu_in, st)
+                 : launch_strip<S, false, CS>(P, A, B, K, cu_in, st);
+}
+
 template <typename S>
 static cudaError_t strip_step_s(const PottsProblem& P, const PottsStateV& a,
                                 const PottsStateV& b, bool aniso, const AdmmCoef& K,
                                 float cu_in, cudaStream_t st) {
     const PottsState<S> A = a.as<S>(), B = b.as<S>();
-    if (P.lev)
-        return aniso ? launch_strip<S, true, true>(P, A, B, K, cu_in, st)
-                     : launch_strip<S, false, true>(P, A, B, K, cu_in, st);
-    return aniso ? launch_strip<S, true, false>(P, A, B, K, cu_in, st)
-                 : launch_strip<S, false, false>(P, A, B, K, cu_in, st);
+    switch (cost_src(P)) {
+        case kCostLevels: return strip_step_cs<S, kCostLevels>(P, A, B, aniso, K, cu_in, st);
+        case kCostF16: return strip_step_cs<S, kCostF16>(P, A, B, aniso, K, cu_in, st);
+        default: return strip_step_cs<S, kCostF32>(P, A, B, aniso, K, cu_in, st);
+    }
 }
 
 cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
@@ -514,21 +533,11 @@ static cudaError_t launch_potts_dr_strip(const PottsProblem& P, const PottsState
     constexpr int RMAX = 16;
     auto kern = k_potts_dr_strip<S, ANISO, SW>;
     auto dyn_for = [](int r) { return (size_t)kStripWarps * (2 * r + 2 * NS + 1) * 32 * 8; };
-    static int resident = 0;
-    if (!resident) {
-        int dev = 0, sms = 0, blocks = 0;
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)dyn_for(RMAX))) != cudaSuccess)
-            return e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripWarps * 32,
-                                                                dyn_for(RMAX))) != cudaSuccess)
-            return e;
-        resident = sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    long long resident = 0;
+    {
+        const cudaError_t e = strip::device_resident_warps(memo, kern, dyn_for(RMAX), resident);
+        if (e != cudaSuccess) return e;
     }
     const Grid& G = P.g;
     constexpr int OUT = 2 * (32 - 2 * (SW + 1));
@@ -573,21 +582,10 @@ cudaError_t potts_dr_strip_step(int storage, const PottsProblem& P, const PottsS
 
 cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const PottsStateV& s,
                                  float cu, cudaStream_t st) {
+    (void)storage;  // p_s is float32 for every flow storage
     const Grid& G = P.g;
     const dim3 grid((G.W + 127) / 128, G.H);
-    switch (storage) {
-        case CMF_F32:
-            k_potts_strip_finalize<float><<<grid, 128, 0, st>>>(G, P.L, s.u, (const float*)s.ps,
-                                                                 cu);
-            break;
-        case CMF_F16:
-            k_potts_strip_finalize<__half><<<grid, 128, 0, st>>>(G, P.L, s.u,
-                                                                  (const __half*)s.ps, cu);
-            break;
-        default:
-            k_potts_strip_finalize<__nv_bfloat16>
-                <<<grid, 128, 0, st>>>(G, P.L, s.u, (const __nv_bfloat16*)s.ps, cu);
-    }
+    k_potts_strip_finalize<<<grid, 128, 0, st>>>(G, P.L, s.u, s.ps, cu);
     return cudaGetLastError();
 }
 
@@ -730,12 +728,15 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             for (int t = r0; t < r1; ++t) {
                 u_n = ld_f(ul, t + 1);
                 const float2 th_n = th_s[wib][t + 1 - r0][lane];
-                float2 Cl = ld_f(Cb, t);
+                float2 Cl = P.C16 ? (ok_row(t) ? Pair<__half>::f2(Pair<__half>::ld(
+                                                      P.C16 + lo + t * G.pitch + c))
+                                               : PF::zero())
+                                  : ld_f(Cb, t);
                 if (P.lev && ok_row(t)) {
                     Cl.x = (Cl.x - lev_l) * (Cl.x - lev_l);
                     Cl.y = (Cl.y - lev_l) * (Cl.y - lev_l);
                 }
-                float2 fp = ld_s(s.p + lo, t), fs = ld_s(s.ps, t);
+                float2 fp = ld_s(s.p + lo, t), fs = ld_f(s.ps, t);
                 al = ld_al(t);
                 flows(t, u_t, u_n, fx, fy);
                 const float wy = row_w(t);
@@ -822,8 +823,8 @@ static cudaError_t launch_potts_eval_strip(const PottsProblem& P, const PottsSta
     // the grid is eval_blocks(H, W) blocks (the partial count every
     // certificate path shares); bands sized for the warps actually resident
     const int blocks = eval_blocks(G.H, G.W);
-    static long long resident = 0;
-    if (!resident) resident = strip::resident_warps(k_potts_eval_strip<S, ANISO, DR>);
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    const long long resident = strip::resident_warps(memo, k_potts_eval_strip<S, ANISO, DR>);
     const long long slots = resident > 0 ? resident : (long long)blocks * kStripWarps;
     const int nstrips = (G.W + kStripOut - 1) / kStripOut;
     const int R = strip::choose_rows(G.H, nstrips, slots, 4, kEvalRmax, 2);

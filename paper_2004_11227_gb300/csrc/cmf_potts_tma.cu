@@ -16,6 +16,18 @@
 
 namespace cmf {
 
+#ifdef CMF_FAULT_INJECTION
+// Fault-injection test build only (never in the library the product loads):
+// extra bytes the p_s stage's barrier expects beyond what its copy delivers.
+// With a non-zero value that barrier's phase cannot complete, the bounded
+// wait runs out, the kernel records kErrWaitTimeout and returns; nothing
+// faults and no copy is left in flight.
+__device__ unsigned int g_inject_extra_tx = 0;
+#define CMF_PS_EXTRA_TX g_inject_extra_tx
+#else
+#define CMF_PS_EXTRA_TX 0u
+#endif
+
 namespace {
 
 constexpr int align128(int b) { return (b + 127) / 128 * 128; }
@@ -30,9 +42,10 @@ struct PottsTmaLayout {
     static constexpr int FU = align128(BY * BXU * 4);
     static constexpr int STAGE = 3 * FS + FU;
     static constexpr uint32_t TX_BYTES = 3u * BY * BXS * sizeof(S) + (uint32_t)BY * BXU * 4u;
-    static constexpr uint32_t PS_BYTES = (uint32_t)BY * BXS * sizeof(S);
+    // p_s is float32 for every flow storage: staged like u
+    static constexpr uint32_t PS_BYTES = (uint32_t)BY * BXU * 4u;
     // + 128: the kernel rounds the dynamic shared-memory base up to 128 bytes
-    static size_t dyn_bytes(int L) { return 2 * STAGE + FS + (size_t)L * TY * 32 * 4 + 128; }
+    static size_t dyn_bytes(int L) { return 2 * STAGE + FU + (size_t)L * TY * 32 * 4 + 128; }
 };
 
 template <typename S>
@@ -67,8 +80,10 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     extern __shared__ __align__(128) unsigned char dsm_raw[];
     // round up to 128 bytes by pointer arithmetic (keeps the shared space)
     unsigned char* dsm = dsm_raw + ((128u - (smem_u32(dsm_raw) & 127u)) & 127u);
-    S* ps_s = reinterpret_cast<S*>(dsm + 2 * Lay::STAGE);
-    float* v_s = reinterpret_cast<float*>(dsm + 2 * Lay::STAGE + Lay::FS);
+    float* ps_s = reinterpret_cast<float*>(dsm + 2 * Lay::STAGE);
+    // the p_s box starts XO - XU columns later than the S boxes
+    const float* sps = ps_s - (XO - XU);
+    float* v_s = reinterpret_cast<float*>(dsm + 2 * Lay::STAGE + Lay::FU);
 
     const Grid G = P.g;
     const int L = P.L;
@@ -92,8 +107,8 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
     }
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[2], Lay::PS_BYTES);
-        tma_load_3d(ps_s, &mps, &bar[2], x0 - XO, y0 - 2, 0);
+        mbar_arrive_expect_tx(&bar[2], Lay::PS_BYTES + CMF_PS_EXTRA_TX);
+        tma_load_3d(ps_s, &mps, &bar[2], x0 - XU, y0 - 2, 0);
         issue(0, 0);
         if (L > 1) issue(1, 1);
     }
@@ -188,7 +203,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
             dv += g_my[n] * sload(sqy + o);
             dv -= sload(sqy + o - BXS);
             g_s[tid + 256 * n] =
-                dv + sload(sp + o) - sload(ps_s + o) - su[g_uoff[n]] * K.inv_c;
+                dv + sload(sp + o) - sps[g_uoff[n]] - su[g_uoff[n]] * K.inv_c;
         }
         __syncthreads();
 
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
             d += o_my[j] * qny[qi];
             d -= qny[qi - QW];
             const int so = (ly + 2) * BXS + lx + XO;
-            const float ps0 = sload(ps_s + so);
+            const float ps0 = sps[(ly + 2) * BXU + lx + XO];
             const float p0 = sload(sp + so);
             const float u0 = su[(ly + 2) * BXU + lx + XO];
             const bool own = o_k[j] >= 0;
@@ -244,9 +259,9 @@ __global__ void __launch_bounds__(256, TY <= 16 ? 4 : 2)
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) {
         const int ly = threadIdx.y + 8 * j, lx = threadIdx.x;
-        const float ps0 = sload(ps_s + (ly + 2) * BXS + lx + XO);
-        ps1[j] = potts_ps_update<S>(K, ps0, accd[j], accp[j]);
-        if (o_k[j] >= 0) St::st(s1.ps + o_k[j], ps1[j]);
+        const float ps0 = sps[(ly + 2) * BXU + lx + XO];
+        ps1[j] = potts_ps_update(K, ps0, accd[j], accp[j]);
+        if (o_k[j] >= 0) s1.ps[o_k[j]] = ps1[j];
     }
 #pragma unroll 1
     for (int l = 0; l < L; ++l) {
@@ -301,8 +316,7 @@ cudaError_t potts_tma_maps(const Grid& G, int L, int storage, const PottsStateV&
     if ((e = encode_tma_3d(&m.p, s.p, es, G.W, G.H, L, G.pitch, bxs, by)) != cudaSuccess)
         return e;
     if ((e = encode_tma_3d(&m.u, s.u, 4, G.W, G.H, L, G.pitch, 40, by)) != cudaSuccess) return e;
-    if ((e = encode_tma_3d(&m.ps, s.ps, es, G.W, G.H, 1, G.pitch, bxs, by)) != cudaSuccess)
-        return e;
+    if ((e = encode_tma_3d(&m.ps, s.ps, 4, G.W, G.H, 1, G.pitch, 40, by)) != cudaSuccess) return e;
     m.ty = ty;
     return cudaSuccess;
 }
@@ -310,15 +324,8 @@ cudaError_t potts_tma_maps(const Grid& G, int L, int storage, const PottsStateV&
 // Raise the kernel's dynamic shared-memory limit to what L labels need.
 template <typename S, bool ANISO, int TY>
 static cudaError_t configure_tma(size_t dyn) {
-    static size_t configured = 0;
-    if (dyn > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_potts_admm_tma<S, ANISO, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn);
-        if (e != cudaSuccess) return e;
-        configured = dyn;
-    }
-    return cudaSuccess;
+    static std::atomic<long long> memo[kMaxDevices];  // limit set on each device
+    return raise_dyn_smem(memo, k_potts_admm_tma<S, ANISO, TY>, dyn);
 }
 
 // Warps of this kernel resident per SM for L labels (0 on error).
@@ -387,3 +394,14 @@ cudaError_t potts_admm_tma_step(int storage, const PottsProblem& P, const PottsS
 }
 
 }  // namespace cmf
+
+#ifdef CMF_FAULT_INJECTION
+// Test hook of the fault-injection build: every later Potts TMA launch on the
+// current device expects `bytes` more on its p_s barrier than its copy
+// delivers (0 switches it off).
+extern "C" cmf_status cmf_debug_inject_tx_mismatch(unsigned int bytes) {
+    return cudaMemcpyToSymbol(cmf::g_inject_extra_tx, &bytes, sizeof(bytes)) == cudaSuccess
+               ? CMF_OK
+               : CMF_ECUDA;
+}
+#endif

@@ -82,8 +82,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+#ifdef CMF_FAULT_INJECTION
+// Fault-injection test build only: about 50 microseconds, so a test can make
+// a wait run out quickly (see cmf_debug_inject_tx_mismatch).
+constexpr long long kWaitLimitCycles = 100000ll;
+#else
 // About one second at the GB300's 2.07 GHz maximum SM clock.
 constexpr long long kWaitLimitCycles = 2000000000ll;
+#endif
 
 // (kErrWaitTimeout, the value a timed-out wait records, is in cmf_kernels.cuh.)
 

@@ -91,11 +91,12 @@ def test_bad_arguments_rejected_without_launch(cmf):
             setattr(q, k, v)
         assert lib.cmf_iterate_binary(ptr, ptr, None, 0.5, 8, 8, 8, ctypes.byref(q), 1, ptr,
                                       ptr, ptr, ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL, bad
-    # Potts: unknown cost input
-    pc = cmf.default_params(cmf.RPADMM_EB, 4)
-    pc.costs = 2
-    assert lib.cmf_iterate_potts(ptr, 4, None, 0.5, 8, 8, 8, ctypes.byref(pc), 1, ptr, ptr, ptr,
-                                 ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL
+    # Potts: unknown cost input (0 float32 planes, 1 image and levels, 2 float16 planes)
+    for bad_costs in (3, -1):
+        pc = cmf.default_params(cmf.RPADMM_EB, 4)
+        pc.costs = bad_costs
+        assert lib.cmf_iterate_potts(ptr, 4, None, 0.5, 8, 8, 8, ctypes.byref(pc), 1, ptr, ptr,
+                                     ptr, ptr, ptr, ptr, 1 << 20, None) == cmf.EINVAL
     # Potts: L out of range
     pp = cmf.default_params(cmf.RPADMM_EB, 4)
     assert lib.cmf_iterate_potts(ptr, 1, None, 0.5, 8, 8, 8, ctypes.byref(pp), 1, ptr, ptr, ptr,
@@ -176,3 +177,16 @@ def test_rho_schedule_binding_keeps_its_array(cmf):
     assert p.rho_schedule_len == 0 and not p.rho_schedule
     q = cmf.default_params(cmf.RPDRQ, 4)
     assert q.rho_schedule_len == 0 and not q.rho_schedule
+
+
+def test_levels_container_leaves_callers_params_alone(cmf):
+    """alloc_potts_levels works on a copy of the parameters (costs = 1), so
+    the caller's object keeps costs = 0 and its relaxation schedule."""
+    import numpy as np
+
+    p = cmf.default_params(cmf.RPADMM_EB, 3, rho_schedule=[1.0, 1.5])
+    I = np.zeros((4, 6), np.float32)
+    s = cmf.alloc_potts_levels(I, [0.1, 0.5, 0.9], 0.3, p, device="cpu")
+    assert p.costs == 0 and s.params.costs == 1
+    assert s.params.rho_schedule_len == 2 and s.params.rho_schedule[1] == 1.5
+    assert s.C.numel() == 4 * s.pitch + 3

@@ -33,6 +33,9 @@ def _cases():
         "L8_37x1": (synth.random_potts(37, 1, 8, seed=23, alpha=0.3), 30),
         "L5_ragged_67x35": (synth.random_potts(67, 35, 5, seed=24, alpha=0.25,
                                                field_alpha=True), 40),
+        # wide enough for interior warp-strip items (no bounds predicates)
+        # beside boundary ones, in both directions
+        "voronoi16_mixed_130x256": (synth.config5(130, 256), 20),
     }
 
 
@@ -435,3 +438,25 @@ def test_levels_solve_certified(cmf):
     assert status == cmf.OK and hist[-1, 3] <= 1e-4
     E, D, gap, res = O.potts_eval(C, inst.alpha, s.state(), O.default_params(2, 4))
     assert gap <= 1.01e-4
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("shape", [(48, 40), (45, 71), (130, 256)])
+def test_half_cost_planes_match_oracle(cmf, algo, shape):
+    """costs = 2: the cost planes stored as float16.  The oracle is given the
+    same rounded costs (upcast to float64), so both solve the same problem."""
+    inst = synth.config5(*shape) if shape[1] > 200 else synth.config3(*shape)
+    C16 = inst.costs.astype(np.float16).astype(np.float32)
+    p = cmf.default_params(algo, inst.L, costs=2)
+    s = cmf.alloc_potts(inst, p)
+    assert s.C.dtype == torch.float16
+    cmf.cmf_init_potts(s)
+    cmf.cmf_iterate_potts(s, 21)
+    got = s.state()
+    po = O.default_params(algo, inst.L)
+    ref = O.potts_run(C16, inst.alpha, po, 21)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        assert np.abs(got[k] - ref[k]).max() <= TOL_U, k
+    E, D, gap, res = cmf.cmf_eval_potts(s)
+    Eo, Do, gapo, reso = O.potts_eval(C16, inst.alpha, got, po)
+    assert abs(E - Eo) <= 1e-5 * abs(Eo) and abs(D - Do) <= 1e-5 * abs(Eo)
