@@ -56,11 +56,24 @@ def default_params(algo: int, L: int = 2, **kw) -> Params:
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
+    """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree),
+    with OpenMP for its element-wise loops where the compiler has it (the
+    results do not depend on the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared",
-                               "-fPIC", "-o", _LIB, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                "-o", _LIB, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's element-wise loops (n < 1 keeps the current
+    setting); returns the count in use (1 without OpenMP)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 _lib = None
@@ -77,6 +90,8 @@ def lib():
         L.orc_div.argtypes = [i, i, dp, dp, dp]
         L.orc_project_alpha.argtypes = [ctypes.c_size_t, dp, dp, dp, i]
         L.orc_srbgs.argtypes = [i, i, ctypes.c_double, ctypes.c_double, dp, dp, i]
+        L.orc_set_threads.argtypes = [i]
+        L.orc_set_threads.restype = i
         L.orc_simplex.argtypes = [i, dp, dp]
         L.orc_simplex.restype = i
         L.orc_binary_init.argtypes = [i, i, dp, dp, i, ctypes.c_double, dp, dp, dp, dp, dp]

@@ -64,7 +64,32 @@ typedef struct {
 
 #define AT(a, i, j) ((a)[(size_t)(i) * (size_t)W + (size_t)(j)])
 
+/* Element-wise loops (each iteration writes only its own elements) may run on
+ * several threads when the oracle is built with OpenMP; results are the same
+ * for any thread count.  Sums stay sequential. */
+#ifdef _OPENMP
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define ORC_PAR_FOR(n) ORC_PRAGMA(omp parallel for schedule(static) if ((n) > 32768))
+#else
+#define ORC_PAR_FOR(n)
+#endif
+
 static double *dalloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(double)); }
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+/* Threads for the element-wise loops (n < 1: leave the setting alone);
+ * returns the number that will be used (1 without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Discrete operators                                                        */
@@ -73,6 +98,7 @@ static double *dalloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(doub
 /* grad g = (g(i,j+1)-g(i,j), g(i+1,j)-g(i,j)); 0 where the neighbour is
  * outside the grid. */
 void orc_grad(int H, int W, const double *g, double *gx, double *gy) {
+    ORC_PAR_FOR((size_t)H * W)
     for (int i = 0; i < H; ++i)
         for (int j = 0; j < W; ++j) {
             AT(gx, i, j) = (j < W - 1) ? AT(g, i, j + 1) - AT(g, i, j) : 0.0;
@@ -85,6 +111,7 @@ void orc_grad(int H, int W, const double *g, double *gx, double *gy) {
  * that end there; components that grad never produces (the far-boundary
  * ones) do not contribute. */
 void orc_div(int H, int W, const double *qx, const double *qy, double *d) {
+    ORC_PAR_FOR((size_t)H * W)
     for (int i = 0; i < H; ++i)
         for (int j = 0; j < W; ++j) {
             double v = 0.0;
@@ -100,12 +127,14 @@ void orc_div(int H, int W, const double *qx, const double *qy, double *d) {
  * reads like (I - (1/a) div^* div) q in the paper. */
 static void orc_div_adjoint(int H, int W, const double *w, double *ox, double *oy) {
     orc_grad(H, W, w, ox, oy);
+    ORC_PAR_FOR((size_t)H * W)
     for (size_t k = 0; k < (size_t)H * W; ++k) { ox[k] = -ox[k]; oy[k] = -oy[k]; }
 }
 
 /* P_alpha (Eq. projections): q / max(1, |q|/alpha); alpha = 0 gives 0.
  * Anisotropic option: clamp each component to [-alpha, alpha]. */
 void orc_project_alpha(size_t n, double *qx, double *qy, const double *alpha, int aniso) {
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double al = alpha[k];
         if (aniso) {
@@ -135,6 +164,7 @@ static double dmin(double x, double y) { return x < y ? x : y; }
  * iteration:quadratic:seg, Eq. pdrq:4labels). */
 static void orc_halfsweep(int H, int W, double kappa, double st, const double *b, double *u,
                           int colour) {
+    ORC_PAR_FOR((size_t)H * W)
     for (int i = 0; i < H; ++i)
         for (int j = 0; j < W; ++j) {
             if (((i + j) & 1) != colour) continue;
@@ -188,6 +218,7 @@ int orc_simplex(int n, const double *v, double *w) {
  * pbar_s = p_s + tau u.  This start is a fixed point when alpha = 0. */
 void orc_binary_init(int H, int W, const double *Cs, const double *Ct, int dr, double tau,
                      double *u, double *qx, double *qy, double *ps, double *pt) {
+    ORC_PAR_FOR((size_t)H * W)
     for (size_t k = 0; k < (size_t)H * W; ++k) {
         u[k] = Ct[k] < Cs[k] ? 1.0 : 0.0;
         qx[k] = 0.0;
@@ -196,6 +227,7 @@ void orc_binary_init(int H, int W, const double *Cs, const double *Ct, int dr, d
     }
     if (!dr) return;
     orc_grad(H, W, u, qx, qy);
+    ORC_PAR_FOR((size_t)H * W)
     for (size_t k = 0; k < (size_t)H * W; ++k) {
         qx[k] *= tau;
         qy[k] *= tau;
@@ -221,8 +253,10 @@ static void binary_admm_step(int H, int W, const double *Cs, const double *Ct, c
     orc_div(H, W, qx, qy, dq);
     orc_div_adjoint(H, W, dq, sx, sy);
     double *h = dq; /* reuse: h = p_t - p_s - u/c */
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) h[k] = pt[k] - ps[k] - u[k] / c;
     orc_grad(H, W, h, gx, gy);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         qx[k] = qx[k] - sx[k] / a + gx[k] / a;
         qy[k] = qy[k] - sy[k] / a + gy[k] / a;
@@ -232,6 +266,7 @@ static void binary_admm_step(int H, int W, const double *Cs, const double *Ct, c
     /* p^{k+1}: both p_t and p_s read p^k (Jacobi). */
     double *d = w1;
     orc_div(H, W, qx, qy, d);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double pt0 = pt[k], ps0 = ps[k];
         double pt1 = dmin(pt0 - (rho / at) * (pt0 - ps0) + (1.0 / at) * (-rho * d[k] + u[k] / c),
@@ -259,11 +294,13 @@ static void binary_dr_step(int H, int W, const double *Cs, const double *Ct, con
     const double sg = P->sigma, tau = P->tau, rho = P->rho;
     double *b = w1;
     orc_div(H, W, qbx, qby, b);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) b[k] = -sg * (b[k] + pbt[k] - pbs[k]);
     /* u^{k+1} = u^k + M^{-1}[b - T u^k], T = sigma tau (-Lap + 2I) */
     orc_srbgs(H, W, 2.0, sg * tau, b, u, P->sweeps);
     double *gx = w2, *gy = w3, *tx = w4, *ty = w5;
     orc_grad(H, W, u, gx, gy);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double q1 = qbx[k] - tau * gx[k];
         double q2 = qby[k] - tau * gy[k];
@@ -273,6 +310,7 @@ static void binary_dr_step(int H, int W, const double *Cs, const double *Ct, con
         gy[k] = q2;
     }
     orc_project_alpha(n, tx, ty, alpha, P->aniso);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double pt1 = pbt[k] + tau * u[k];
         double ps1 = pbs[k] - tau * u[k];
@@ -297,8 +335,10 @@ static void binary_ty_step(int H, int W, const double *Cs, const double *Ct, con
     orc_div(H, W, qx, qy, dq);
     orc_div_adjoint(H, W, dq, sx, sy);
     double *h = dq;
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) h[k] = pt[k] - ps[k] - u[k] / c;
     orc_grad(H, W, h, gx, gy);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         qx[k] = qx[k] - sx[k] / a + gx[k] / a;
         qy[k] = qy[k] - sy[k] / a + gy[k] / a;
@@ -306,6 +346,7 @@ static void binary_ty_step(int H, int W, const double *Cs, const double *Ct, con
     orc_project_alpha(n, qx, qy, alpha, P->aniso);
     double *d = w1;
     orc_div(H, W, qx, qy, d);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         ps[k] = dmin(pt[k] + d[k] - u[k] / c + 1.0 / c, Cs[k]);
         pt[k] = dmin(ps[k] - d[k] + u[k] / c, Ct[k]);
@@ -319,6 +360,7 @@ static void binary_cp_ubar(int H, int W, double tau, const double *u, const doub
                            const double *qy, const double *ps, const double *pt, double *ubar) {
     const size_t n = (size_t)H * W;
     orc_div(H, W, qx, qy, ubar);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) ubar[k] = u[k] - tau * (ubar[k] + pt[k] - ps[k]);
 }
 
@@ -332,16 +374,19 @@ static void binary_cp_step(int H, int W, const double *Cs, const double *Ct, con
     const double sg = P->sigma, tau = P->tau;
     double *gx = w1, *gy = w2, *d = w3;
     orc_grad(H, W, ubar, gx, gy);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         qx[k] = qx[k] - sg * gx[k];
         qy[k] = qy[k] - sg * gy[k];
     }
     orc_project_alpha(n, qx, qy, alpha, P->aniso);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         pt[k] = dmin(pt[k] + sg * ubar[k], Ct[k]);
         ps[k] = dmin(ps[k] - sg * ubar[k] + sg, Cs[k]);
     }
     orc_div(H, W, qx, qy, d);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         const double u0 = u[k];
         u[k] = u0 - tau * (d[k] + pt[k] - ps[k]);
@@ -390,6 +435,7 @@ void orc_binary_eval(int H, int W, const double *Cs, const double *Ct, const dou
     const size_t n = (size_t)H * W;
     double *ub = dalloc(n), *gx = dalloc(n), *gy = dalloc(n), *fx = dalloc(n), *fy = dalloc(n),
            *fs = dalloc(n), *ft = dalloc(n), *d = dalloc(n);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) ub[k] = u[k] < 0.0 ? 0.0 : (u[k] > 1.0 ? 1.0 : u[k]);
     orc_grad(H, W, ub, gx, gy);
     double E = 0.0;
@@ -399,6 +445,7 @@ void orc_binary_eval(int H, int W, const double *Cs, const double *Ct, const dou
     }
     if (dr) {
         orc_grad(H, W, u, gx, gy);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             fx[k] = qx[k] - tau * gx[k];
             fy[k] = qy[k] - tau * gy[k];
@@ -438,6 +485,7 @@ void orc_binary_eval(int H, int W, const double *Cs, const double *Ct, const dou
 void orc_potts_init(int H, int W, int L, const double *C, int dr, double tau, double *u,
                     double *qx, double *qy, double *p, double *ps) {
     const size_t n = (size_t)H * W;
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         int best = 0;
         for (int i = 1; i < L; ++i)
@@ -454,12 +502,14 @@ void orc_potts_init(int H, int W, int L, const double *C, int dr, double tau, do
     if (!dr) return;
     for (int i = 0; i < L; ++i) {
         orc_grad(H, W, u + i * n, qx + i * n, qy + i * n);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             qx[i * n + k] *= tau;
             qy[i * n + k] *= tau;
             p[i * n + k] -= tau * u[i * n + k];
         }
     }
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) ps[k] += tau; /* sum_i u_i = 1 */
 }
 
@@ -481,8 +531,10 @@ static void potts_admm_step(int H, int W, int L, const double *C, const double *
         const double *Pi = p + i * n, *Ui = u + i * n;
         orc_div(H, W, Qx, Qy, w1);
         orc_div_adjoint(H, W, w1, w2, w3);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) w1[k] = Pi[k] - ps[k] - Ui[k] / c;
         orc_grad(H, W, w1, w4, w5);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             Qx[k] = Qx[k] - w2[k] / a + w4[k] / a;
             Qy[k] = Qy[k] - w3[k] / a + w5[k] / a;
@@ -491,6 +543,7 @@ static void potts_admm_step(int H, int W, int L, const double *C, const double *
         orc_div(H, W, Qx, Qy, d + i * n);
     }
     /* p_s^{k+1} (uses p^k and p_s^k) */
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double s = 0.0;
         for (int i = 0; i < L; ++i) s += rho * d[i * n + k];
@@ -499,6 +552,7 @@ static void potts_admm_step(int H, int W, int L, const double *C, const double *
     }
     /* p_i^{k+1}, then u_i^{k+1} */
     for (int i = 0; i < L; ++i)
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             size_t ik = i * n + k;
             double p0 = p[ik];
@@ -530,8 +584,10 @@ static void potts_ty_step(int H, int W, int L, const double *C, const double *al
         const double *Pi = p + i * n, *Ui = u + i * n;
         orc_div(H, W, Qx, Qy, w1);
         orc_div_adjoint(H, W, w1, w2, w3);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) w1[k] = Pi[k] - ps[k] - Ui[k] / c;
         orc_grad(H, W, w1, w4, w5);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             Qx[k] = Qx[k] - w2[k] / a + w4[k] / a;
             Qy[k] = Qy[k] - w3[k] / a + w5[k] / a;
@@ -540,16 +596,19 @@ static void potts_ty_step(int H, int W, int L, const double *C, const double *al
         orc_div(H, W, Qx, Qy, d + i * n);
     }
     for (int i = 0; i < L; ++i)
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             size_t ik = i * n + k;
             p[ik] = dmin(ps[k] - d[ik] + u[ik] / c, C[ik]);
         }
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double s = 0.0;
         for (int i = 0; i < L; ++i) s += p[i * n + k] + d[i * n + k] - u[i * n + k] / c;
         ps[k] = s / L + 1.0 / (L * c);
     }
     for (int i = 0; i < L; ++i)
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             size_t ik = i * n + k;
             u[ik] = u[ik] - c * (p[ik] - ps[k] + d[ik]);
@@ -568,6 +627,7 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
      *       + sigma tau ((L-1) u_i - sum_{j != i} u_j)   (uses u^k) */
     for (int i = 0; i < L; ++i) {
         orc_div(H, W, qbx + i * n, qby + i * n, b + i * n);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             double others = 0.0;
             for (int j = 0; j < L; ++j)
@@ -579,6 +639,7 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
     /* u_i^{k+1}: sRBGS for sigma tau T_0, T_0 = -Lap + (L+1) I (Lemma 1) */
     for (int i = 0; i < L; ++i) orc_srbgs(H, W, (double)(L + 1), sg * tau, b + i * n, u + i * n,
                                           P->sweeps);
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double s = 0.0;
         for (int i = 0; i < L; ++i) s += u[i * n + k];
@@ -588,6 +649,7 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
         double *Ui = u + i * n, *Qx = qbx + i * n, *Qy = qby + i * n, *Pb = pb + i * n;
         const double *Ci = C + i * n;
         orc_grad(H, W, Ui, w1, w2);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             double q1 = Qx[k] - tau * w1[k];
             double q2 = Qy[k] - tau * w2[k];
@@ -597,6 +659,7 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
             w2[k] = q2;
         }
         orc_project_alpha(n, w3, w4, alpha, P->aniso);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             double p1 = Pb[k] + tau * Ui[k];
             Qx[k] = Qx[k] + rho * (w3[k] - w1[k]);
@@ -604,6 +667,7 @@ static void potts_dr_step(int H, int W, int L, const double *C, const double *al
             Pb[k] = Pb[k] + rho * (dmin(2.0 * p1 - Pb[k], Ci[k]) - p1);
         }
     }
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double ps1 = pbs[k] - tau * usum[k];
         pbs[k] = pbs[k] + rho * ((2.0 * ps1 - pbs[k] + tau) - ps1);
@@ -617,6 +681,7 @@ static void potts_cp_ubar(int H, int W, int L, double tau, const double *u, cons
     for (int i = 0; i < L; ++i) {
         double *Ub = ubar + i * n;
         orc_div(H, W, qx + i * n, qy + i * n, Ub);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k)
             Ub[k] = u[i * n + k] - tau * (Ub[k] + p[i * n + k] - ps[k]);
     }
@@ -633,13 +698,16 @@ static void potts_cp_step(int H, int W, int L, const double *C, const double *al
         double *Qx = qx + i * n, *Qy = qy + i * n, *Pi = p + i * n;
         const double *Ub = ubar + i * n, *Ci = C + i * n;
         orc_grad(H, W, Ub, w1, w2);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             Qx[k] = Qx[k] - sg * w1[k];
             Qy[k] = Qy[k] - sg * w2[k];
         }
         orc_project_alpha(n, Qx, Qy, alpha, P->aniso);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) Pi[k] = dmin(Pi[k] + sg * Ub[k], Ci[k]);
     }
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double s = 0.0;
         for (int i = 0; i < L; ++i) s += ubar[i * n + k];
@@ -648,6 +716,7 @@ static void potts_cp_step(int H, int W, int L, const double *C, const double *al
     for (int i = 0; i < L; ++i) {
         double *Ui = u + i * n, *Ub = ubar + i * n;
         orc_div(H, W, qx + i * n, qy + i * n, w3);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) {
             const double u0 = Ui[k];
             Ui[k] = u0 - tau * (w3[k] + p[i * n + k] - ps[k]);
@@ -697,8 +766,9 @@ int orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, in
     double *ub = dalloc(n * L), *gx = dalloc(n), *gy = dalloc(n), *fx = dalloc(n * L),
            *fy = dalloc(n * L), *fp = dalloc(n * L), *fs = dalloc(n), *d = dalloc(n),
            *mn = dalloc(n);
-    double v[64], w[64];
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
+        double v[64], w[64];
         for (int i = 0; i < L; ++i) v[i] = u[i * n + k];
         orc_simplex(L, v, w);
         for (int i = 0; i < L; ++i) ub[i * n + k] = w[i];
@@ -711,6 +781,7 @@ int orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, in
             E += ub[i * n + k] * C[i * n + k] + alpha[k] * tv;
         }
     }
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) {
         double s = 0.0;
         for (int i = 0; i < L; ++i) s += u[i * n + k];
@@ -719,6 +790,7 @@ int orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, in
     for (int i = 0; i < L; ++i) {
         if (dr) {
             orc_grad(H, W, u + i * n, gx, gy);
+            ORC_PAR_FOR(n)
             for (size_t k = 0; k < n; ++k) {
                 fx[i * n + k] = qx[i * n + k] - tau * gx[k];
                 fy[i * n + k] = qy[i * n + k] - tau * gy[k];
@@ -738,10 +810,12 @@ int orc_potts_eval(int H, int W, int L, const double *C, const double *alpha, in
             res += rr * rr;
         }
     }
+    ORC_PAR_FOR(n)
     for (size_t k = 0; k < n; ++k) mn[k] = INFINITY;
     for (int i = 0; i < L; ++i) {
         orc_project_alpha(n, fx + i * n, fy + i * n, alpha, aniso);
         orc_div(H, W, fx + i * n, fy + i * n, d);
+        ORC_PAR_FOR(n)
         for (size_t k = 0; k < n; ++k) mn[k] = dmin(mn[k], C[i * n + k] + d[k]);
     }
     double D = 0.0;
