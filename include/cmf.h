@@ -166,6 +166,29 @@ typedef struct {
                           scheduled iterations from the host, one launch per
                           iteration, and the rest as usual.              */
     int rho_schedule_len;
+    int phase_storage; /* cmf_solve_potts only (no counterpart in the paper; a
+                          storage schedule): 0 = off; CMF_F16 or CMF_BF16 = a
+                          two-phase solve.  p->storage must be CMF_F32 (the
+                          caller's buffers) and the solve starts cold.  Phase
+                          one runs in phase_storage (flows q_i, p_i in 16 bits;
+                          u, p_s float32) in state sets inside the workspace
+                          until the certified gap is <= phase_gap; the state
+                          is then written exactly into the caller's float32
+                          buffers and phase two continues in float32 to
+                          tol_gap.  Iteration counts and history rows run on
+                          across the switch; phase one alone may use up
+                          max_iter.  16-bit flows cannot certify arbitrarily
+                          small gaps (rounding of q_i and p_i holds the
+                          16-label 4096^2 workload near 3e-4 in float16,
+                          near 3e-3 in bfloat16): phase_gap must lie above
+                          that floor and above tol_gap.                    */
+    double phase_gap;
+    int tune_step;     /* cmf_autotune_*: 0 = launch configurations only; 1 =
+                          also the ADMM step size c of pADMMI, rpADMMI,
+                          rpADMMII and pADMM-TY (candidates c, 2c, 4c, 8c
+                          with the given kernel variant; Sec. 4 takes c = 0.3,
+                          and any c > 0 keeps the convergence results of Thm 1
+                          and Thm 2).  Other algorithms ignore it.           */
 } cmf_params;
 
 /* Fill *p with the paper's defaults for `algo` and L labels (L = 2 for the
@@ -331,9 +354,10 @@ cmf_status cmf_solve_potts(const float *d_C, int L, const float *d_alpha, float 
 /* Autotuning (no counterpart in the paper: a launch-configuration search).  */
 /* Solves the problem from a cold start once per candidate configuration --  */
 /* the kernel variant (1, 2, 4 (binary), 8, 16, 32) of the fused ADMM       */
-/* algorithms, or the                                                        */
-/* sRBGS sweep count (1, 2, 3) of fused rPDRQ -- with everything else taken  */
-/* from *p, and writes the candidate with the shortest time to p->tol_gap    */
+/* algorithms, or the sRBGS sweep count (1, 2, 3) of fused rPDRQ, and with   */
+/* p->tune_step = 1 the ADMM step size c (c, 2c, 4c, 8c) -- with everything  */
+/* else taken from *p, and writes the candidate with the shortest time to   */
+/* p->tol_gap                                                               */
 /* (CUDA events on `stream`, best of two runs after a warm-up) to *best and  */
 /* its time in milliseconds to *h_best_ms (host, may be NULL).  The state    */
 /* buffers are overwritten (they hold the last trial's solution).  Returns  */

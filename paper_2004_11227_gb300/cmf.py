@@ -43,6 +43,8 @@ class Params(ctypes.Structure):
         ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("tol_gap", ctypes.c_double),
         ("costs", ctypes.c_int),
         ("rho_schedule", ctypes.POINTER(ctypes.c_double)), ("rho_schedule_len", ctypes.c_int),
+        ("phase_storage", ctypes.c_int), ("phase_gap", ctypes.c_double),
+        ("tune_step", ctypes.c_int),
     ]
 
     def set_rho_schedule(self, rhos) -> "Params":
@@ -459,15 +461,16 @@ def cmf_autotune_potts(s: Potts, stream=None):
 
 def tuned_params(problem, cache_path: str | None = None) -> Params:
     """Autotuned parameters for a Binary / Potts container, cached in a JSON
-    file keyed by (model, H, W, L, storage, algo, impl, SM count, device)."""
+    file keyed by (model, H, W, L, storage, algo, impl, tune_step, c, SM
+    count, device)."""
     import json
 
     p = problem.params
     props = torch.cuda.get_device_properties(problem.u.device)
     key = "|".join(str(v) for v in (
         "binary" if isinstance(problem, Binary) else "potts", problem.H, problem.W,
-        getattr(problem, "L", 2), p.storage, p.algo, p.impl, props.multi_processor_count,
-        props.name))
+        getattr(problem, "L", 2), p.storage, p.algo, p.impl, p.tune_step, p.c,
+        props.multi_processor_count, props.name))
     path = cache_path or os.environ.get(
         "CMF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cmf_tune.json"))
     try:
@@ -480,14 +483,15 @@ def tuned_params(problem, cache_path: str | None = None) -> Params:
     q._rho_keep = getattr(p, "_rho_keep", None)  # the copied schedule pointer
     if key in cache:
         q.variant, q.sweeps = cache[key]["variant"], cache[key]["sweeps"]
+        q.c = cache[key].get("c", q.c)
         return q
     if isinstance(problem, Binary):
         best, ms = cmf_autotune_binary(problem)
     else:
         best, ms = cmf_autotune_potts(problem)
-    cache[key] = {"variant": best.variant, "sweeps": best.sweeps, "ms_to_gap": ms}
+    cache[key] = {"variant": best.variant, "sweeps": best.sweeps, "c": best.c, "ms_to_gap": ms}
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     with open(path, "w") as f:
         json.dump(cache, f, indent=1)
-    q.variant, q.sweeps = best.variant, best.sweeps
+    q.variant, q.sweeps, q.c = best.variant, best.sweeps, best.c
     return q

@@ -20,6 +20,8 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Workspace regions (offsets from the workspace base).
 struct WsLayout {
+    size_t phase;     // two state sets in phase_storage (two-phase Potts solves)
+    size_t phase_set; // bytes of one of them
     size_t state;     // second state buffer set (ping-pong of the fused form)
     size_t state2;    // third set (binary fused form: routes two-iteration launches)
     size_t tmp;       // float planes used by the plain form
@@ -43,6 +45,13 @@ WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool pot
                              : align_up(plane * 4) + 4 * align_up(plane * es);
     WsLayout w;
     size_t off = 0;
+    w.phase = off;
+    w.phase_set = 0;
+    if (potts && p.phase_storage != 0) {
+        const size_t ep = dtype_size(p.phase_storage);
+        w.phase_set = align_up(plane * 4 * L) + 3 * align_up(plane * ep * L) + align_up(plane * 4);
+        off += 2 * w.phase_set;
+    }
     w.state = off;
     off += set;
     w.state2 = off;
@@ -86,6 +95,13 @@ cmf_status check_params(const cmf_params* p, int L) {
         p->variant != 8 && p->variant != 16 && p->variant != 32)
         return CMF_EINVAL;
     if (p->costs < 0 || p->costs > 2) return CMF_EINVAL;
+    if (p->tune_step != 0 && p->tune_step != 1) return CMF_EINVAL;
+    // two-phase Potts solves: a 16-bit first phase, the caller's buffers float32
+    if (p->phase_storage < 0 || p->phase_storage > CMF_BF16) return CMF_EINVAL;
+    if (p->phase_storage != 0 &&
+        (p->storage != CMF_F32 || !(p->phase_gap > p->tol_gap) || p->rho_schedule_len != 0 ||
+         p->warm_start != 0))
+        return CMF_EINVAL;
     // relaxation schedule {rho_k}: non-decreasing in (0, 2) (Thm 1, Thm 2),
     // continued by rho, for the two relaxed algorithms only
     if (p->rho_schedule_len < 0) return CMF_EINVAL;
@@ -201,6 +217,7 @@ cmf_status binary_prepare(const float* Cs, const float* Ct, const float* alpha, 
     cmf_status s;
     if ((s = check_params(p, 2)) != CMF_OK) return s;
     if (p->costs != 0) return CMF_EINVAL;  // binary costs are planes
+    if (p->phase_storage != 0) return CMF_EINVAL;  // two-phase solves: Potts only
     if ((s = check_grid(H, W, pitch)) != CMF_OK) return s;
     if (!Cs || !Ct || !u || !qx || !qy || !ps || !pt || !ws) return CMF_EINVAL;
     if (!alpha && !(alpha0 >= 0.0f && isfinite(alpha0))) return CMF_EINVAL;
@@ -398,10 +415,10 @@ cmf_status binary_eval_state(const BinaryCall& c, const BinStateV& s, double* h_
 
 // ---- Potts ----------------------------------------------------------------
 
-PottsStateV ws_potts_state(char* ws, const WsLayout& w, const Grid& G, int L, int storage) {
+PottsStateV ws_potts_state(char* ws, size_t off, const Grid& G, int L, int storage) {
     const size_t plane = G.plane;
     const size_t es = dtype_size(storage);
-    char* base = ws + w.state;
+    char* base = ws + off;
     PottsStateV s;
     s.u = (float*)base;
     base += align_up(plane * 4 * L);
@@ -447,9 +464,12 @@ struct PottsCall {
     int* err;                    // sticky device error word
 };
 
+// `layout`: the parameters the workspace was sized for (default *p); `set`:
+// the second state set (default: the workspace's own, in p->storage).
 cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0, int H, int W,
                          int pitch, const cmf_params* p, float* u, void* qx, void* qy, void* pp,
-                         void* ps, void* ws, size_t ws_bytes, PottsCall& call) {
+                         void* ps, void* ws, size_t ws_bytes, PottsCall& call,
+                         const cmf_params* layout = nullptr, const PottsStateV* set = nullptr) {
     cmf_status s;
     if (L < 2 || L > 64) return CMF_EINVAL;
     if ((s = check_params(p, L)) != CMF_OK) return s;
@@ -462,12 +482,12 @@ cmf_status potts_prepare(const float* C, int L, const float* alpha, float alpha0
     if (!aligned(qx, es) || !aligned(qy, es) || !aligned(pp, es) || !aligned(ps, 4))
         return CMF_EINVAL;
     if (!aligned(ws, kAlign)) return CMF_EINVAL;
-    call.w = ws_layout(H, W, L, pitch, *p, true);
+    call.w = ws_layout(H, W, L, pitch, layout ? *layout : *p, true);
     if (ws_bytes < call.w.total) return CMF_ENOMEM;
     call.P = potts_problem(C, L, alpha, alpha0, H, W, pitch, p->costs);
     call.user = PottsStateV{u, qx, qy, pp, (float*)ps};
     call.wsbase = (char*)ws;
-    call.ws = ws_potts_state(call.wsbase, call.w, call.P.g, L, p->storage);
+    call.ws = set ? *set : ws_potts_state(call.wsbase, call.w.state, call.P.g, L, p->storage);
     call.cfg = make_step(*p, L, true);
     call.prm = *p;
     call.storage = p->storage;
@@ -639,6 +659,9 @@ SolveSig make_sig(int model, int L, int H, int W, int pitch, float alpha0,
     k.p.tau = p.tau;
     k.p.tol_gap = p.tol_gap;
     k.p.costs = p.costs;
+    k.p.phase_storage = p.phase_storage;
+    k.p.phase_gap = p.phase_gap;
+    k.p.tune_step = p.tune_step;
     return k;
 }
 
@@ -884,11 +907,16 @@ cmf_status finish_loop(const LoopState& ls, Copy copy_back, int* h_iters, cudaSt
 // rest in the device-driven graph where it applies, else host-driven.
 // `chunk(stream, from, to, tail)` captures one graph chunk with its
 // certificates, `end_of(from)` tells the set a chunk ends in.
+// it0, nh0: iterations and history rows an earlier phase of the same solve
+// has already done (the loop continues their count; max_iter is the total).
 template <typename RunCert, typename Copy, typename Chunk, typename EndOf>
 cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
                         RunCert run_cert, Copy copy_back, Chunk chunk, EndOf end_of,
-                        double* h_hist, int hist_cap, int* h_iters, cudaStream_t st) {
+                        double* h_hist, int hist_cap, int* h_iters, cudaStream_t st,
+                        int it0 = 0, int nh0 = 0) {
     LoopState ls;
+    ls.it = it0;
+    ls.nh = nh0;
     if (!graph_eligible(*p)) {
         cmf_status s = loop_chunks(p, p->max_iter, run_cert, h_hist, hist_cap, ls);
         if (s != CMF_OK) return s;
@@ -1110,8 +1138,59 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
     if (hist_cap < 0) return CMF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     CMF_CUDA_TRY(cudaMemsetAsync(c.err, 0, sizeof(int), st));
-    if (!p->warm_start)
+    int it0 = 0, nh0 = 0;
+    if (p->phase_storage != 0) {
+        // phase one: the same solve in 16-bit flow storage, in the
+        // workspace's two phase sets, to the switch gap
+        cmf_params q = *p;
+        q.storage = p->phase_storage;
+        q.tol_gap = p->phase_gap;
+        q.phase_storage = 0;
+        q.phase_gap = 0.0;
+        const Grid G = make_grid(H, W, pitch);
+        const PottsStateV A = ws_potts_state((char*)d_ws, c.w.phase, G, L, q.storage);
+        const PottsStateV B =
+            ws_potts_state((char*)d_ws, c.w.phase + c.w.phase_set, G, L, q.storage);
+        PottsCall c1;
+        s = potts_prepare(d_C, L, d_alpha, alpha0, H, W, pitch, &q, A.u, A.qx, A.qy, A.p, A.ps,
+                          d_ws, ws_bytes, c1, p, &B);
+        if (s != CMF_OK) return s;
+        CMF_CUDA_TRY(potts_init(c1.storage, c1.P, c1.user, c1.cfg.dr, c1.cfg.dc.tau, st));
+        const SolveSig sig1 = make_sig(2, L, H, W, pitch, alpha0, {d_C, d_alpha, d_ws}, q);
+        int it1 = 0;
+        s = solve_driver(
+            &q, sig1, c1.wsbase, c1.w,
+            [&](int n, int& cur, int k0, double* out) -> cmf_status {
+                const EvalTail T = reduce_tail(c1.wsbase, c1.w);
+                CMF_CUDA_TRY(cudaMemsetAsync(&T.ctl->arrive, 0, sizeof(unsigned), st));
+                CMF_CUDA_TRY(potts_run(c1, n, cur, st, k0, &T));
+                return finish_eval(c1.wsbase, c1.w, out, st);
+            },
+            [&](int) { return copy_potts(c1.user, c1.ws, c1.P.g, L, c1.storage, st); },
+            [&](cudaStream_t s2, int from, int& to, const EvalTail& T) {
+                to = from;
+                return potts_run(c1, q.check_every, to, s2, 0, &T);
+            },
+            [&](int from) {
+                int to = from;
+                potts_run(c1, q.check_every, to, nullptr, 0, nullptr, true);
+                return to;
+            },
+            h_hist, hist_cap, &it1, st);
+        if (s != CMF_OK && s != CMF_NOT_CONVERGED) return s;
+        // the switch: the 16-bit state written exactly into the caller's
+        // float32 buffers; phase two continues from it
+        CMF_CUDA_TRY(potts_widen(q.storage, G, L, A, c.user, st));
+        it0 = it1;
+        nh0 = it1 / p->check_every;
+        if (it0 >= p->max_iter) {
+            CMF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (h_iters) *h_iters = it0;
+            return CMF_NOT_CONVERGED;
+        }
+    } else if (!p->warm_start) {
         CMF_CUDA_TRY(potts_init(c.storage, c.P, c.user, c.cfg.dr, c.cfg.dc.tau, st));
+    }
     const SolveSig sig = make_sig(1, L, H, W, pitch, alpha0,
                                   {d_C, d_alpha, d_u, d_qx, d_qy, d_p, d_ps, d_ws}, *p);
     return solve_driver(
@@ -1132,7 +1211,7 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
             potts_run(c, p->check_every, to, nullptr, p->rho_schedule_len, nullptr, true);
             return to;
         },
-        h_hist, hist_cap, h_iters, st);
+        h_hist, hist_cap, h_iters, st, it0, nh0);
 }
 
 }  // extern "C"
@@ -1158,6 +1237,16 @@ std::vector<cmf_params> tune_candidates(const cmf_params& p, bool binary) {
             cmf_params q = p;
             q.variant = v;
             q.sweeps = s;
+            q.warm_start = 0;
+            out.push_back(q);
+        }
+    // the ADMM step size (tune_step): larger c with the given variant
+    const bool admm = p.algo == CMF_PADMM || p.algo == CMF_RPADMM_FG ||
+                      p.algo == CMF_RPADMM_EB || p.algo == CMF_TY;
+    if (p.tune_step == 1 && admm)
+        for (double f : {2.0, 4.0, 8.0}) {
+            cmf_params q = p;
+            q.c = p.c * f;
             q.warm_start = 0;
             out.push_back(q);
         }

@@ -180,6 +180,7 @@ cmf_status check_batch_params(const cmf_params* p) {
     if (!p) return CMF_EINVAL;
     if (p->algo < CMF_PADMM || p->algo > CMF_CP) return CMF_EINVAL;
     if (p->costs != 0) return CMF_EINVAL;  // batches take cost planes
+    if (p->phase_storage != 0) return CMF_EINVAL;  // two-phase solves: single Potts solves only
     if (p->rho_schedule_len != 0) return CMF_EINVAL;  // one rho for every instance
     if (p->storage < CMF_F32 || p->storage > CMF_BF16) return CMF_EINVAL;
     if (p->impl != CMF_FUSED) return CMF_EINVAL;  // the batch runs the fused kernels

@@ -316,6 +316,9 @@ int eval_blocks(int H, int W);
 // --- launchers (Potts) ---
 cudaError_t potts_init(int storage, const PottsProblem& P, const PottsStateV& s, bool dr,
                        float tau, cudaStream_t st);
+// State set a (flows in `storage`) copied into float32 state set b.
+cudaError_t potts_widen(int storage, const Grid& G, int L, const PottsStateV& a,
+                        const PottsStateV& b, cudaStream_t st);
 cudaError_t potts_step(int storage, const PottsProblem& P, const PottsStateV& a,
                        const PottsStateV& b, const StepConfig& cfg, float* tmp, cudaStream_t st);
 cudaError_t potts_eval(int storage, const PottsProblem& P, const PottsStateV& s, bool aniso,

@@ -63,6 +63,27 @@ __global__ void k_potts_init(PottsProblem P, PottsState<S> s, float tau) {
 }
 
 // ---------------------------------------------------------------------------
+// The state of one storage type written into float32 planes (the switch of a
+// two-phase solve from 16-bit to float32 storage): every value is exact in
+// float32, so the iteration continues from the same state.
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void k_potts_widen(Grid G, int L, PottsState<S> a, PottsState<float> b) {
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int r = blockIdx.y * 8 + threadIdx.y;
+    if (r >= G.H || c >= G.W) return;
+    const size_t k = G.idx(r, c);
+    for (int i = 0; i < L; ++i) {
+        const size_t ki = (size_t)i * G.plane + k;
+        b.u[ki] = a.u[ki];
+        b.qx[ki] = Store<S>::ld(a.qx + ki);
+        b.qy[ki] = Store<S>::ld(a.qy + ki);
+        b.p[ki] = Store<S>::ld(a.p + ki);
+    }
+    b.ps[k] = a.ps[k];
+}
+
+// ---------------------------------------------------------------------------
 // Fused ADMM iteration.  Per label i the tile computes
 //   g_i = div q_i^k + p_i^k - p_s^k - u_i^k / c            (halo of 1)
 //   q_i^{k+1} = P_alpha(q_i^k + (1/a) grad g_i)
@@ -563,6 +584,24 @@ static cudaError_t potts_init_s(const PottsProblem& P, const PottsStateV& sv, bo
     const PottsState<S> s = sv.as<S>();
     if (dr) k_potts_init<S, true><<<pgrid(P.g, 8), dim3(32, 8), 0, st>>>(P, s, tau);
     else k_potts_init<S, false><<<pgrid(P.g, 8), dim3(32, 8), 0, st>>>(P, s, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t potts_widen(int storage, const Grid& G, int L, const PottsStateV& a,
+                        const PottsStateV& b, cudaStream_t st) {
+    const dim3 grid((G.W + 31) / 32, (G.H + 7) / 8);
+    const PottsState<float> B = b.as<float>();
+    switch (storage) {
+        case CMF_F16:
+            k_potts_widen<__half><<<grid, dim3(32, 8), 0, st>>>(G, L, a.as<__half>(), B);
+            break;
+        case CMF_BF16:
+            k_potts_widen<__nv_bfloat16>
+                <<<grid, dim3(32, 8), 0, st>>>(G, L, a.as<__nv_bfloat16>(), B);
+            break;
+        default:
+            k_potts_widen<float><<<grid, dim3(32, 8), 0, st>>>(G, L, a.as<float>(), B);
+    }
     return cudaGetLastError();
 }
 

@@ -190,3 +190,44 @@ def test_levels_container_leaves_callers_params_alone(cmf):
     assert p.costs == 0 and s.params.costs == 1
     assert s.params.rho_schedule_len == 2 and s.params.rho_schedule[1] == 1.5
     assert s.C.numel() == 4 * s.pitch + 3
+
+
+def test_params_mirror_has_the_c_size(cmf):
+    """cmf_default_params clears sizeof(cmf_params) bytes: the bytes right after
+    the ctypes mirror must stay untouched, and the last field must be set."""
+    n = ctypes.sizeof(cmf.Params)
+    buf = (ctypes.c_ubyte * (n + 64))(*([0xAB] * (n + 64)))
+    assert cmf.lib().cmf_default_params(2, 4, ctypes.cast(buf, ctypes.c_void_p)) == cmf.OK
+    assert bytes(buf[n:]) == b"\xab" * 64
+    p = cmf.Params.from_buffer_copy(bytes(buf[:n]))
+    assert p.phase_storage == 0 and p.phase_gap == 0.0 and p.a2 == 8.0
+
+
+def test_two_phase_parameters_validated(cmf):
+    """A two-phase solve needs float32 buffers, a 16-bit first phase, a switch
+    gap above the tolerance, a cold start and no relaxation schedule; binary
+    solves have no two-phase form."""
+    lib = cmf.lib()
+    ptr = ctypes.c_void_p(256)
+    hist = (ctypes.c_double * 10)()
+    it = ctypes.c_int(0)
+
+    def potts(**kw):
+        q = cmf.default_params(cmf.RPADMM_EB, 4, **kw)
+        return lib.cmf_solve_potts(ptr, 4, None, 0.5, 8, 8, 8, ctypes.byref(q), ptr, ptr, ptr,
+                                   ptr, ptr, hist, 2, ctypes.byref(it), ptr, 1 << 30, None)
+
+    for bad in [dict(phase_storage=1, phase_gap=1e-4),            # not above tol_gap
+                dict(phase_storage=1, phase_gap=2e-3, storage=1),  # buffers not float32
+                dict(phase_storage=3, phase_gap=2e-3),
+                dict(phase_storage=1, phase_gap=2e-3, warm_start=1),
+                dict(phase_storage=2, phase_gap=2e-3, rho_schedule=[1.5])]:
+        assert potts(**bad) == cmf.EINVAL, bad
+    q = cmf.default_params(cmf.RPADMM_EB, 2, phase_storage=1, phase_gap=2e-3)
+    assert lib.cmf_solve_binary(ptr, ptr, None, 0.5, 8, 8, 8, ctypes.byref(q), ptr, ptr, ptr,
+                                ptr, ptr, hist, 2, ctypes.byref(it), ptr, 1 << 30,
+                                None) == cmf.EINVAL
+    # the workspace grows by the two 16-bit phase sets
+    p0 = cmf.default_params(cmf.RPADMM_EB, 4)
+    p1 = cmf.default_params(cmf.RPADMM_EB, 4, phase_storage=1, phase_gap=2e-3)
+    assert cmf.cmf_workspace_bytes(64, 64, 4, 64, p1) > cmf.cmf_workspace_bytes(64, 64, 4, 64, p0)

@@ -460,3 +460,56 @@ def test_half_cost_planes_match_oracle(cmf, algo, shape):
     E, D, gap, res = cmf.cmf_eval_potts(s)
     Eo, Do, gapo, reso = O.potts_eval(C16, inst.alpha, got, po)
     assert abs(E - Eo) <= 1e-5 * abs(Eo) and abs(D - Do) <= 1e-5 * abs(Eo)
+
+
+@pytest.mark.parametrize("phase_storage,switch", [(1, 2e-3), (2, 1e-2)])
+def test_two_phase_solve(cmf, phase_storage, switch):
+    """phase_storage: the solve runs in 16-bit flows to the switch gap, then
+    in float32 from exactly that state.  Phase one equals the 16-bit solve
+    to the switch gap row for row; phase two equals a float32 warm start from
+    its state row for row; the result is certified by the oracle."""
+    inst = synth.config5(96, 128)
+    tol = 1e-4
+    kw = dict(max_iter=20000, check_every=10)
+    p16 = cmf.default_params(2, 16, storage=phase_storage, tol_gap=switch, **kw)
+    a = cmf.alloc_potts(inst, p16)
+    st_a, it_a, h_a = cmf.cmf_solve_potts(a)
+    assert st_a == cmf.OK and h_a[-1, 3] <= switch
+    p32 = cmf.default_params(2, 16, tol_gap=tol, warm_start=1, **kw)
+    c = cmf.alloc_potts(inst, p32)
+    c.load_state(a.state())  # 16-bit values are exact in float32
+    st_c, it_c, h_c = cmf.cmf_solve_potts(c)
+    p = cmf.default_params(2, 16, tol_gap=tol, phase_storage=phase_storage, phase_gap=switch, **kw)
+    b = cmf.alloc_potts(inst, p)
+    st_b, it_b, h_b = cmf.cmf_solve_potts(b)
+    assert st_b == cmf.OK == st_c and it_b == it_a + it_c
+    np.testing.assert_array_equal(h_b[:len(h_a)], h_a)
+    np.testing.assert_array_equal(h_b[len(h_a):, 1:], h_c[:, 1:])
+    np.testing.assert_array_equal(h_b[len(h_a):, 0], h_c[:, 0] + it_a)
+    got = b.state()
+    for k in ("u", "qx", "qy", "p", "ps"):
+        np.testing.assert_array_equal(got[k], c.state()[k])
+    E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, got, O.default_params(2, 16))
+    assert gap <= 1.001e-4
+
+
+def test_autotune_step_size(cmf, tmp_path):
+    """tune_step = 1 adds the ADMM step sizes c, 2c, 4c, 8c to the search.  The
+    tuned c is a parameter of the same method: the GPU iterates with it match
+    the oracle run with the same c, and its solve is certified by the oracle."""
+    inst = synth.config5(64, 96)
+    p = cmf.default_params(2, 16, tol_gap=1e-4, max_iter=8000, check_every=10, tune_step=1)
+    s = cmf.alloc_potts(inst, p)
+    best, ms = cmf.cmf_autotune_potts(s)
+    assert ms > 0 and any(abs(best.c - 0.3 * f) < 1e-12 for f in (1, 2, 4, 8))
+    q = cmf.tuned_params(s, cache_path=str(tmp_path / "tune.json"))
+    assert abs(q.c - best.c) < 1e-12
+    g = _gpu_run(cmf, inst, 2, 25, c=best.c)
+    ref, _ = _oracle_run(inst, 2, 25, c=best.c)
+    for k in ("u", "qx", "qy", "p", "ps"):
+        assert np.abs(g.state()[k] - ref[k]).max() <= TOL_U, k
+    t = cmf.alloc_potts(inst, q)
+    st, it, hist = cmf.cmf_solve_potts(t)
+    assert st == cmf.OK
+    E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, t.state(), O.default_params(2, 16))
+    assert gap <= 1.001e-4
