@@ -1,19 +1,29 @@
 #!/usr/bin/env python
 """Benchmark: continuous max-flow segmentation on GB300.
 
-Workload: the binary model on a 1024 x 1024 image of eight random disks /
-rectangles (0.8 on 0.2, noise sigma 0.15), edge-weighted alpha(x) =
-0.5 exp(-10 |grad I|), costs C_s = |I - 0.2|, C_t = |I - 0.8|.  One step = one
-solve from a cold start to a relative primal-dual gap <= 1e-4 (certificates
-every 10 iterations) with the fused float32 rpADMMII solver.
+Headline workload: the 16-label Potts model on a 4096 x 4096 image (Voronoi
+partition of 512 seeds, 16 grey levels i/15, noise sigma 0.05), costs
+C_i = (I - c_i)^2, edge-weighted alpha(x) = 0.3 exp(-10 |grad I|).  One step =
+one solve from a cold start to a relative primal-dual gap <= 1e-4
+(certificates every 50 iterations) with the fused rpADMMII solver in two
+phases: flows q_i and p_i stored as float16 until the certified gap is 2e-3,
+then float32 (16-bit rounding of q_i and p_i holds this workload's gap near
+3e-4); p_s, u and the arithmetic are float32, the certificates double-float /
+FP64.
 
-Metric: pixel*label*iterations per second (binary counts as L = 2), plus the
-time to the 1e-4 gap of the fused solver and of the plain one-kernel-per-step
-form.  The L2 cache (129 MB) is flushed before every timed step.
+Metric: pixel*label*iterations per second, plus the time to the 1e-4 gap
+(fused vs the plain one-kernel-per-step form, float16 vs float32 flows).  The
+inputs and state (several GB) are far larger than the 129 MB L2.
+
+Side measurements on the same JSON line: the binary 1024^2 workload (its
+state stays in L2: bound "l2"), the 4-label 2048^2 workload in float32,
+float16 and bfloat16 storage, the 256-instance batch, the FP64 oracle's error
+against the GPU results, and the oracle's own speed on one host core and on
+all of them.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun every rank solves its own instance (seed 2 + rank): weak scaling,
-no collective on the data path.
+Under torchrun every rank solves its own instance (seed 5 + rank): weak
+scaling, no collective on the data path.
 """
 from __future__ import annotations
 
@@ -31,13 +41,25 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-H = W = 1024
-L = 2
+H = W = 4096
+L = 16
 TOL = 1e-4
-CHECK_EVERY = 10
-FLAGSHIP = 2          # rpADMMII (fewest iterations to the gap on this workload)
-BYTES_PER_PX = 52     # 10 state floats r+w, C_s, C_t, alpha: algorithmic bytes / pixel / iteration
-WORKLOAD = "binary 1024x1024 shapes, edge-weighted alpha, solve to gap 1e-4"
+FLAGSHIP = 2          # rpADMMII
+STORAGE = 0           # the caller's state buffers: float32
+PHASE_STORAGE = 1     # first phase in float16 flows (q_i, p_i), inside the workspace
+PHASE_GAP = 2e-3      # switch to float32 storage at this certified gap
+COSTS = 0             # cost planes as given (float32)
+CHECK_EVERY = 50      # a 16-label certificate launch costs about 1.7 iterations
+CHECK_SIDE = 10       # the side workloads check every 10 iterations
+MAX_ITER = 12000
+# Algorithmic bytes of one iteration of this workload counted with every
+# stored field in 16 bits: L (8 s + s_c) + 2 s + 4 with s = s_c = 2 (u, q_i,
+# p_i and p_s read and written once, the costs and the alpha field read once):
+# 296 B per pixel.  The solver keeps u and p_s in float32 and reads float32
+# cost planes (design_bytes_per_px below).
+BYTES_PER_PX_16BIT = 296
+WORKLOAD = ("potts L=16 4096x4096 Voronoi (512 seeds), edge-weighted alpha, float16 flows "
+            "to gap 2e-3 then float32, solve to gap 1e-4")
 
 
 def _dist():
@@ -141,36 +163,86 @@ def _traffic(kernel_src: str, kernel_name: str):
         return None
 
 
-def cpu_oracle_rate(inst, n_iter: int):
-    """The FP64 oracle (single-threaded C) on a bounded sample: n_iter
-    rpADMMII iterations of the full workload; returns px*label*it/s."""
+def rank_instance(rank: int, n: int = H):
+    """The headline instance of one rank: replicas solve their own seeds."""
+    from paper_2004_11227_gb300 import synth
+
+    return synth.config5(n, n, seed=5 + rank)
+
+
+def algorithmic_bytes_per_px(model: str, L: int, storage: int, alpha_field: bool,
+                             costs: str = "f32") -> int:
+    """State read and written once, costs and alpha read once (halos and
+    recomputed values excluded).  Binary: u float32, four flow planes in the
+    storage type.  Potts: u float32, q_i and p_i in the storage type, p_s
+    float32; costs "f32" or "f16" planes, or "levels" (one float32 image
+    plane)."""
+    s = 4 if storage == 0 else 2
+    al = 4 if alpha_field else 0
+    if model == "binary":
+        return 4 * 2 + 4 * s * 2 + 8 + al
+    c = {"f32": 4 * L, "f16": 2 * L, "levels": 4}[costs]
+    return L * (4 * 2 + 3 * s * 2) + c + 4 * 2 + al
+
+
+def _timed(fn, reps=1):
+    """Median CUDA-event time of fn() over reps calls (ms) and its last result."""
+    import torch
+
+    ts, out = [], None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), out
+
+
+def oracle_rate(inst, algo: int, n_iter: int, threads: int):
+    """The FP64 oracle on a bounded sample: n_iter iterations of `algo` from a
+    cold start on the whole instance with `threads` host threads (0: all).
+    Returns (pixel*label*iterations/s, seconds, threads used)."""
     import oracle
 
     oracle.build()
-    p = oracle.default_params(oracle.RPADMM_EB, 2)
-    t0 = time.perf_counter()
-    oracle.binary_run(inst.costs[0], inst.costs[1], inst.alpha, p, n_iter)
+    used = oracle.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
+    p = oracle.default_params(algo, inst.L)
+    alpha = inst.alpha if np.isscalar(inst.alpha) else inst.alpha.astype(np.float64)
+    if inst.kind == "binary":
+        cs, ct = (inst.costs[i].astype(np.float64) for i in range(2))
+        t0 = time.perf_counter()
+        oracle.binary_run(cs, ct, alpha, p, n_iter)
+    else:
+        c = inst.costs.astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.potts_run(c, alpha, p, n_iter)
     dt = time.perf_counter() - t0
-    return H * W * L * n_iter / dt, dt
+    return inst.H * inst.W * inst.L * n_iter / dt, dt, used
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (the paper ships no code) on the
+    headline workload, rank 0 only, all host cores, each step a bounded sample
+    of one rpADMMII iteration of the whole 4096^2 x 16 instance."""
     ws, rank = _dist()
     if rank != 0:
         return
-    from paper_2004_11227_gb300 import synth
-
-    inst = synth.config2(H, W, seed=2)
-    n_iter = 40
-    cpu_oracle_rate(inst, 2)  # build + warm the page cache
+    inst = rank_instance(0)
+    oracle_rate(inst, FLAGSHIP, 1, 0)  # build, page in
     for _ in range(args.warmup):
-        cpu_oracle_rate(inst, 2)
-    rates, times = [], []
+        oracle_rate(inst, FLAGSHIP, 1, 0)
+    rates, times, used = [], [], 1
     for _ in range(args.steps):
-        r, dt = cpu_oracle_rate(inst, n_iter)
+        r, dt, used = oracle_rate(inst, FLAGSHIP, 1, 0)
         rates.append(r)
         times.append(dt)
     value = float(np.mean(rates))
+    sample = (f"1 rpADMMII iteration of the full 4096x4096x16 workload per step, FP64 C "
+              f"oracle, {used} threads")
     line = {
         "impl": "reference", "metric": "pixel*label*iterations/s", "value": value,
         "unit": "px*label*it/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -178,9 +250,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L,
                                         "algo": "rpADMMII"},
-        "cpu_baseline": {"value": value, "unit": "px*label*it/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n_iter} rpADMMII iterations of the full 1024x1024 workload "
-                                   "per step, FP64 C oracle, one thread"},
+        "cpu_baseline": {"value": value, "unit": "px*label*it/s", "cores": used,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "px*label*it/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -202,95 +273,111 @@ KERNEL_CASES = {
     "potts4-dr-2048": ("potts", 3, 2048, 2048, 4, 0, 0),
     "potts16-admm-2048-f16": ("potts", 2, 2048, 2048, 16, 1, 0),
     "potts16-admm-4096-f16": ("potts", 2, 4096, 4096, 16, 1, 0),
+    "potts16-admm-2048-f32": ("potts", 2, 2048, 2048, 16, 0, 0),
+    "potts16-admm-4096-f32": ("potts", 2, 4096, 4096, 16, 0, 0),
+    "potts16-eval-2048-f32": ("potts-eval", 2, 2048, 2048, 16, 0, 0),
     "potts4-plain-2048": ("potts", 2, 2048, 2048, 4, 0, 1),
     # a host-driven solve to gap 1e-4 (use_graph = 0), so a profiler sees every launch
     "binary-solve-host-1024": ("binary-solve", 2, 1024, 1024, 2, 0, 0),
 }
 
 
-def algorithmic_bytes_per_px(model: str, L: int, storage: int, alpha_field: bool,
-                             levels: bool = False) -> int:
-    """State read + written once, costs and alpha read once (halos excluded);
-    with levels the L cost planes are replaced by one image plane."""
-    s = 4 if storage == 0 else 2
-    if model == "binary":
-        return 4 * 2 + 4 * s * 2 + 8 + (4 if alpha_field else 0)
-    costs = 4 if levels else 4 * L
-    return L * (4 * 2 + 3 * s * 2) + costs + 2 * s + (4 if alpha_field else 0)
-
-
-def potts_workloads(cmf, synth, flush) -> dict:
-    """The HBM-bound Potts workloads, measured on the side: 2048^2 with 4
-    labels in float32 and 4096^2 with 16 labels and float16 flow storage
-    (rpADMMII).  Per workload: the fused iteration's time and algorithmic
-    bandwidth over 50 back-to-back launches (inputs far larger than L2), and
-    the time to a 1e-4 gap from a cold start."""
+def binary_workload(cmf, synth, flush, peak) -> dict:
+    """The binary 1024^2 workload (eight disks / rectangles, edge-weighted
+    alpha): time to the 1e-4 gap of every algorithm, fused and plain, and the
+    two-iterations-per-launch warp-strip kernel's bandwidth.  Its state (about
+    75 MB) stays in the 129 MB L2, so the bound is L2, not HBM."""
     import torch
 
-    peak, _ = _peaks()
-    out = {}
-    # The 4096^2 float16 solve is capped at 1000 iterations: with 16-bit flow
-    # storage this workload's certified gap stalls near 1e-3 (--precision-study);
-    # the same workload with float32 flows is then solved to the 1e-4 gap.
-    cases = [("potts L=4 2048x2048 float32, alpha 0.3", lambda: synth.config3(), 0, 20000, True),
-             ("potts L=16 4096x4096 float16 flows, edge-weighted alpha", lambda: synth.config5(),
-              1, 1000, True),
-             ("potts L=16 4096x4096 float32 flows, edge-weighted alpha", lambda: synth.config5(),
-              0, 6000, False)]
-    for name, make, storage, max_iter, warm in cases:
-        inst = make()
-        p = cmf.default_params(2, inst.L, storage=storage, tol_gap=1e-4, max_iter=max_iter,
-                               check_every=10)
+    inst = synth.config2()
+    out = {"workload": "binary 1024x1024 shapes, edge-weighted alpha, solve to gap 1e-4",
+           "time_to_gap_ms": {}}
+    for algo in (0, 1, 2, 3, 4, 5):
+        for impl in (0, 1):
+            q = cmf.default_params(algo, 2, tol_gap=TOL, max_iter=20000,
+                                   check_every=CHECK_SIDE, impl=impl)
+            bb = cmf.alloc_binary(inst, q)
+            cmf.cmf_solve_binary(bb)  # warm (graph instantiation)
+            ts = []
+            for _ in range(3):
+                flush.zero_()
+                ms, (st, it, _) = _timed(lambda: cmf.cmf_solve_binary(bb))
+                ts.append(ms)
+            out["time_to_gap_ms"][f"{cmf.ALGO_NAMES[algo]}_{'fused' if impl == 0 else 'plain'}"] = {
+                "ms": round(float(np.median(ts)), 3), "iters": it, "converged": st == cmf.OK}
+            del bb
+    t = out["time_to_gap_ms"]
+    out["speedup_fused_vs_plain_rpADMMII"] = round(t["rpADMMII_plain"]["ms"] /
+                                                   t["rpADMMII_fused"]["ms"], 3)
+    # the fused kernel: 200 iterations = 100 two-iteration launches, back to back
+    p = cmf.default_params(FLAGSHIP, 2)
+    b = cmf.alloc_binary(inst, p)
+    cmf.cmf_init_binary(b)
+    cmf.cmf_iterate_binary(b, 20)
+    flush.zero_()
+    ms, _ = _timed(lambda: cmf.cmf_iterate_binary(b, 200))
+    launch_ms = ms / 100
+    nbytes = 2 * algorithmic_bytes_per_px("binary", 2, 0, True) * inst.H * inst.W
+    out["roofline"] = {"bound": "l2", "kernel": "k_binary_strip2", "launch_ms": launch_ms,
+                       "iterations_per_launch": 2, "algorithmic_bytes_per_launch": nbytes,
+                       "achieved": nbytes / launch_ms / 1e6, "unit": "GB/s",
+                       "frac_of_hbm_peak": nbytes / launch_ms / 1e6 / peak,
+                       "traffic": _traffic("paper_2004_11227_gb300/csrc/cmf_binary_strip2.cu",
+                                           "k_binary_strip2"),
+                       "note": "effective: iteration k+1 stays on chip and the state in L2"}
+    return out
+
+
+def potts4_workload(cmf, synth, flush, peak) -> dict:
+    """The 4-label 2048^2 Voronoi workload (alpha 0.3): per flow storage the
+    fused iteration's time and bandwidth and the time to the 1e-4 gap, and the
+    plain float32 form's time to the gap."""
+    inst = synth.config3()
+    out = {"workload": "potts L=4 2048x2048 Voronoi (64 seeds), alpha 0.3, solve to gap 1e-4"}
+    for storage, name, impl, max_iter in ((0, "float32", 0, 20000), (1, "float16", 0, 4000),
+                                         (2, "bfloat16", 0, 4000),
+                                         (0, "float32_plain", 1, 20000)):
+        p = cmf.default_params(FLAGSHIP, inst.L, storage=storage, impl=impl, tol_gap=TOL,
+                               max_iter=max_iter, check_every=CHECK_SIDE)
         s = cmf.alloc_potts(inst, p)
         cmf.cmf_init_potts(s)
-        cmf.cmf_iterate_potts(s, 10)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        n = 50
-        e0.record()
-        cmf.cmf_iterate_potts(s, n)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / n
-        nb = algorithmic_bytes_per_px("potts", inst.L, storage,
-                                      isinstance(inst.alpha, np.ndarray)) * inst.H * inst.W
-        if warm:
-            cmf.cmf_solve_potts(s)
+        cmf.cmf_iterate_potts(s, 20)
+        ms, _ = _timed(lambda: cmf.cmf_iterate_potts(s, 50))
+        ms /= 50
+        nb = algorithmic_bytes_per_px("potts", inst.L, storage, False) * inst.H * inst.W
+        cmf.cmf_solve_potts(s)  # warm
         flush.zero_()
-        torch.cuda.synchronize()
-        e0.record()
-        st, iters, hist = cmf.cmf_solve_potts(s)
-        e1.record()
-        e1.synchronize()
-        ttg_ms = e0.elapsed_time(e1)
-        # the same iteration with the costs computed from (I, levels) in the kernels
-        p_lev = cmf.default_params(2, inst.L, storage=storage)
-        s_lev = cmf.alloc_potts_levels(inst.image.astype(np.float32),
-                                       np.asarray(inst.levels, np.float32), inst.alpha, p_lev)
-        cmf.cmf_init_potts(s_lev)
-        cmf.cmf_iterate_potts(s_lev, 10)
-        torch.cuda.synchronize()
-        e0.record()
-        cmf.cmf_iterate_potts(s_lev, n)
-        e1.record()
-        e1.synchronize()
-        ms_lev = e0.elapsed_time(e1) / n
-        nb_lev = algorithmic_bytes_per_px("potts", inst.L, storage,
-                                          isinstance(inst.alpha, np.ndarray), True) * inst.H * inst.W
-        del s_lev
-        out[name] = {
-            "ms_per_iter_costs_from_levels": round(ms_lev, 4),
-            "algorithmic_GBps_costs_from_levels": nb_lev / ms_lev / 1e6,
-            "ms_per_iter": round(ms, 4),
-            "px_label_it_per_s": inst.H * inst.W * inst.L / ms * 1e3,
-            "algorithmic_GBps": nb / ms / 1e6, "hbm_frac_of_measured": nb / ms / 1e6 / peak,
-            "bytes_per_px": nb // (inst.H * inst.W),
-            "time_to_gap_ms": round(ttg_ms, 2), "iterations": iters,
-            "converged": st == cmf.OK, "final_gap": float(hist[-1, 3]),
-        }
+        ttg, (st, iters, hist) = _timed(lambda: cmf.cmf_solve_potts(s))
+        out[name] = {"ms_per_iter": round(ms, 4), "px_label_it_per_s": inst.H * inst.W * inst.L / ms * 1e3,
+                     "algorithmic_GBps": nb / ms / 1e6, "hbm_frac_of_measured": nb / ms / 1e6 / peak,
+                     "bytes_per_px": nb // (inst.H * inst.W), "time_to_gap_ms": round(ttg, 2),
+                     "iterations": iters, "converged": st == cmf.OK,
+                     "final_gap": float(hist[-1, 3])}
         del s
-        torch.cuda.empty_cache()
+    out["speedup_fused_vs_plain_float32"] = round(out["float32_plain"]["time_to_gap_ms"] /
+                                                  out["float32"]["time_to_gap_ms"], 3)
+    return out
+
+
+def potts16_other_forms(cmf, inst, flush) -> dict:
+    """The headline workload in one storage throughout: float32 flows, fused
+    and plain, to the 1e-4 gap, and float16 flows alone (capped at 3000
+    iterations: the certified gap stalls near 3e-4).  One solve each; building
+    the solve graph, well under a millisecond of host time, is inside the
+    timed region."""
+    out = {}
+    for name, storage, impl, max_iter in (("float32_fused", 0, 0, MAX_ITER),
+                                          ("float32_plain", 0, 1, MAX_ITER),
+                                          ("float16_fused_alone", 1, 0, 3000)):
+        p = cmf.default_params(FLAGSHIP, L, storage=storage, impl=impl, tol_gap=TOL,
+                               max_iter=max_iter, check_every=CHECK_EVERY)
+        s = cmf.alloc_potts(inst, p)
+        flush.zero_()
+        ms, (st, iters, hist) = _timed(lambda: cmf.cmf_solve_potts(s))
+        out[name] = {"time_to_gap_ms": round(ms, 1), "iterations": iters,
+                     "converged": st == cmf.OK, "final_gap": float(hist[-1, 3]),
+                     "ms_per_iter": round(ms / iters, 4)}
+        del s
     return out
 
 
@@ -328,6 +415,93 @@ def batch_workload(cmf, synth, flush) -> dict:
            "label_pixels": sum(i.H * i.W * i.L for i in insts)}
     del batch, items
     torch.cuda.empty_cache()
+    return out
+
+
+def oracle_checks(cmf, s, inst, flush) -> dict:
+    """The FP64 oracle against the GPU on the headline workload.
+    * one_step_windows: from the solved state, one GPU iteration against one
+      oracle iteration of the same stored state on four windows (corners,
+      interior), float16 results compared after rounding the oracle's;
+    * certificate: the oracle's E, D and gap of the solved state (the whole
+      4096^2 x 16 grid) against the GPU's;
+    * labelling: the 256^2 instance of the same recipe solved to 1e-4 by the
+      GPU (the same two-phase solve) and by the oracle; agreement of the argmax
+      labels and max |u - u_oracle|."""
+    import torch
+
+    import oracle as O
+
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    out = {}
+    po = O.default_params(FLAGSHIP, L)
+    alpha = inst.alpha_field()
+    # --- certificate of the solved state ---------------------------------------------
+    t0 = time.perf_counter()
+    st = s.state()
+    E, D, gap, res = cmf.cmf_eval_potts(s)
+    Eo, Do, gapo, reso = O.potts_eval(inst.costs, inst.alpha, st, po)
+    out["certificate"] = {"gap_gpu": gap, "gap_oracle": gapo, "gap_diff": abs(gap - gapo),
+                          "E_rel_diff": abs(E - Eo) / abs(Eo), "D_rel_diff": abs(D - Do) / abs(Eo),
+                          "oracle_s": round(time.perf_counter() - t0, 1)}
+    # --- one step on windows -----------------------------------------------------------
+    keys = ("u", "qx", "qy", "p", "ps")
+    Wd = s.W
+    before = {k: getattr(s, k)[..., :Wd].float().clone() for k in keys}
+    del st
+    cmf.cmf_iterate_potts(s, 1)
+    torch.cuda.synchronize()
+    err = {k: 0.0 for k in keys}
+    margin = 8
+    for (r0, c0, h, w) in [(0, 0, 40, 40), (H - 37, W - 45, 37, 45), (2001, 3007, 64, 64),
+                           (0, 1111, 33, 70)]:
+        R0, C0 = max(r0 - margin, 0), max(c0 - margin, 0)
+        R1, C1 = min(r0 + h + margin, H), min(c0 + w + margin, W)
+        stw = {k: v[..., R0:R1, C0:C1].cpu().double().numpy() for k, v in before.items()}
+        ref = O.potts_run(inst.costs[:, R0:R1, C0:C1], alpha[R0:R1, C0:C1], po, 1, stw)
+        ri0, ci0 = r0 - R0, c0 - C0
+        for k in keys:
+            got = getattr(s, k)[..., r0:r0 + h, c0:c0 + w].float().cpu().double().numpy()
+            rk = ref[k][..., ri0:ri0 + h, ci0:ci0 + w]
+            t = getattr(s, k).dtype
+            if k != "u":  # one rounding of the oracle's result to the stored type
+                rk = torch.as_tensor(rk).to(t).double().numpy()
+            err[k] = max(err[k], float(np.abs(got - rk).max()))
+    out["one_step_windows_max_abs"] = err
+    # --- 256^2: both solved to the gap -------------------------------------------------
+    small = rank_instance(0, 256)
+    p = cmf.default_params(FLAGSHIP, L, storage=STORAGE, costs=COSTS, tol_gap=TOL,
+                           max_iter=MAX_ITER, check_every=CHECK_SIDE,
+                           phase_storage=PHASE_STORAGE, phase_gap=PHASE_GAP)
+    g = cmf.alloc_potts(small, p)
+    stg, itg, hg = cmf.cmf_solve_potts(g)
+    t0 = time.perf_counter()
+    sto, ito, ho = O.solve(small, FLAGSHIP, tol=TOL, max_iter=MAX_ITER, check_every=50)
+    ug = g.state()["u"]
+    out["labelling_256"] = {
+        "gpu_iters": itg, "gpu_gap": float(hg[-1, 3]), "oracle_iters": ito,
+        "oracle_gap": float(ho[-1][3]),
+        "agreement": float(np.mean(O.potts_labels(ug) == O.potts_labels(sto["u"]))),
+        "max_abs_u_diff": float(np.abs(ug - sto["u"]).max()),
+        "oracle_s": round(time.perf_counter() - t0, 1)}
+    return out
+
+
+def oracle_speed() -> dict:
+    """The FP64 oracle's own speed on the two HBM-bound Potts workloads, on
+    one host thread and on all of them (bounded samples, extrapolated to a
+    whole solve with the GPU's iteration count)."""
+    from paper_2004_11227_gb300 import synth
+
+    out = {"host_cpu_count": os.cpu_count()}
+    for name, inst, n1, nall in (("potts L=4 2048x2048", synth.config3(), 2, 10),
+                                 ("potts L=16 4096x4096", rank_instance(0), 1, 4)):
+        r1, dt1, _ = oracle_rate(inst, FLAGSHIP, n1, 1)
+        ra, dta, used = oracle_rate(inst, FLAGSHIP, nall, 0)
+        out[name] = {"one_thread": {"px_label_it_per_s": r1, "iterations": n1, "s": round(dt1, 2)},
+                     "all_threads": {"px_label_it_per_s": ra, "iterations": nall,
+                                     "s": round(dta, 2), "threads": used}}
     return out
 
 
@@ -396,6 +570,13 @@ def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int =
         inst = synth.config3(h, w) if nl == 4 else synth.config5(h, w)
         st = cmf.alloc_potts(inst, p)
         init, step, ev = cmf.cmf_init_potts, cmf.cmf_iterate_potts, cmf.cmf_eval_potts
+        if model == "potts-eval":  # certificate launches only, after `iters` iterations
+            init(st)
+            step(st, iters)
+            for _ in range(3):
+                print(name, ev(st))
+            torch.cuda.synchronize()
+            return
     init(st)
     step(st, iters)
     if time_it:
@@ -420,7 +601,7 @@ def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int =
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel-case", default=None, choices=sorted(KERNEL_CASES),
@@ -428,8 +609,8 @@ def main():
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--time", action="store_true", help="time the kernel case")
     ap.add_argument("--variant", type=int, default=0, help="cmf_params.variant")
-    ap.add_argument("--skip-potts", action="store_true",
-                    help="skip the side measurements of the Potts workloads")
+    ap.add_argument("--skip-side", action="store_true",
+                    help="skip the side measurements (other workloads, oracle checks)")
     ap.add_argument("--precision-study", type=int, default=0, metavar="SIZE",
                     help="convergence of the 16-label workload at SIZE^2 per storage type")
     ap.add_argument("--study-iters", type=int, default=6000)
@@ -458,9 +639,12 @@ def main():
     __graft_entry__.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    inst = synth.config2(H, W, seed=2 + rank)
-    p = cmf.default_params(FLAGSHIP, L, tol_gap=TOL, max_iter=20000, check_every=CHECK_EVERY)
-    b = cmf.alloc_binary(inst, p)
+    peak, peak_kind = _peaks()
+    inst = rank_instance(rank)
+    p = cmf.default_params(FLAGSHIP, L, storage=STORAGE, costs=COSTS, tol_gap=TOL,
+                           max_iter=MAX_ITER, check_every=CHECK_EVERY,
+                           phase_storage=PHASE_STORAGE, phase_gap=PHASE_GAP)
+    s = cmf.alloc_potts(inst, p)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -468,157 +652,168 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step(buf):
-        st, iters, hist = cmf.cmf_solve_binary(buf)
-        assert st == cmf.OK, "solve did not reach the gap"
+    def step():
+        st, iters, hist = cmf.cmf_solve_potts(s)
+        assert st == cmf.OK, f"solve did not reach the gap (status {st}, gap {hist[-1, 3]})"
         return iters, hist
 
-    for _ in range(max(args.warmup, 3)):
-        step(b)
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        step()
 
     sampler = ClockSampler(local)
     sampler.start()
     barrier()
-    times, iters_all = [], []
+    times, iters_all, gaps, phase1 = [], [], [], []
     for _ in range(args.steps):
         flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        iters, hist = step(b)
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        ms, (iters, hist) = _timed(step)
+        times.append(ms)
         iters_all.append(iters)
+        gaps.append(float(hist[-1, 3]))
+        # the first check at or below the switch gap ends the 16-bit phase
+        phase1.append(int(hist[int(np.argmax(hist[:, 3] <= PHASE_GAP)), 0]))
     barrier()
     clocks = sampler.stop()
-
     total_ms, total_units = job_totals(times, iters_all, world, dev)
     value = total_units / (total_ms / 1000.0)
     iters = int(np.median(iters_all))
-    n_checks = int(np.ceil(iters / CHECK_EVERY))
-    # per solve: init, loop reset; per check: the chunk's iteration launches (two
-    # iterations per launch, one single launch for an odd remainder; three buffer sets
-    # let a chunk of two or more launches end in the caller's buffers) and the
-    # certificate launch (its last block reduces and takes the stop decision); a lone
-    # launch per chunk would make the loop body two chunks long, closed by one
-    # loop-condition kernel
-    chunk_launches = CHECK_EVERY // 2 + CHECK_EVERY % 2
-    bodies = (n_checks + 1) // 2 if chunk_launches == 1 else 0
-    launches = args.steps * (2 + n_checks * (chunk_launches + 1) + bodies)
+    it16 = int(np.median(phase1))
+    # per solve: cold start, two loop resets, the float16-to-float32 switch;
+    # per check: check_every iteration launches, the launch that turns w back
+    # into u, the certificate launch (its last block reduces and takes the
+    # stop decision)
+    launches = args.steps * (4 + (iters // CHECK_EVERY) * (CHECK_EVERY + 2))
 
     # --- end to end through the C ABI with host buffers -------------------------------
-    costs_h = [torch.from_numpy(np.ascontiguousarray(np.pad(
-        inst.costs[i], ((0, 0), (0, b.pitch - W))))).pin_memory() for i in range(2)]
-    alpha_h = torch.from_numpy(np.ascontiguousarray(np.pad(
-        inst.alpha, ((0, 0), (0, b.pitch - W))))).pin_memory()
-    u_h = torch.empty((H, b.pitch), dtype=torch.float32).pin_memory()
+    cdt = s.C.dtype
+    costs_h = torch.empty(tuple(s.C.shape), dtype=cdt).pin_memory()
+    costs_h.copy_(s.C.cpu())
+    alpha_h = torch.empty(tuple(s.alpha.shape), dtype=torch.float32).pin_memory()
+    alpha_h.copy_(s.alpha.cpu())
+    u_h = torch.empty(tuple(s.u.shape), dtype=torch.float32).pin_memory()
     e2e_times = []
+    n_e2e = min(args.steps, 3)
     barrier()
-    for _ in range(args.steps):
+    for _ in range(n_e2e):
         flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        b.Cs.copy_(costs_h[0], non_blocking=True)
-        b.Ct.copy_(costs_h[1], non_blocking=True)
-        b.alpha.copy_(alpha_h, non_blocking=True)
-        step(b)
-        u_h.copy_(b.u, non_blocking=True)
-        e1.record()
-        e1.synchronize()
-        e2e_times.append(e0.elapsed_time(e1))
+
+        def e2e_step():
+            s.C.copy_(costs_h, non_blocking=True)
+            s.alpha.copy_(alpha_h, non_blocking=True)
+            it, _ = step()
+            u_h.copy_(s.u, non_blocking=True)
+            return it
+
+        ms, it = _timed(e2e_step)
+        e2e_times.append(ms)
     barrier()
-    e2e_ms = job_max_ms(e2e_times, world, dev)
-    e2e_value = total_units / (e2e_ms / 1000.0)
-    h2d = 3 * H * b.pitch * 4
-    d2h = H * b.pitch * 4
+    e2e_ms = job_max_ms(e2e_times, world, dev) / n_e2e
+    e2e_value = H * W * L * iters * world / (e2e_ms / 1000.0)
+    h2d = costs_h.numel() * costs_h.element_size() + alpha_h.numel() * 4
+    d2h = u_h.numel() * 4
 
-    # --- dominant kernel: fused iteration, back-to-back launches -----------------------
-    cmf.cmf_init_binary(b)
-    cmf.cmf_iterate_binary(b, 20)
-    flush.zero_()
-    torch.cuda.synchronize()
-    n_rf = 200
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    cmf.cmf_iterate_binary(b, n_rf)
-    e1.record()
-    e1.synchronize()
-    # the solver picks the two-iterations-per-launch warp-strip kernel here: n_rf
-    # iterations are n_rf / 2 launches; a launch's algorithmic bytes are those of its
-    # two iterations (the "effective" figure: the intermediate state never reaches
-    # memory, so it can exceed the copy bandwidth; ncu's DRAM bytes are in `traffic`)
-    kern_ms = e0.elapsed_time(e1) / (n_rf // 2)
-    peak, peak_kind = _peaks()
-    bytes_launch = 2 * BYTES_PER_PX * H * W
-    achieved = bytes_launch / (kern_ms / 1000.0) / 1e9
-    traffic = _traffic("paper_2004_11227_gb300/csrc/cmf_binary_strip2.cu", "k_binary_strip2")
+    # --- the fused iteration, back to back: float16 (phase one), float32 (two) -------
+    def kernel_ms(storage):
+        q = cmf.default_params(FLAGSHIP, L, storage=storage, costs=COSTS)
+        k = cmf.alloc_potts(inst, q)
+        cmf.cmf_init_potts(k)
+        cmf.cmf_iterate_potts(k, 20)
+        flush.zero_()
+        ms, _ = _timed(lambda: cmf.cmf_iterate_potts(k, 50))
+        del k
+        torch.cuda.empty_cache()
+        return ms / 50
 
-    # --- plain one-kernel-per-step form and the other algorithms: time to gap ---------
-    def time_to_gap(algo, impl):
-        q = cmf.default_params(algo, L, tol_gap=TOL, max_iter=20000, check_every=CHECK_EVERY,
-                               impl=impl)
-        bb = cmf.alloc_binary(inst, q)
-        cmf.cmf_solve_binary(bb)  # warm
-        ts = []
-        for _ in range(3):
-            flush.zero_()
-            torch.cuda.synchronize()
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record()
-            st, it, _ = cmf.cmf_solve_binary(bb)
-            a1.record()
-            a1.synchronize()
-            ts.append(a0.elapsed_time(a1))
-        return float(np.median(ts)), it
+    ms16, ms32 = kernel_ms(1), kernel_ms(0)
+    t16, t32 = ms16 * it16, ms32 * (iters - it16)
+    storage_dom = 1 if t16 >= t32 else 0
+    launch_ms = ms16 if storage_dom == 1 else ms32
+    # algorithmic bytes of the dominant instantiation; the 16-bit count of the
+    # workload's fields (296 B/px) for the float16 one, the float32 count (every
+    # field 4 bytes: u, q_i, p_i, p_s read and written, costs and alpha read:
+    # 16 x 36 + 8 + 4 = 588 B/px, equal to what the kernel moves) for float32
+    algo_px = BYTES_PER_PX_16BIT if storage_dom == 1 else \
+        algorithmic_bytes_per_px("potts", L, 0, True, "f32")
+    design_px = algorithmic_bytes_per_px("potts", L, storage_dom, True,
+                                         {0: "f32", 2: "f16"}[COSTS])
+    achieved = algo_px * H * W / (launch_ms / 1000.0) / 1e9
+    name = "k_potts_strip<__half>" if storage_dom == 1 else "k_potts_strip<float>"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "traffic": _traffic("paper_2004_11227_gb300/csrc/cmf_potts_strip.cu", name),
+                "kernel": name, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_px": algo_px,
+                "algorithmic_bytes_per_launch": algo_px * H * W, "launch_ms": launch_ms,
+                "design_bytes_per_px": design_px,
+                "time_share_in_solve": {"float16_phase": t16 / (t16 + t32),
+                                        "float32_phase": t32 / (t16 + t32)},
+                "float16_kernel": {"launch_ms": ms16, "bytes_per_px_16bit": BYTES_PER_PX_16BIT,
+                                   "frac_16bit_count": BYTES_PER_PX_16BIT * H * W / ms16 / 1e6 / peak,
+                                   "design_bytes_per_px": algorithmic_bytes_per_px(
+                                       "potts", L, 1, True, {0: "f32", 2: "f16"}[COSTS]),
+                                   "frac_design": algorithmic_bytes_per_px(
+                                       "potts", L, 1, True, {0: "f32", 2: "f16"}[COSTS]) *
+                                   H * W / ms16 / 1e6 / peak},
+                "float32_kernel": {"launch_ms": ms32,
+                                   "frac": algorithmic_bytes_per_px("potts", L, 0, True, "f32") *
+                                   H * W / ms32 / 1e6 / peak},
+                "note": "launch time = 50 back-to-back iterations / 50 (one w-to-u pass per "
+                        "call included); the dominant instantiation by time in the solve"}
 
-    ttg = {}
-    for algo in (0, 1, 2, 3, 4, 5):
-        for impl in (0, 1):
-            ms, it = time_to_gap(algo, impl)
-            ttg[f"{cmf.ALGO_NAMES[algo]}_{'fused' if impl == 0 else 'plain'}"] = {
-                "ms": round(ms, 3), "iters": it}
-    fused_ms = ttg["rpADMMII_fused"]["ms"]
-    plain_ms = ttg["rpADMMII_plain"]["ms"]
-
-    potts = potts_workloads(cmf, synth, flush) if rank == 0 and not args.skip_potts else {}
-    batch = batch_workload(cmf, synth, flush) if rank == 0 and not args.skip_potts else {}
+    side = {}
+    if rank == 0 and not args.skip_side:
+        side["potts16_float32_flows"] = potts16_other_forms(cmf, inst, flush)
+        side["oracle_check"] = oracle_checks(cmf, s, inst, flush)
+        del s
+        torch.cuda.empty_cache()
+        side["potts4_2048"] = potts4_workload(cmf, synth, flush, peak)
+        side["binary_1024"] = binary_workload(cmf, synth, flush, peak)
+        side["batch_workload"] = batch_workload(cmf, synth, flush)
+        side["oracle_speed"] = oracle_speed()
 
     if rank == 0:
-        rate, dt = cpu_oracle_rate(inst, 150)
+        c5 = side.get("oracle_speed", {}).get("potts L=16 4096x4096", {})
+        if c5:
+            rate, used = c5["all_threads"]["px_label_it_per_s"], c5["all_threads"]["threads"]
+            sample = (f"{c5['all_threads']['iterations']} rpADMMII iterations of the full "
+                      f"4096x4096x16 workload, FP64 C oracle, {used} threads "
+                      f"({c5['all_threads']['s']} s)")
+        else:
+            rate, dt, used = oracle_rate(inst, FLAGSHIP, 1, 0)
+            sample = (f"1 rpADMMII iteration of the full 4096x4096x16 workload, FP64 C oracle, "
+                      f"{used} threads ({dt:.1f} s)")
+        f32 = side.get("potts16_float32_flows", {})
         line = {
             "metric": "pixel*label*iterations/s", "value": value, "unit": "px*label*it/s",
-            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "n_gpus": world, "steps": args.steps, "warmup": warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "H": H, "W": W, "L": L, "algo": "rpADMMII fused",
+                       "flow_storage": "float16 q_i, p_i to gap 2e-3, then float32; p_s, u "
+                                       "float32",
                        "check_every": CHECK_EVERY, "tol_gap": TOL,
-                       "l2": "flushed (256 MB write) before every timed step",
+                       "l2": "inputs and state (several GB) far larger than L2; 256 MB flush "
+                             "before every timed step",
                        "parallelism": f"replicas x{world}"},
-            "time_to_gap_ms": {"fused": fused_ms, "plain": plain_ms,
-                               "speedup_fused_vs_plain": round(plain_ms / fused_ms, 3),
-                               "iterations": iters, "all": ttg},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_binary_strip2", "peak_kind": peak_kind,
-                         "iterations_per_launch": 2, "effective": True,
-                         "algorithmic_bytes_per_launch": bytes_launch,
-                         "launch_ms": kern_ms},
-            "cpu_baseline": {"value": rate, "unit": "px*label*it/s", "cores": 1,
-                             "kind": "oracle",
-                             "sample": "150 rpADMMII iterations of the full 1024x1024 workload, "
-                                       f"FP64 C oracle, one thread ({dt:.1f} s)"},
+            "time_to_gap_ms": {"two_phase_fused": round(float(np.median(times)), 1),
+                               "iterations": iters, "iterations_float16_phase": it16,
+                               "final_gap_max": max(gaps),
+                               **{k: v["time_to_gap_ms"] for k, v in f32.items()},
+                               **({"speedup_two_phase_vs_float32_fused": round(
+                                   f32["float32_fused"]["time_to_gap_ms"] /
+                                   float(np.median(times)), 3),
+                                   "speedup_two_phase_vs_plain_float32": round(
+                                   f32["float32_plain"]["time_to_gap_ms"] /
+                                   float(np.median(times)), 3)} if f32 else {})},
+            "roofline": roofline,
+            "cpu_baseline": {"value": rate, "unit": "px*label*it/s", "cores": used,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": e2e_value, "unit": "px*label*it/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "potts_workloads": potts,
-            "batch_workload": batch,
             "gpu_launches": launches,
             "clocks": clocks,
+            **side,
         }
         print(json.dumps(line))
     if world > 1:

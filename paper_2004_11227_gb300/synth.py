@@ -231,8 +231,8 @@ def config3(H: int = 2048, W: int = 2048) -> Instance:
     return potts_voronoi(H, W, L=4, n_seeds=n_seeds, sigma=0.1, seed=3, alpha_base=0.3)
 
 
-def config5(H: int = 4096, W: int = 4096) -> Instance:
+def config5(H: int = 4096, W: int = 4096, seed: int = 5) -> Instance:
     """Potts L=16 4096^2 Voronoi (512 seeds), 16 levels i/15, edge-weighted alpha."""
     n_seeds = max(8, int(round(512 * (H * W) / (4096 * 4096)))) if H * W < 4096 * 4096 else 512
-    return potts_voronoi(H, W, L=16, n_seeds=n_seeds, sigma=0.05, seed=5, alpha_base=0.3,
+    return potts_voronoi(H, W, L=16, n_seeds=n_seeds, sigma=0.05, seed=seed, alpha_base=0.3,
                          edge_weighted=True)

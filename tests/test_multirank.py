@@ -60,8 +60,10 @@ def test_single_rank_needs_no_process_group():
 def test_ranks_solve_their_own_instances():
     from paper_2004_11227_gb300 import synth
 
-    a, b = synth.config2(64, 64, seed=2), synth.config2(64, 64, seed=3)
+    a, b = bench.rank_instance(0, 64), bench.rank_instance(1, 64)
     assert not np.array_equal(a.costs[0], b.costs[0])
+    assert a.costs.shape == (bench.L, 64, 64)
+    np.testing.assert_array_equal(a.costs, synth.config5(64, 64).costs)
 
 
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
