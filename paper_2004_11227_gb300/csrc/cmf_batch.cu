@@ -2,12 +2,15 @@
 // count advanced together inside one CUDA graph (conditional WHILE node), with
 // per-instance convergence masks.
 //
-// Every iteration launches one kernel over the tiles of all binary instances
-// and one over the tiles of all Potts instances; a block maps its tile to an
-// instance through a device table and returns at once when that instance has
-// converged.  Every check_every iterations the certificates of all instances
-// are computed tile by tile, reduced per instance in a fixed order, and one
-// decide kernel retires converged instances and sets the loop condition.
+// Every iteration launches one kernel over the tiles of all binary instances,
+// one over the tiles of the Potts instances that run on tiles (odd widths,
+// rPDRQ) and one over the warp-strip items of the other Potts instances; a
+// block (tiles) or warp (strip items) maps its work to an instance through a
+// device table and skips it when that instance has converged.  Every
+// check_every iterations the strip instances' multipliers are turned back from
+// the w form into u, the certificates of all instances are computed tile by
+// tile, reduced per instance in a fixed order, and one decide kernel retires
+// converged instances and sets the loop condition.
 #include <math.h>
 #include <string.h>
 
@@ -23,9 +26,25 @@ constexpr size_t kAl = 256;
 inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
 struct BatchLayout {
-    size_t desc, tiles, partials, scal, ctl, states, total;
-    int n_bin_tiles, n_potts_tiles, n_bin_ev, n_potts_ev, potts_rows, max_l;
+    size_t desc, tiles, items, partials, scal, ctl, states, total;
+    int n_bin_tiles, n_potts_tiles, n_bin_ev, n_potts_ev, potts_rows, max_l, n_strip_items;
 };
+
+// Whether a Potts instance of a batch runs by warp strips (the ADMM family,
+// even pitch with room for a padding column when the width is odd,
+// pair-aligned buffers; the workspace set is aligned anyway), and its strip
+// and band counts.
+bool batch_strip(const cmf_instance& in, const cmf_params& p) {
+    if (in.model != 1 || p.algo == CMF_RPDRQ) return false;
+    const Grid G{in.H, in.W, in.pitch, (size_t)in.H * (size_t)in.pitch};
+    const PottsStateV s{in.d_u, in.d_qx, in.d_qy, in.d_p, (float*)in.d_ps};
+    return potts_strip_eligible(G, p.storage, in.d_cost, in.d_alpha, s, s, true);
+}
+int strip_count(const cmf_instance& in) { return (in.W + 59) / 60; }
+int strip_items(const cmf_instance& in) {
+    const int R = potts_strip_max_rows();
+    return strip_count(in) * ((in.H + R - 1) / R);
+}
 
 int potts_rows_for(int maxL) { return maxL <= 8 ? 4 : (maxL <= 16 ? 2 : 1); }
 
@@ -54,7 +73,10 @@ BatchLayout batch_layout(const cmf_instance* inst, int n, const cmf_params& p) {
             b.n_bin_ev += ev;
         } else {
             const int ty = 8 * b.potts_rows;
-            b.n_potts_tiles += ntx * ((in.H + ty - 1) / ty);
+            if (batch_strip(in, p))
+                b.n_strip_items += strip_items(in);
+            else
+                b.n_potts_tiles += ntx * ((in.H + ty - 1) / ty);
             b.n_potts_ev += ev;
         }
     }
@@ -63,6 +85,8 @@ BatchLayout batch_layout(const cmf_instance* inst, int n, const cmf_params& p) {
     off += al(sizeof(BatchDesc) * (size_t)n);
     b.tiles = off;
     off += al(sizeof(int) * (size_t)(b.n_bin_tiles + b.n_potts_tiles + b.n_bin_ev + b.n_potts_ev + 4));
+    b.items = off;
+    off += al(sizeof(int2) * (size_t)(b.n_strip_items + 1));
     b.partials = off;
     off += al(sizeof(double) * 3 * (size_t)(b.n_bin_ev + b.n_potts_ev + 1));
     b.scal = off;
@@ -227,6 +251,9 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
     // descriptors and tile tables
     std::vector<BatchDesc> desc(n);
     std::vector<int> tb, tp, eb, ep;
+    // (instance, strip item) of the strip-eligible Potts instances, even and
+    // odd widths apart (the odd ones run the kernel with the last-pair masks)
+    std::vector<int2> sitems, oitems;
     char* sbase = ws + B.states;
     const int pty = 8 * B.potts_rows;
     for (int i = 0; i < n; ++i) {
@@ -278,7 +305,14 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
             D.pw.ps = (float*)b;
             D.tile_base = (int)tp.size();
             D.ev_tab = (int)ep.size();
-            for (int t = 0; t < ntx * ((in.H + pty - 1) / pty); ++t) tp.push_back(i);
+            if (batch_strip(in, *p)) {
+                D.sp_nstrips = strip_count(in);
+                D.sp_rows = potts_strip_max_rows();
+                std::vector<int2>& dst = in.W % 2 ? oitems : sitems;
+                for (int t = 0; t < strip_items(in); ++t) dst.push_back(make_int2(i, t));
+            } else {
+                for (int t = 0; t < ntx * ((in.H + pty - 1) / pty); ++t) tp.push_back(i);
+            }
             for (int t = 0; t < D.ev_count; ++t) ep.push_back(i);
         }
         sbase += state_bytes(in, p->storage);
@@ -302,6 +336,14 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
                                  cudaMemcpyHostToDevice, st));
     if (!all.empty())
         CMF_CUDA_TRY(cudaMemcpyAsync(tables, all.data(), sizeof(int) * all.size(),
+                                     cudaMemcpyHostToDevice, st));
+    int2* d_items = (int2*)(ws + B.items);
+    int2* d_oitems = d_items + sitems.size();
+    if (!sitems.empty())
+        CMF_CUDA_TRY(cudaMemcpyAsync(d_items, sitems.data(), sizeof(int2) * sitems.size(),
+                                     cudaMemcpyHostToDevice, st));
+    if (!oitems.empty())
+        CMF_CUDA_TRY(cudaMemcpyAsync(d_oitems, oitems.data(), sizeof(int2) * oitems.size(),
                                      cudaMemcpyHostToDevice, st));
     // cold starts
     if (!p->warm_start) {
@@ -346,7 +388,18 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
             if (e == cudaSuccess && !tp.empty())
                 e = batch_potts_step(p->storage, aniso, dr, p->sweeps, B.potts_rows, B.max_l,
                                      d_desc, d_tp, (int)tp.size(), parity, cs);
+            if (e == cudaSuccess && !sitems.empty())
+                e = batch_potts_strip_step(p->storage, aniso, false, d_desc, d_items,
+                                           (int)sitems.size(), parity, k == 0, cs);
+            if (e == cudaSuccess && !oitems.empty())
+                e = batch_potts_strip_step(p->storage, aniso, true, d_desc, d_oitems,
+                                           (int)oitems.size(), parity, k == 0, cs);
         }
+        // the strip instances hold w = u - cu p_s after the chunk: back to u
+        // (both tables are contiguous in the workspace)
+        const int nall = (int)(sitems.size() + oitems.size());
+        if (e == cudaSuccess && nall > 0)
+            e = batch_potts_strip_finalize(d_desc, d_items, nall, cs);
         if (e == cudaSuccess && !eb.empty())
             e = batch_binary_eval(p->storage, aniso, dr, (float)p->tau, d_desc, d_eb,
                                   (int)eb.size(), partials, cs);

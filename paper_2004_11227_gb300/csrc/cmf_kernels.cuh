@@ -358,8 +358,11 @@ cudaError_t binary_eval_strip(int storage, const BinProblem& P, const BinStateV&
 
 // --- warp-strip Potts ADMM (cmf_potts_strip.cu) ---
 // Eligible: even W and pitch, H * pitch within int, pair-aligned planes.
+// odd_width_ok: the ADMM items of a batch also take odd widths (their last
+// pair is masked; the pitch must leave room for the padding column).
 bool potts_strip_eligible(const Grid& G, int storage, const float* C, const float* alpha,
-                          const PottsStateV& a, const PottsStateV& b);
+                          const PottsStateV& a, const PottsStateV& b,
+                          bool odd_width_ok = false);
 // One iteration a -> b.  Reads u_i = a.u_i + cu_in * a.p_s; writes
 // w_i = u_i^{k+1} - cu * p_s^{k+1} into b.u (see potts_strip_finalize).
 cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
@@ -425,6 +428,8 @@ struct BatchDesc {
     PottsStateV pu, pw;    // caller's and workspace state (Potts)
     AdmmCoef ak;           // coefficients for this instance's L
     DrCoef dk;
+    int sp_nstrips;        // Potts by warp strips: strips of the grid (0: tiles)
+    int sp_rows;           // band height of its strip items
 };
 
 // parity 0: caller's buffers -> workspace; 1: workspace -> caller's buffers
@@ -434,6 +439,17 @@ cudaError_t batch_binary_step(int storage, bool aniso, bool dr, int sweeps,
 cudaError_t batch_potts_step(int storage, bool aniso, bool dr, int sweeps, int rows, int maxL,
                              const BatchDesc* desc, const int* tile_inst, int ntiles,
                              int parity, cudaStream_t st);
+// Potts instances of a batch by warp strips: one launch over the (instance,
+// item) table (items of retired instances are skipped); first: the chunk's
+// first iteration (reads u itself, later ones the w form).  The finalize
+// launch turns w back into u on the same items.
+cudaError_t batch_potts_strip_step(int storage, bool aniso, bool odd_width, const BatchDesc* desc,
+                                   const int2* items, int nitems, int parity, int first,
+                                   cudaStream_t st);
+cudaError_t batch_potts_strip_finalize(const BatchDesc* desc, const int2* items, int nitems,
+                                       cudaStream_t st);
+int potts_strip_max_rows();  // band rows the strip kernels take at most
+
 cudaError_t batch_binary_eval(int storage, bool aniso, bool dr, float tau,
                               const BatchDesc* desc, const int* tile_inst, int ntiles,
                               double* partials, cudaStream_t st);

@@ -45,10 +45,221 @@ struct RowVals {
 
 }  // namespace
 
-// One launch: every work item is a strip `cs` of 64 columns and a band of
-// rows r0 .. r1-1, all labels.  CS: the cost source (kCostF32 planes,
-// kCostLevels, kCostF16 planes), a template parameter so each instantiation
-// carries only its own loads.  p_s is float32 whatever the flow storage S.
+// One work item of the Potts strip kernels: strip `cs` (64 columns, two per
+// lane, 60 owned), band rows r0 .. r1-1, all labels.  CS: the cost source
+// (kCostF32 planes, kCostLevels, kCostF16 planes), a template parameter so
+// each instantiation carries only its own loads.  p_s is float32 whatever the
+// flow storage S.  Arguments by value: the caller's copies stay in registers
+// or the parameter bank.  ODDW: the grid may have an odd width; the pair of
+// its last column is (W-1, W), whose second element falls on the padding
+// column: it is loaded as zero and never stored, and the last column's own
+// x-difference gets weight zero (the single-problem solver takes even widths
+// only and compiles without these masks).
+template <typename S, bool ANISO, int CS, bool ODDW = false>
+__device__ __forceinline__ void potts_strip_item(const PottsProblem P, const PottsState<S> s0,
+                                                 const PottsState<S> s1, const AdmmCoef K,
+                                                 const float cu_in, const int cs, const int r0,
+                                                 const int r1, float2 (*acc)[32],
+                                                 const int lane) {
+    using St = Store<S>;
+    using PS = Pair<S>;
+    using PF = Pair<float>;
+    using PH = Pair<__half>;
+    const Grid G = P.g;
+    const int L = P.L;
+    const unsigned full = 0xffffffffu;
+    const int c = cs - 2 + 2 * lane;  // even column of the pair (W is even)
+    const bool colin = c >= 0 && c < G.W;
+    const bool own = colin && lane >= 1 && lane <= 30;
+    const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;  // odd column is not the last
+    const bool oddin = !ODDW || c + 1 < G.W;        // the pair's second column exists
+    const float mxe = (!ODDW || c < G.W - 1) ? 1.f : 0.f;  // even column is not the last
+    auto row_ok = [&](int r) { return colin && r >= 0 && r < G.H; };
+    // weight of a row's own y term: row H-1 has no forward difference
+    auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+
+    // one row of state at (r, c..c+1): zero outside the grid
+    auto load_row = [&](const S* qx, const S* qy, const S* pp, const float* w, int r,
+                        RowVals<S>& x) {
+        const bool ok = row_ok(r);
+        const int o = r * G.pitch + c;
+        x.qx = ok ? PS::ld(qx + o) : PS::zero();
+        x.qy = ok ? PS::ld(qy + o) : PS::zero();
+        x.p = ok ? PS::ld(pp + o) : PS::zero();
+        x.ps = ok ? PF::ld(s0.ps + o) : PF::zero();
+        x.w = ok ? PF::ld(w + o) : PF::zero();
+        if (ODDW && !oddin) {
+            x.qx = PS::lo(x.qx);
+            x.qy = PS::lo(x.qy);
+            x.p = PS::lo(x.p);
+            x.ps.y = 0.f;
+            x.w.y = 0.f;
+        }
+    };
+    // g = div q + p_i - p_s - u_i / c at row r, given the row above's q_y
+    // (outside the grid the loaded values are zero)
+    auto g_of = [&](const RowVals<S>& x, float2 qy_up, int r) {
+        const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy), p = PS::f2(x.p);
+        const float2 ps = x.ps;
+        const float qx_left = __shfl_up_sync(full, qx.y, 1);
+        const float wy = row_w(r);
+        const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
+        float2 g;
+        g.x = qx.x - qx_left + wy * qy.x - qy_up.x + p.x - ps.x - u_e * K.inv_c;
+        g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + p.y - ps.y - u_o * K.inv_c;
+        return g;
+    };
+
+    // q^{k+1} = P_alpha(q + grad g / a) at row t of this pair, from g at
+    // rows t and t+1 (zero outside the grid)
+    struct QN {
+        float tx_e, tx_o, ty_e, ty_o;
+    };
+    auto q_new = [&](const RowVals<S>& x, float2 g_t, float2 g_b, float2 al, int t) {
+        const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
+        const float my = row_w(t) * K.inv_a;
+        const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
+        QN q;
+        q.tx_e = qx.x + (g_t.y - g_t.x) * (ODDW ? mxe * K.inv_a : K.inv_a);
+        q.tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
+        q.ty_e = qy.x + (g_b.x - g_t.x) * my;
+        q.ty_o = qy.y + (g_b.y - g_t.y) * my;
+        project_sel<ANISO>(q.tx_e, q.ty_e, al.x);
+        project_sel<ANISO>(q.tx_o, q.ty_o, al.y);
+        const bool in = colin && t >= 0 && t < G.H;
+        q.tx_e = in ? St::rt(q.tx_e) : 0.f;
+        q.tx_o = (in && oddin) ? St::rt(q.tx_o) : 0.f;
+        q.ty_e = in ? St::rt(q.ty_e) : 0.f;
+        q.ty_o = (in && oddin) ? St::rt(q.ty_o) : 0.f;
+        return q;
+    };
+
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const size_t lo = (size_t)l * G.plane;
+        const S* qx0 = s0.qx + lo;
+        const S* qy0 = s0.qy + lo;
+        const S* p0 = s0.p + lo;
+        const float* w0 = s0.u + lo;
+        // costs of label l: its plane, or (I - c_l)^2 from the image plane
+        const float* Cb = CS == kCostLevels ? P.C : P.C + lo;
+        const __half* Ch = CS == kCostF16 ? P.C16 + lo : nullptr;
+        const float lev_l = CS == kCostLevels ? __ldg(P.lev + l) : 0.f;
+        S* qx1 = s1.qx + lo;
+        S* qy1 = s1.qy + lo;
+        S* p1o = s1.p + lo;
+        float* w1 = s1.u + lo;
+        auto row = [&](int r, RowVals<S>& x) { load_row(qx0, qy0, p0, w0, r, x); };
+        // costs at row r (zero outside the grid; never used there), a select
+        // rather than a branch on the lane's bounds
+        auto ld_c = [&](int r) {
+            const bool ok = row_ok(r);
+            float2 v;
+            if (CS == kCostF16)
+                v = ok ? PH::f2(PH::ld(Ch + r * G.pitch + c)) : PF::zero();
+            else
+                v = ok ? PF::ld(Cb + r * G.pitch + c) : PF::zero();
+            if (CS == kCostLevels) {
+                v.x = (v.x - lev_l) * (v.x - lev_l);
+                v.y = (v.y - lev_l) * (v.y - lev_l);
+            }
+            if (ODDW && !oddin) v.y = 0.f;
+            return v;
+        };
+        auto ld_al = [&](int r) {
+            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
+            float2 v = row_ok(r) ? PF::ld(P.alpha.plane + r * G.pitch + c) : PF::zero();
+            if (ODDW && !oddin) v.y = 0.f;
+            return v;
+        };
+        // d = div q^{k+1} at output row t from the new q of rows t and t-1,
+        // then p_i^{k+1}, w_i and this label's share of the p_s update
+        auto finish = [&](int t, const QN& q, float2 qy_up, const RowVals<S>& x, float2 cl,
+                          float2 g) {
+            const float txl = __shfl_up_sync(full, q.tx_o, 1);  // new q_x at c-1
+            const float wy = row_w(t);
+            const float d_e = q.tx_e - txl + wy * q.ty_e - qy_up.x;
+            const float d_o = mxo * q.tx_o - q.tx_e + wy * q.ty_o - qy_up.y;
+            const float2 pv = PS::f2(x.p), ps = x.ps;
+            const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
+            float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
+            const float p1_e =
+                potts_label_pu<S>(K, g.x, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
+            const float p1_o =
+                potts_label_pu<S>(K, g.y, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
+            float2& ac = acc[t - r0][lane];
+            const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
+            if (l == 0) {
+                ac = share;
+            } else {
+                ac.x += share.x;
+                ac.y += share.y;
+            }
+            if (own) {
+                const int o = t * G.pitch + c;
+                if (!ODDW || oddin) {
+                    PS::st(qx1 + o, q.tx_e, q.tx_o);
+                    PS::st(qy1 + o, q.ty_e, q.ty_o);
+                    PS::st(p1o + o, p1_e, p1_o);
+                    PF::st(w1 + o, v_e, v_o);
+                } else {  // the last column alone
+                    St::st(qx1 + o, q.tx_e);
+                    St::st(qy1 + o, q.ty_e);
+                    St::st(p1o + o, p1_e);
+                    w1[o] = v_e;
+                }
+            }
+        };
+
+        // top-down: step t makes q^{k+1} of row t and finishes row t;
+        // row t+2 is loaded during the step
+        RowVals<S> a, b, nx;
+        const int rm2 = r0 - 2;
+        const float2 qy_m2 =
+            PS::f2((colin && rm2 >= 0) ? (oddin ? PS::ld(qy0 + rm2 * G.pitch + c)
+                                            : PS::lo(PS::ld(qy0 + rm2 * G.pitch + c)))
+                                   : PS::zero());
+        row(r0 - 1, a);
+        row(r0, b);
+        float2 g_t = g_of(a, qy_m2, r0 - 1);
+        float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
+        float2 al_t = ld_al(r0 - 1), cl_t = PF::zero(), al_n = al_t, cl_n = cl_t;
+#pragma unroll 1
+        for (int t = r0 - 1; t < r1; ++t) {
+            if (t + 2 <= r1) row(t + 2, nx);
+            if (t + 1 < r1) {
+                al_n = ld_al(t + 1);
+                cl_n = ld_c(t + 1);
+            }
+            const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);
+            const QN q = q_new(a, g_t, g_n, al_t, t);
+            if (t >= r0) finish(t, q, qyn_up, a, cl_t, g_t);
+            qyn_up = make_float2(q.ty_e, q.ty_o);
+            a = b;
+            b = nx;
+            g_t = g_n;
+            al_t = al_n;
+            cl_t = cl_n;
+        }
+    }
+
+    // p_s^{k+1} on the band from the summed label shares
+#pragma unroll 1
+    for (int t = r0; t < r1; ++t) {
+        if (!own) continue;
+        const int o = t * G.pitch + c;
+        const float2 ps = PF::ld(s0.ps + o);
+        const float2 ac = acc[t - r0][lane];
+        if (!ODDW || oddin)
+            PF::st(s1.ps + o, potts_ps_update(K, ps.x, ac.x, 0.f),
+                   potts_ps_update(K, ps.y, ac.y, 0.f));
+        else
+            s1.ps[o] = potts_ps_update(K, ps.x, ac.x, 0.f);
+    }
+}
+
+// One launch of the single-problem solver: every work item is a strip and a
+// band of R rows.
 template <typename S, bool ANISO, int CS>
 __global__ void __launch_bounds__(kStripWarps * 32, 7)
     k_potts_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, AdmmCoef K, float cu_in,
@@ -56,183 +267,146 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7)
     __shared__ float2 acc_s[kStripWarps][kStripRmax][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     float2(*acc)[32] = acc_s[wib];
-
     for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
          item += gridDim.x * kStripWarps) {
         const int cs = (item % nstrips) * kStripOut;
         const int r0 = (item / nstrips) * R;
         const int r1 = min(r0 + R, P.g.H);
-        using St = Store<S>;
-        using PS = Pair<S>;
-        using PF = Pair<float>;
-        using PH = Pair<__half>;
-        const Grid G = P.g;
-        const int L = P.L;
-        const unsigned full = 0xffffffffu;
-        const int c = cs - 2 + 2 * lane;  // even column of the pair (W is even)
-        const bool colin = c >= 0 && c < G.W;
-        const bool own = colin && lane >= 1 && lane <= 30;
-        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;  // odd column is not the last
-        auto row_ok = [&](int r) { return colin && r >= 0 && r < G.H; };
-        // weight of a row's own y term: row H-1 has no forward difference
-        auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+        potts_strip_item<S, ANISO, CS>(P, s0, s1, K, cu_in, cs, r0, r1, acc, lane);
+    }
+}
 
-        // one row of state at (r, c..c+1): zero outside the grid
-        auto load_row = [&](const S* qx, const S* qy, const S* pp, const float* w, int r,
-                            RowVals<S>& x) {
-            const bool ok = row_ok(r);
-            const int o = r * G.pitch + c;
-            x.qx = ok ? PS::ld(qx + o) : PS::zero();
-            x.qy = ok ? PS::ld(qy + o) : PS::zero();
-            x.p = ok ? PS::ld(pp + o) : PS::zero();
-            x.ps = ok ? PF::ld(s0.ps + o) : PF::zero();
-            x.w = ok ? PF::ld(w + o) : PF::zero();
-        };
-        // g = div q + p_i - p_s - u_i / c at row r, given the row above's q_y
-        // (outside the grid the loaded values are zero)
-        auto g_of = [&](const RowVals<S>& x, float2 qy_up, int r) {
-            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy), p = PS::f2(x.p);
-            const float2 ps = x.ps;
-            const float qx_left = __shfl_up_sync(full, qx.y, 1);
-            const float wy = row_w(r);
-            const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
-            float2 g;
-            g.x = qx.x - qx_left + wy * qy.x - qy_up.x + p.x - ps.x - u_e * K.inv_c;
-            g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + p.y - ps.y - u_o * K.inv_c;
-            return g;
-        };
+// Batched Potts ADMM by warp strips: the strip items of every strip-eligible
+// Potts instance of a batch in one table of (instance, item) pairs; a warp
+// takes its item's problem, state sets and coefficients from the instance's
+// descriptor and skips items of retired instances (per-instance convergence
+// mask).  parity 0: caller's buffers -> workspace, 1: back; first: the
+// chunk's first iteration reads u itself, later ones the w form.  Four
+// blocks per SM: each warp holds its instance's problem and coefficients in
+// registers (the single-problem kernel has them in the parameter bank), and
+// the bound keeps them from spilling.
+template <typename S, bool ANISO, bool ODDW>
+__global__ void __launch_bounds__(kStripWarps * 32, 4)
+    k_batch_potts_strip(const BatchDesc* __restrict__ desc, const int2* __restrict__ items,
+                        int nitems, int parity, int first) {
+    __shared__ float2 acc_s[kStripWarps][kStripRmax][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float2(*acc)[32] = acc_s[wib];
+    for (int it = blockIdx.x * kStripWarps + wib; it < nitems; it += gridDim.x * kStripWarps) {
+        const int2 e = items[it];
+        const BatchDesc* D = desc + e.x;
+        if (!D->active) continue;
+        const int nstrips = D->sp_nstrips, R = D->sp_rows;
+        const PottsStateV a = parity ? D->pw : D->pu, b = parity ? D->pu : D->pw;
+        const PottsProblem P = D->pp;
+        const AdmmCoef K = D->ak;
+        const int cs = (e.y % nstrips) * kStripOut;
+        const int r0 = (e.y / nstrips) * R;
+        const int r1 = min(r0 + R, P.g.H);
+        potts_strip_item<S, ANISO, kCostF32, ODDW>(P, a.as<S>(), b.as<S>(), K,
+                                                   first ? 0.f : K.cu, cs, r0, r1, acc, lane);
+    }
+}
 
-        // q^{k+1} = P_alpha(q + grad g / a) at row t of this pair, from g at
-        // rows t and t+1 (zero outside the grid)
-        struct QN {
-            float tx_e, tx_o, ty_e, ty_o;
-        };
-        auto q_new = [&](const RowVals<S>& x, float2 g_t, float2 g_b, float2 al, int t) {
-            const float g_r = __shfl_down_sync(full, g_t.x, 1);  // g(t, c+2)
-            const float my = row_w(t) * K.inv_a;
-            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
-            QN q;
-            q.tx_e = qx.x + (g_t.y - g_t.x) * K.inv_a;
-            q.tx_o = qx.y + (g_r - g_t.y) * (mxo * K.inv_a);
-            q.ty_e = qy.x + (g_b.x - g_t.x) * my;
-            q.ty_o = qy.y + (g_b.y - g_t.y) * my;
-            project_sel<ANISO>(q.tx_e, q.ty_e, al.x);
-            project_sel<ANISO>(q.tx_o, q.ty_o, al.y);
-            const bool in = colin && t >= 0 && t < G.H;
-            q.tx_e = in ? St::rt(q.tx_e) : 0.f;
-            q.tx_o = in ? St::rt(q.tx_o) : 0.f;
-            q.ty_e = in ? St::rt(q.ty_e) : 0.f;
-            q.ty_o = in ? St::rt(q.ty_o) : 0.f;
-            return q;
-        };
-
-    #pragma unroll 1
-        for (int l = 0; l < L; ++l) {
-            const size_t lo = (size_t)l * G.plane;
-            const S* qx0 = s0.qx + lo;
-            const S* qy0 = s0.qy + lo;
-            const S* p0 = s0.p + lo;
-            const float* w0 = s0.u + lo;
-            // costs of label l: its plane, or (I - c_l)^2 from the image plane
-            const float* Cb = CS == kCostLevels ? P.C : P.C + lo;
-            const __half* Ch = CS == kCostF16 ? P.C16 + lo : nullptr;
-            const float lev_l = CS == kCostLevels ? __ldg(P.lev + l) : 0.f;
-            S* qx1 = s1.qx + lo;
-            S* qy1 = s1.qy + lo;
-            S* p1o = s1.p + lo;
-            float* w1 = s1.u + lo;
-            auto row = [&](int r, RowVals<S>& x) { load_row(qx0, qy0, p0, w0, r, x); };
-            // costs at row r (zero outside the grid; never used there), a select
-            // rather than a branch on the lane's bounds
-            auto ld_c = [&](int r) {
-                const bool ok = row_ok(r);
-                float2 v;
-                if (CS == kCostF16)
-                    v = ok ? PH::f2(PH::ld(Ch + r * G.pitch + c)) : PF::zero();
-                else
-                    v = ok ? PF::ld(Cb + r * G.pitch + c) : PF::zero();
-                if (CS == kCostLevels) {
-                    v.x = (v.x - lev_l) * (v.x - lev_l);
-                    v.y = (v.y - lev_l) * (v.y - lev_l);
+// u_i = w_i + cu p_s on the owned pixels of every item of an active strip
+// instance (the state is in the caller's buffers after an even chunk).
+__global__ void k_batch_potts_strip_finalize(const BatchDesc* __restrict__ desc,
+                                             const int2* __restrict__ items, int nitems) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int it = blockIdx.x * kStripWarps + wib; it < nitems; it += gridDim.x * kStripWarps) {
+        const int2 e = items[it];
+        const BatchDesc* D = desc + e.x;
+        if (!D->active) continue;
+        const Grid G = D->pp.g;
+        const int cs = (e.y % D->sp_nstrips) * kStripOut;
+        const int r0 = (e.y / D->sp_nstrips) * D->sp_rows;
+        const int r1 = min(r0 + D->sp_rows, G.H);
+        const int c = cs - 2 + 2 * lane;
+        if (lane < 1 || lane > 30 || c >= G.W) continue;
+        const float cu = D->ak.cu;
+        float* u = D->pu.u;
+        const float* ps = D->pu.ps;
+        const bool pair = c + 1 < G.W;  // else the last column of an odd width alone
+        for (int r = r0; r < r1; ++r) {
+            const size_t k = G.idx(r, c);
+            if (pair) {
+                const float2 s = Pair<float>::ld(ps + k);
+                for (int l = 0; l < D->pp.L; ++l) {
+                    float2* q = reinterpret_cast<float2*>(u + (size_t)l * G.plane + k);
+                    float2 v = *q;
+                    v.x += cu * s.x;
+                    v.y += cu * s.y;
+                    *q = v;
                 }
-                return v;
-            };
-            auto ld_al = [&](int r) {
-                if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
-                return row_ok(r) ? PF::ld(P.alpha.plane + r * G.pitch + c) : PF::zero();
-            };
-            // d = div q^{k+1} at output row t from the new q of rows t and t-1,
-            // then p_i^{k+1}, w_i and this label's share of the p_s update
-            auto finish = [&](int t, const QN& q, float2 qy_up, const RowVals<S>& x, float2 cl,
-                              float2 g) {
-                const float txl = __shfl_up_sync(full, q.tx_o, 1);  // new q_x at c-1
-                const float wy = row_w(t);
-                const float d_e = q.tx_e - txl + wy * q.ty_e - qy_up.x;
-                const float d_o = mxo * q.tx_o - q.tx_e + wy * q.ty_o - qy_up.y;
-                const float2 pv = PS::f2(x.p), ps = x.ps;
-                const float u_e = fmaf(cu_in, ps.x, x.w.x), u_o = fmaf(cu_in, ps.y, x.w.y);
-                float sa_e = 0.f, sb_e = 0.f, sa_o = 0.f, sb_o = 0.f, v_e, v_o;
-                const float p1_e =
-                    potts_label_pu<S>(K, g.x, d_e, pv.x, ps.x, u_e, cl.x, sa_e, sb_e, v_e);
-                const float p1_o =
-                    potts_label_pu<S>(K, g.y, d_o, pv.y, ps.y, u_o, cl.y, sa_o, sb_o, v_o);
-                float2& ac = acc[t - r0][lane];
-                const float2 share = make_float2(sa_e + sb_e, sa_o + sb_o);
-                if (l == 0) {
-                    ac = share;
-                } else {
-                    ac.x += share.x;
-                    ac.y += share.y;
-                }
-                if (own) {
-                    const int o = t * G.pitch + c;
-                    PS::st(qx1 + o, q.tx_e, q.tx_o);
-                    PS::st(qy1 + o, q.ty_e, q.ty_o);
-                    PS::st(p1o + o, p1_e, p1_o);
-                    PF::st(w1 + o, v_e, v_o);
-                }
-            };
-
-            // top-down: step t makes q^{k+1} of row t and finishes row t;
-            // row t+2 is loaded during the step
-            RowVals<S> a, b, nx;
-            const int rm2 = r0 - 2;
-            const float2 qy_m2 =
-                PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c) : PS::zero());
-            row(r0 - 1, a);
-            row(r0, b);
-            float2 g_t = g_of(a, qy_m2, r0 - 1);
-            float2 qyn_up = make_float2(0.f, 0.f);  // new q_y of the row above
-            float2 al_t = ld_al(r0 - 1), cl_t = PF::zero(), al_n = al_t, cl_n = cl_t;
-    #pragma unroll 1
-            for (int t = r0 - 1; t < r1; ++t) {
-                if (t + 2 <= r1) row(t + 2, nx);
-                if (t + 1 < r1) {
-                    al_n = ld_al(t + 1);
-                    cl_n = ld_c(t + 1);
-                }
-                const float2 g_n = g_of(b, PS::f2(a.qy), t + 1);
-                const QN q = q_new(a, g_t, g_n, al_t, t);
-                if (t >= r0) finish(t, q, qyn_up, a, cl_t, g_t);
-                qyn_up = make_float2(q.ty_e, q.ty_o);
-                a = b;
-                b = nx;
-                g_t = g_n;
-                al_t = al_n;
-                cl_t = cl_n;
+            } else {
+                const float s = ps[k];
+                for (int l = 0; l < D->pp.L; ++l) u[(size_t)l * G.plane + k] += cu * s;
             }
         }
-
-        // p_s^{k+1} on the band from the summed label shares
-    #pragma unroll 1
-        for (int t = r0; t < r1; ++t) {
-            if (!own) continue;
-            const int o = t * G.pitch + c;
-            const float2 ps = PF::ld(s0.ps + o);
-            const float2 ac = acc[t - r0][lane];
-            PF::st(s1.ps + o, potts_ps_update(K, ps.x, ac.x, 0.f), potts_ps_update(K, ps.y, ac.y, 0.f));
-        }
     }
+}
+
+int potts_strip_max_rows() { return kStripRmax; }
+
+template <typename S, bool ANISO, bool ODDW>
+static cudaError_t launch_batch_strip(const BatchDesc* desc, const int2* items, int nitems,
+                                      int parity, int first, cudaStream_t st) {
+    auto kern = k_batch_potts_strip<S, ANISO, ODDW>;
+    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
+    long long resident = 0;
+    {
+        const cudaError_t e = strip::device_resident_warps(memo, kern, 0, resident);
+        if (e != cudaSuccess) return e;
+    }
+    const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
+    const int grid = blocks < resident / kStripWarps ? blocks : resident / kStripWarps;
+    kern<<<grid, kStripWarps * 32, 0, st>>>(desc, items, nitems, parity, first);
+    return cudaGetLastError();
+}
+
+template <bool ODDW>
+static cudaError_t batch_strip_step_o(int storage, bool aniso, const BatchDesc* desc,
+                                      const int2* items, int nitems, int parity, int first,
+                                      cudaStream_t st) {
+    switch (storage) {
+        case CMF_F32:
+            return aniso ? launch_batch_strip<float, true, ODDW>(desc, items, nitems, parity, first, st)
+                         : launch_batch_strip<float, false, ODDW>(desc, items, nitems, parity, first,
+                                                                  st);
+        case CMF_F16:
+            return aniso ? launch_batch_strip<__half, true, ODDW>(desc, items, nitems, parity, first,
+                                                                  st)
+                         : launch_batch_strip<__half, false, ODDW>(desc, items, nitems, parity,
+                                                                   first, st);
+        default:
+            return aniso ? launch_batch_strip<__nv_bfloat16, true, ODDW>(desc, items, nitems, parity,
+                                                                         first, st)
+                         : launch_batch_strip<__nv_bfloat16, false, ODDW>(desc, items, nitems,
+                                                                          parity, first, st);
+    }
+}
+
+cudaError_t batch_potts_strip_step(int storage, bool aniso, bool odd_width, const BatchDesc* desc,
+                                   const int2* items, int nitems, int parity, int first,
+                                   cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    return odd_width
+               ? batch_strip_step_o<true>(storage, aniso, desc, items, nitems, parity, first, st)
+               : batch_strip_step_o<false>(storage, aniso, desc, items, nitems, parity, first, st);
+}
+
+cudaError_t batch_potts_strip_finalize(const BatchDesc* desc, const int2* items, int nitems,
+                                       cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
+    const int grid = blocks < 8 * sms ? blocks : 8 * sms;
+    k_batch_potts_strip_finalize<<<grid, kStripWarps * 32, 0, st>>>(desc, items, nitems);
+    return cudaGetLastError();
 }
 
 // rPDRQ by warp strips (Eq. pdrq:4labels, general L).  Per band: phase 1
@@ -453,8 +627,9 @@ __global__ void k_potts_strip_finalize(Grid G, int L, float* u, const float* ps,
 // ---- host side -------------------------------------------------------------
 
 bool potts_strip_eligible(const Grid& G, int storage, const float* C, const float* alpha,
-                          const PottsStateV& a, const PottsStateV& b) {
-    if (G.W % 2 || G.pitch % 2) return false;
+                          const PottsStateV& a, const PottsStateV& b, bool odd_width_ok) {
+    if ((G.W % 2 && !odd_width_ok) || G.pitch % 2) return false;
+    if (G.W % 2 && G.pitch < G.W + 1) return false;  // the last pair reads column W
     if ((size_t)G.H * (size_t)G.pitch > (size_t)INT_MAX) return false;
     const size_t es2 = 2 * dtype_size(storage);
     auto al = [](const void* p, size_t n) { return ((uintptr_t)p % n) == 0; };

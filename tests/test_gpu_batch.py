@@ -1,7 +1,9 @@
 """Batched solve (many instances of uneven size and label count in one
 device-driven loop) against the single-instance solver run with the same
-shared-memory tile kernels: identical iteration counts and states within
-float32 rounding, each instance certified by the FP64 oracle."""
+kernels (warp strips for Potts instances of even width under the ADMM
+algorithms, shared-memory tiles for the others): identical iteration counts
+and states within float32 rounding, each instance certified by the FP64
+oracle."""
 import numpy as np
 import pytest
 import torch
@@ -54,6 +56,8 @@ def test_batch_matches_single_solves(cmf, algo):
         # the batch shares p (sigma, tau, c, ...) and takes a2 = max(a2, 2L)
         q = cmf.default_params(algo, 2, **kw)
         q.a2 = max(q.a2, 2.0 * inst.L)
+        if inst.kind == "potts" and inst.W % 2 == 0 and algo != 3:
+            q.variant = 2  # the batch runs this instance by warp strips
         single = _alloc(cmf, inst, q)
         if inst.kind == "binary":
             st, it, hist = cmf.cmf_solve_binary(single)
@@ -87,3 +91,54 @@ def test_batch_rejects_bad_parameters(cmf):
         p = cmf.default_params(2, 2, **bad)
         with pytest.raises(cmf.CmfError):
             cmf.cmf_solve_batch(items, p)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_batch_strip_instances_float16(cmf, storage):
+    """Even-width Potts instances run by warp strips inside the batch: the
+    same iteration counts and states as single strip solves, in float32 and
+    with float16 flows."""
+    insts = [synth.potts_shapes(120, 88, 8, seed=104), synth.potts_shapes(33, 150, 4, seed=105),
+             synth.potts_shapes(64, 64, 3, seed=107)]
+    kw = dict(tol_gap=2e-3 if storage else 1e-4, max_iter=20000, check_every=10,
+              storage=storage)
+    p = cmf.default_params(2, 2, **kw)
+    items = [cmf.alloc_potts(i, p) for i in insts]
+    status, res = cmf.cmf_solve_batch(items, p)
+    assert status == cmf.OK, res
+    for inst, item, r in zip(insts, items, res):
+        q = cmf.default_params(2, 2, variant=2, **kw)
+        q.a2 = max(q.a2, 2.0 * inst.L)
+        single = cmf.alloc_potts(inst, q)
+        st, it, hist = cmf.cmf_solve_potts(single)
+        assert st == cmf.OK and it == r["iters"], (it, r["iters"])
+        a, b = item.state(), single.state()
+        # the two kernels compile the same item arithmetic separately (their
+        # coefficients come from registers or from the parameter bank), so
+        # float32 results may differ in the last bit; float16 storage turns
+        # that into a few units in the last place of the stored flows
+        for k in a:
+            assert np.abs(a[k] - b[k]).max() <= (1e-5 if storage == 0 else 8e-3), k
+        assert r["gap"] <= kw["tol_gap"] and hist[-1, 3] <= kw["tol_gap"]
+
+
+@pytest.mark.parametrize("algo", [0, 2, 4, 5])
+def test_batch_strip_odd_widths_match_oracle(cmf, algo):
+    """Potts instances of odd width run by warp strips inside the batch (the
+    last pair masked): after a fixed number of iterations every instance
+    matches the FP64 oracle element by element (float32 state, 1e-4)."""
+    insts = [synth.potts_shapes(37, 71, 3, seed=111), synth.potts_shapes(66, 129, 8, seed=112),
+             synth.potts_shapes(45, 60, 4, seed=113), synth.config5(33, 181)]
+    kw = dict(tol_gap=0.0, max_iter=40, check_every=10)
+    if algo == 5:
+        kw["tau"] = 1.0 / (25 * 0.4)
+    p = cmf.default_params(algo, 2, **kw)
+    items = [cmf.alloc_potts(i, p) for i in insts]
+    status, res = cmf.cmf_solve_batch(items, p)
+    assert status == cmf.NOT_CONVERGED and all(r["iters"] == 40 for r in res)
+    for inst, item in zip(insts, items):
+        q = O.default_params(algo, inst.L, a2=max(p.a2, 2.0 * inst.L), sigma=p.sigma, tau=p.tau)
+        ref = O.potts_run(inst.costs, inst.alpha, q, 40)
+        got = item.state()
+        for k in ("u", "qx", "qy", "p", "ps"):
+            assert np.abs(got[k] - ref[k]).max() <= 1e-4, (inst.W, k)
