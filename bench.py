@@ -274,6 +274,13 @@ KERNEL_CASES = {
     "potts16-admm-2048-f16": ("potts", 2, 2048, 2048, 16, 1, 0),
     "potts16-admm-4096-f16": ("potts", 2, 4096, 4096, 16, 1, 0),
     "potts16-admm-2048-f32": ("potts", 2, 2048, 2048, 16, 0, 0),
+    "potts16-admm-1024-f32": ("potts", 2, 1024, 1024, 16, 0, 0),
+    "potts16-admm-1024-f16": ("potts", 2, 1024, 1024, 16, 1, 0),
+    "potts16-eval-1024-f32": ("potts-eval", 2, 1024, 1024, 16, 0, 0),
+    # one two-phase solve of the 4096^2 workload (the bench's step), for a launch list
+    "potts16-solve-4096": ("potts-solve", 2, 4096, 4096, 16, 0, 0),
+    # the same solve host-driven (use_graph = 0): a profiler sees every launch
+    "potts16-solve-host-4096": ("potts-solve-host", 2, 4096, 4096, 16, 0, 0),
     "potts16-admm-4096-f32": ("potts", 2, 4096, 4096, 16, 0, 0),
     "potts16-eval-2048-f32": ("potts-eval", 2, 2048, 2048, 16, 0, 0),
     "potts4-plain-2048": ("potts", 2, 2048, 2048, 4, 0, 1),
@@ -379,6 +386,30 @@ def potts16_other_forms(cmf, inst, flush) -> dict:
                      "ms_per_iter": round(ms / iters, 4)}
         del s
     return out
+
+
+def tuned_step(cmf, inst, flush) -> dict:
+    """The step-size search: cmf_autotune_potts with tune_step = 1 (c, 2c, 4c,
+    8c beside the launch variants) on the 1024^2 instance of the recipe, then
+    one two-phase solve of the 4096^2 instance with the chosen c."""
+    small = rank_instance(0, 1024)
+    p = cmf.default_params(FLAGSHIP, L, tol_gap=TOL, max_iter=MAX_ITER, check_every=CHECK_EVERY,
+                           phase_storage=PHASE_STORAGE, phase_gap=PHASE_GAP, tune_step=1)
+    s = cmf.alloc_potts(small, p)
+    t0 = time.perf_counter()
+    best, ms_small = cmf.cmf_autotune_potts(s)
+    tune_s = time.perf_counter() - t0
+    del s
+    q = cmf.default_params(FLAGSHIP, L, tol_gap=TOL, max_iter=MAX_ITER, check_every=CHECK_EVERY,
+                           phase_storage=PHASE_STORAGE, phase_gap=PHASE_GAP, c=best.c,
+                           variant=best.variant)
+    g = cmf.alloc_potts(inst, q)
+    flush.zero_()
+    ms, (st, iters, hist) = _timed(lambda: cmf.cmf_solve_potts(g))
+    del g
+    return {"c": best.c, "variant": best.variant, "tuned_on": "1024x1024 instance of the recipe",
+            "tuning_s": round(tune_s, 1), "time_to_gap_ms": round(ms, 1), "iterations": iters,
+            "converged": st == cmf.OK, "final_gap": float(hist[-1, 3])}
 
 
 def batch_workload(cmf, synth, flush) -> dict:
@@ -555,6 +586,14 @@ def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int =
     __graft_entry__.build()
     model, algo, h, w, nl, storage, impl = KERNEL_CASES[name]
     p = cmf.default_params(algo, nl, storage=storage, impl=impl, variant=variant)
+    if model in ("potts-solve", "potts-solve-host"):
+        q = cmf.default_params(FLAGSHIP, nl, tol_gap=TOL, max_iter=MAX_ITER,
+                               check_every=CHECK_EVERY, phase_storage=PHASE_STORAGE,
+                               phase_gap=PHASE_GAP, use_graph=int(model == "potts-solve"))
+        st = cmf.alloc_potts(rank_instance(0, h), q)
+        print(name, cmf.cmf_solve_potts(st)[:2])
+        torch.cuda.synchronize()
+        return
     if model == "binary-solve":
         p.use_graph = 0
         b = cmf.alloc_binary(synth.config2(h, w), p)
@@ -764,6 +803,7 @@ def main():
     side = {}
     if rank == 0 and not args.skip_side:
         side["potts16_float32_flows"] = potts16_other_forms(cmf, inst, flush)
+        side["potts16_tuned_step"] = tuned_step(cmf, inst, flush)
         side["oracle_check"] = oracle_checks(cmf, s, inst, flush)
         del s
         torch.cuda.empty_cache()
