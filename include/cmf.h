@@ -381,7 +381,9 @@ cmf_status cmf_autotune_potts(const float *d_C, int L, const float *d_alpha, flo
 /* conditional WHILE node repeats {check_every iterations of every active   */
 /* instance, certificates, per-instance stop test}).  Converged instances   */
 /* stop iterating (per-instance convergence masks); the loop ends when all  */
-/* have converged or reached max_iter.                                     */
+/* have converged or reached max_iter.  p->use_graph = 0 runs the same      */
+/* chunks host-driven (the stop flag read back after each), with the same   */
+/* results: for profilers and drivers without conditional graph nodes.      */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {

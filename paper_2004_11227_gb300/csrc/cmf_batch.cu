@@ -151,8 +151,10 @@ __global__ void k_batch_reduce(const BatchDesc* desc, const double* partials, do
 }
 
 // One block: retire converged instances, decide whether the loop runs again.
+// set_h = 0: a host-driven loop (no graph), which reads ctl->stop instead.
 __global__ void k_batch_decide(BatchDesc* desc, int n, const double* scal, BatchCtl* ctl, int K,
-                               int max_iter, double tol, cudaGraphConditionalHandle h) {
+                               int max_iter, double tol, cudaGraphConditionalHandle h,
+                               int set_h) {
     const int it = ctl->it + K;
     int any = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -179,7 +181,7 @@ __global__ void k_batch_decide(BatchDesc* desc, int n, const double* scal, Batch
     if (threadIdx.x == 0) {
         ctl->it = it;
         ctl->stop = any ? 0 : 1;
-        cudaGraphSetConditional(h, any ? 1u : 0u);
+        if (set_h) cudaGraphSetConditional(h, any ? 1u : 0u);
     }
 }
 
@@ -358,6 +360,73 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
     k_batch_reset<<<1, 256, 0, st>>>(d_desc, n, ctl);
     CMF_CUDA_TRY(cudaGetLastError());
 
+    // one chunk: check_every iterations of every active instance, the
+    // certificates and the per-instance stop decision
+    auto enqueue_chunk = [&](cudaStream_t s, cudaGraphConditionalHandle h,
+                             int set_h) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < p->check_every && e == cudaSuccess; ++k) {
+            const int parity = k & 1;
+            if (!tb.empty())
+                e = batch_binary_step(p->storage, aniso, dr, p->sweeps, d_desc, d_tb,
+                                      (int)tb.size(), parity, s);
+            if (e == cudaSuccess && !tp.empty())
+                e = batch_potts_step(p->storage, aniso, dr, p->sweeps, B.potts_rows, B.max_l,
+                                     d_desc, d_tp, (int)tp.size(), parity, s);
+            if (e == cudaSuccess && !sitems.empty())
+                e = batch_potts_strip_step(p->storage, aniso, false, d_desc, d_items,
+                                           (int)sitems.size(), parity, k == 0, s);
+            if (e == cudaSuccess && !oitems.empty())
+                e = batch_potts_strip_step(p->storage, aniso, true, d_desc, d_oitems,
+                                           (int)oitems.size(), parity, k == 0, s);
+        }
+        // the strip instances hold w = u - cu p_s after the chunk: back to u
+        // (both tables are contiguous in the workspace)
+        const int nall = (int)(sitems.size() + oitems.size());
+        if (e == cudaSuccess && nall > 0)
+            e = batch_potts_strip_finalize(d_desc, d_items, nall, s);
+        if (e == cudaSuccess && !eb.empty())
+            e = batch_binary_eval(p->storage, aniso, dr, (float)p->tau, d_desc, d_eb,
+                                  (int)eb.size(), partials, s);
+        if (e == cudaSuccess && !ep.empty())
+            e = batch_potts_eval(p->storage, aniso, dr, (float)p->tau, d_desc, d_ep,
+                                 (int)ep.size(), partials, s);
+        if (e == cudaSuccess) {
+            k_batch_reduce<<<n, 256, 0, s>>>(d_desc, partials, scal);
+            k_batch_decide<<<1, 256, 0, s>>>(d_desc, n, scal, ctl, p->check_every, p->max_iter,
+                                              p->tol_gap, h, set_h);
+            e = cudaGetLastError();
+        }
+        return e;
+    };
+    auto collect = [&]() -> cmf_status {
+        bool all_ok = true;
+        for (int i = 0; i < n; ++i) {
+            inst[i].iters = desc[i].iters;
+            inst[i].status = desc[i].status;
+            inst[i].energy = desc[i].energy;
+            inst[i].dual = desc[i].dual;
+            inst[i].gap = desc[i].gap;
+            inst[i].res = desc[i].res;
+            all_ok = all_ok && desc[i].status == CMF_OK;
+        }
+        return all_ok ? CMF_OK : CMF_NOT_CONVERGED;
+    };
+    if (!p->use_graph) {
+        // host-driven: one chunk per round trip, the stop flag read back
+        for (;;) {
+            CMF_CUDA_TRY(enqueue_chunk(st, 0, 0));
+            BatchCtl hc;
+            CMF_CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+            CMF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hc.stop) break;
+        }
+        CMF_CUDA_TRY(cudaMemcpyAsync(desc.data(), d_desc, sizeof(BatchDesc) * n,
+                                     cudaMemcpyDeviceToHost, st));
+        CMF_CUDA_TRY(cudaStreamSynchronize(st));
+        return collect();
+    }
+
     cudaStream_t cs = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
@@ -379,39 +448,7 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
         if (cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed) != cudaSuccess)
             break;
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k < p->check_every && e == cudaSuccess; ++k) {
-            const int parity = k & 1;
-            if (!tb.empty())
-                e = batch_binary_step(p->storage, aniso, dr, p->sweeps, d_desc, d_tb,
-                                      (int)tb.size(), parity, cs);
-            if (e == cudaSuccess && !tp.empty())
-                e = batch_potts_step(p->storage, aniso, dr, p->sweeps, B.potts_rows, B.max_l,
-                                     d_desc, d_tp, (int)tp.size(), parity, cs);
-            if (e == cudaSuccess && !sitems.empty())
-                e = batch_potts_strip_step(p->storage, aniso, false, d_desc, d_items,
-                                           (int)sitems.size(), parity, k == 0, cs);
-            if (e == cudaSuccess && !oitems.empty())
-                e = batch_potts_strip_step(p->storage, aniso, true, d_desc, d_oitems,
-                                           (int)oitems.size(), parity, k == 0, cs);
-        }
-        // the strip instances hold w = u - cu p_s after the chunk: back to u
-        // (both tables are contiguous in the workspace)
-        const int nall = (int)(sitems.size() + oitems.size());
-        if (e == cudaSuccess && nall > 0)
-            e = batch_potts_strip_finalize(d_desc, d_items, nall, cs);
-        if (e == cudaSuccess && !eb.empty())
-            e = batch_binary_eval(p->storage, aniso, dr, (float)p->tau, d_desc, d_eb,
-                                  (int)eb.size(), partials, cs);
-        if (e == cudaSuccess && !ep.empty())
-            e = batch_potts_eval(p->storage, aniso, dr, (float)p->tau, d_desc, d_ep,
-                                 (int)ep.size(), partials, cs);
-        if (e == cudaSuccess) {
-            k_batch_reduce<<<n, 256, 0, cs>>>(d_desc, partials, scal);
-            k_batch_decide<<<1, 256, 0, cs>>>(d_desc, n, scal, ctl, p->check_every, p->max_iter,
-                                              p->tol_gap, h);
-            e = cudaGetLastError();
-        }
+        const cudaError_t e = enqueue_chunk(cs, h, 1);
         cudaGraph_t captured = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
         if (e != cudaSuccess || e2 != cudaSuccess) break;
@@ -421,17 +458,7 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
                             st) != cudaSuccess)
             break;
         if (cudaStreamSynchronize(st) != cudaSuccess) break;
-        bool all_ok = true;
-        for (int i = 0; i < n; ++i) {
-            inst[i].iters = desc[i].iters;
-            inst[i].status = desc[i].status;
-            inst[i].energy = desc[i].energy;
-            inst[i].dual = desc[i].dual;
-            inst[i].gap = desc[i].gap;
-            inst[i].res = desc[i].res;
-            all_ok = all_ok && desc[i].status == CMF_OK;
-        }
-        status = all_ok ? CMF_OK : CMF_NOT_CONVERGED;
+        status = collect();
     } while (0);
     if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);

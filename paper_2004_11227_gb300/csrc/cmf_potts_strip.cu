@@ -52,9 +52,13 @@ struct RowVals {
 // flow storage S.  Arguments by value: the caller's copies stay in registers
 // or the parameter bank.  ODDW: the grid may have an odd width; the pair of
 // its last column is (W-1, W), whose second element falls on the padding
-// column: it is loaded as zero and never stored, and the last column's own
-// x-difference gets weight zero (the single-problem solver takes even widths
-// only and compiles without these masks).
+// column.  That element is loaded as it is (whatever the padding holds) and
+// never stored; the one value of it that reaches a grid column, g at the
+// padding column (through the last column's x-difference, whose weight is
+// zero), is selected to zero after it is computed.  Masking the loaded values
+// instead would consume each prefetched row as soon as it is loaded (measured:
+// twice the time per item).  The single-problem solver takes even widths only
+// and compiles without these masks.
 template <typename S, bool ANISO, int CS, bool ODDW = false>
 __device__ __forceinline__ void potts_strip_item(const PottsProblem P, const PottsState<S> s0,
                                                  const PottsState<S> s1, const AdmmCoef K,
@@ -88,13 +92,6 @@ __device__ __forceinline__ void potts_strip_item(const PottsProblem P, const Pot
         x.p = ok ? PS::ld(pp + o) : PS::zero();
         x.ps = ok ? PF::ld(s0.ps + o) : PF::zero();
         x.w = ok ? PF::ld(w + o) : PF::zero();
-        if (ODDW && !oddin) {
-            x.qx = PS::lo(x.qx);
-            x.qy = PS::lo(x.qy);
-            x.p = PS::lo(x.p);
-            x.ps.y = 0.f;
-            x.w.y = 0.f;
-        }
     };
     // g = div q + p_i - p_s - u_i / c at row r, given the row above's q_y
     // (outside the grid the loaded values are zero)
@@ -107,6 +104,7 @@ __device__ __forceinline__ void potts_strip_item(const PottsProblem P, const Pot
         float2 g;
         g.x = qx.x - qx_left + wy * qy.x - qy_up.x + p.x - ps.x - u_e * K.inv_c;
         g.y = mxo * qx.y - qx.x + wy * qy.y - qy_up.y + p.y - ps.y - u_o * K.inv_c;
+        if (ODDW) g.y = oddin ? g.y : 0.f;  // the padding column: finite, weight zero
         return g;
     };
 
@@ -163,14 +161,11 @@ __device__ __forceinline__ void potts_strip_item(const PottsProblem P, const Pot
                 v.x = (v.x - lev_l) * (v.x - lev_l);
                 v.y = (v.y - lev_l) * (v.y - lev_l);
             }
-            if (ODDW && !oddin) v.y = 0.f;
             return v;
         };
         auto ld_al = [&](int r) {
             if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
-            float2 v = row_ok(r) ? PF::ld(P.alpha.plane + r * G.pitch + c) : PF::zero();
-            if (ODDW && !oddin) v.y = 0.f;
-            return v;
+            return row_ok(r) ? PF::ld(P.alpha.plane + r * G.pitch + c) : PF::zero();
         };
         // d = div q^{k+1} at output row t from the new q of rows t and t-1,
         // then p_i^{k+1}, w_i and this label's share of the p_s update
@@ -216,9 +211,7 @@ __device__ __forceinline__ void potts_strip_item(const PottsProblem P, const Pot
         RowVals<S> a, b, nx;
         const int rm2 = r0 - 2;
         const float2 qy_m2 =
-            PS::f2((colin && rm2 >= 0) ? (oddin ? PS::ld(qy0 + rm2 * G.pitch + c)
-                                            : PS::lo(PS::ld(qy0 + rm2 * G.pitch + c)))
-                                   : PS::zero());
+            PS::f2((colin && rm2 >= 0) ? PS::ld(qy0 + rm2 * G.pitch + c) : PS::zero());
         row(r0 - 1, a);
         row(r0, b);
         float2 g_t = g_of(a, qy_m2, r0 - 1);
@@ -281,12 +274,13 @@ __global__ void __launch_bounds__(kStripWarps * 32, 7)
 // takes its item's problem, state sets and coefficients from the instance's
 // descriptor and skips items of retired instances (per-instance convergence
 // mask).  parity 0: caller's buffers -> workspace, 1: back; first: the
-// chunk's first iteration reads u itself, later ones the w form.  Four
+// chunk's first iteration reads u itself, later ones the w form.  Three
 // blocks per SM: each warp holds its instance's problem and coefficients in
-// registers (the single-problem kernel has them in the parameter bank), and
-// the bound keeps them from spilling.
+// registers (the single-problem kernel has them in the parameter bank); at
+// four the 128-register bound spilled, and the spill reloads sat on the row
+// pipeline (measured: 4% slower for even widths, 2x for odd ones).
 template <typename S, bool ANISO, bool ODDW>
-__global__ void __launch_bounds__(kStripWarps * 32, 4)
+__global__ void __launch_bounds__(kStripWarps * 32, 3)
     k_batch_potts_strip(const BatchDesc* __restrict__ desc, const int2* __restrict__ items,
                         int nitems, int parity, int first) {
     __shared__ float2 acc_s[kStripWarps][kStripRmax][32];

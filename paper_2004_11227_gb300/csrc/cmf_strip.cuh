@@ -28,7 +28,6 @@ struct Pair<float> {
         __stcs(reinterpret_cast<float2*>(p), make_float2(a, b));
     }
     static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
-    static __device__ __forceinline__ T lo(T v) { return make_float2(v.x, 0.f); }
     static __device__ __forceinline__ float2 f2(T v) { return v; }
     static __device__ __forceinline__ void st(float* p, float a, float b) {
         *reinterpret_cast<float2*>(p) = make_float2(a, b);
@@ -49,9 +48,6 @@ struct Pair<__half> {
         __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(a, b));
     }
     static __device__ __forceinline__ T zero() { return __float2half2_rn(0.f); }
-    static __device__ __forceinline__ T lo(T v) {
-        return __halves2half2(__low2half(v), __float2half_rn(0.f));
-    }
     static __device__ __forceinline__ float2 f2(T v) { return __half22float2(v); }
     static __device__ __forceinline__ void st(__half* p, float a, float b) {
         *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
@@ -71,9 +67,6 @@ struct Pair<__nv_bfloat16> {
         __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(a, b));
     }
     static __device__ __forceinline__ T zero() { return __float2bfloat162_rn(0.f); }
-    static __device__ __forceinline__ T lo(T v) {
-        return __halves2bfloat162(__low2bfloat16(v), __float2bfloat16_rn(0.f));
-    }
     static __device__ __forceinline__ float2 f2(T v) { return __bfloat1622float2(v); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
         *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);

@@ -142,3 +142,53 @@ def test_batch_strip_odd_widths_match_oracle(cmf, algo):
         got = item.state()
         for k in ("u", "qx", "qy", "p", "ps"):
             assert np.abs(got[k] - ref[k]).max() <= 1e-4, (inst.W, k)
+
+
+@pytest.mark.parametrize("algo", [2, 3])
+def test_batch_host_driven_loop_equals_graph(cmf, algo):
+    """use_graph = 0 runs the batch's chunks host-driven: the same kernels in
+    the same order, so the same iteration counts, certificates and states bit
+    for bit as the device-driven graph."""
+    insts = _instances() + [synth.potts_shapes(45, 61, 4, seed=114)]
+    out = []
+    for g in (1, 0):
+        p = cmf.default_params(algo, 2, tol_gap=1e-4, max_iter=20000, check_every=10,
+                               use_graph=g)
+        items = [_alloc(cmf, i, p) for i in insts]
+        status, res = cmf.cmf_solve_batch(items, p)
+        assert status == cmf.OK, res
+        out.append((res, [it.state() for it in items]))
+    (r1, s1), (r0, s0) = out
+    for a, b in zip(r1, r0):
+        assert a["iters"] == b["iters"] and a["gap"] == b["gap"], (a, b)
+    for a, b in zip(s1, s0):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("algo", [0, 2])
+def test_batch_strip_odd_widths_ignore_the_padding_column(cmf, algo):
+    """The padding column next to an odd width is read by the strip kernel's
+    last pair but must not reach the grid: with NaN in every padding column
+    of the costs, alpha and the caller's state, the batch still matches the
+    FP64 oracle element by element and its certificates stay finite."""
+    insts = [synth.potts_shapes(37, 71, 3, seed=111), synth.config5(33, 181)]
+    kw = dict(tol_gap=0.0, max_iter=40, check_every=10)
+    p = cmf.default_params(algo, 2, **kw)
+    items = [cmf.alloc_potts(i, p) for i in insts]
+    nan = float("nan")
+    for it in items:
+        assert it.W % 2 == 1 and it.pitch > it.W
+        for t in (it.C, it.u, it.qx, it.qy, it.p, it.ps):
+            t[..., it.W:] = nan
+        if isinstance(it.alpha, torch.Tensor):
+            it.alpha[..., it.W:] = nan
+    status, res = cmf.cmf_solve_batch(items, p)
+    assert status == cmf.NOT_CONVERGED and all(r["iters"] == 40 for r in res)
+    assert all(np.isfinite(r["gap"]) for r in res), res
+    for inst, item in zip(insts, items):
+        q = O.default_params(algo, inst.L, a2=max(p.a2, 2.0 * inst.L))
+        ref = O.potts_run(inst.costs, inst.alpha, q, 40)
+        got = item.state()
+        for k in ("u", "qx", "qy", "p", "ps"):
+            assert np.abs(got[k] - ref[k]).max() <= 1e-4, (inst.W, k)
