@@ -25,6 +25,7 @@ struct WsLayout {
     size_t state;     // second state buffer set (ping-pong of the fused form)
     size_t state2;    // third set (binary fused form: routes two-iteration launches)
     size_t tmp;       // float planes used by the plain form
+    size_t usum;      // two float planes of sum_i u_i (Potts rPDRQ by warp strips)
     size_t partials;  // 3 doubles per certificate block
     size_t scalars;   // 4 doubles
     size_t ctl;       // solve-loop control block (graph path)
@@ -60,6 +61,10 @@ WsLayout ws_layout(int H, int W, int L, int pitch, const cmf_params& p, bool pot
     // plain forms: g and div q^{k+1} (per label for Potts); the fused kernels
     // keep everything on chip
     off += align_up(plane * 4 * (size_t)(p.impl == CMF_PLAIN ? (potts ? 2 * L : 2) : 0));
+    w.usum = off;
+    // fused Potts rPDRQ: each launch writes sum_i u_i of its output for the
+    // next launch (ping-pong)
+    if (potts && p.algo == CMF_RPDRQ && p.impl == CMF_FUSED) off += 2 * align_up(plane * 4);
     w.partials = off;
     {
         // one triple per certificate block: the certificate kernels' grid, or
@@ -539,7 +544,13 @@ cudaError_t potts_run(const PottsCall& c, int n, int& cur, cudaStream_t st, int 
         } else if (c.strip && cfg.dr) {
             const PottsStateV& a = cur == 0 ? c.user : c.ws;
             const PottsStateV& b = cur == 0 ? c.ws : c.user;
-            cudaError_t e = potts_dr_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.dc, st);
+            // sum_i u_i planes: the call's first launch sums u itself, later
+            // ones read what the previous launch wrote
+            float* U = (float*)(c.wsbase + c.w.usum);
+            const size_t up = align_up((size_t)c.P.g.H * (size_t)c.P.g.pitch * 4) / 4;
+            cudaError_t e = potts_dr_strip_step(c.storage, c.P, a, b, cfg.aniso, cfg.dc,
+                                                i == 0 ? nullptr : U + cur * up,
+                                                U + (cur ^ 1) * up, st);
             if (e != cudaSuccess) return e;
             cur ^= 1;
         } else if (c.strip) {

@@ -247,22 +247,25 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             // half-sweep stages on rows m-1 .. m-NS
 #pragma unroll
             for (int st = 0; st < NS; ++st) {
+                // j, and so the colour, is the same for the whole warp: one
+                // branch, one shuffle per stage
                 const int j = m - 1 - st;
+                if (j < 0 || j >= G.H) continue;
                 const bool red = (st & 1) == 0;          // red: (row + col) even
                 const bool act_e = ((j & 1) == 0) == red;  // the pair's even column is active
                 const float2 cur = V[st + 1], up = V[st + 2], dn = V[st];
-                const float left = __shfl_up_sync(full, cur.y, 1);   // u(j, c-1)
-                const float right = __shfl_down_sync(full, cur.x, 1);  // u(j, c+2)
                 const float ncy = (j > 0 ? 1.f : 0.f) + (j < G.H - 1 ? 1.f : 0.f);
                 const float2 bj = Bh[st + 1];
-                if (ok_row(j)) {
-                    if (act_e) {
-                        const float sum = left + cur.y + up.x + dn.x;
-                        V[st + 1].x = (bj.x * D.inv_st + sum) / (D.kappa + ncx_e + ncy);
-                    } else {
-                        const float sum = cur.x + right + up.y + dn.y;
-                        V[st + 1].y = (bj.y * D.inv_st + sum) / (D.kappa + ncx_o + ncy);
-                    }
+                if (act_e) {
+                    const float left = __shfl_up_sync(full, cur.y, 1);  // u(j, c-1)
+                    const float v = __fdividef(bj.x * D.inv_st + (left + cur.y + up.x + dn.x),
+                                               D.kappa + ncx_e + ncy);
+                    if (colin) V[st + 1].x = v;
+                } else {
+                    const float right = __shfl_down_sync(full, cur.x, 1);  // u(j, c+2)
+                    const float v = __fdividef(bj.y * D.inv_st + (cur.x + right + up.y + dn.y),
+                                               D.kappa + ncx_o + ncy);
+                    if (colin) V[st + 1].y = v;
                 }
             }
             // finish row t = m - NS - 1: flows, reflections, outputs

@@ -373,9 +373,11 @@ cudaError_t potts_eval_strip(int storage, const PottsProblem& P, const PottsStat
                              bool aniso, bool dr, float tau, double* partials, cudaStream_t st,
                              const EvalTail& T);
 // rPDRQ iteration a -> b with the pipelined red-black sweeps (all labels).
+// U_in: sum_i u_i of state a (a plane), or null to sum it from a's u planes;
+// U_out: receives sum_i u_i of state b (the next launch's U_in), or null.
 cudaError_t potts_dr_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
                                 const PottsStateV& b, bool aniso, const DrCoef& D,
-                                cudaStream_t st);
+                                const float* U_in, float* U_out, cudaStream_t st);
 // s.u_i += cu * s.p_s on every label (w back to u).
 cudaError_t potts_strip_finalize(int storage, const PottsProblem& P, const PottsStateV& s,
                                  float cu, cudaStream_t st);

@@ -403,209 +403,6 @@ cudaError_t batch_potts_strip_finalize(const BatchDesc* desc, const int2* items,
     return cudaGetLastError();
 }
 
-// rPDRQ by warp strips (Eq. pdrq:4labels, general L).  Per band: phase 1
-// sums u_j^k over the labels for the band's rows and the pipeline's halo rows
-// (shared memory); phase 2 runs, label by label, the binary kernel's pipeline
-// (b_i = -sigma (div qbar_i + pbar_i - pbar_s) + sigma tau (L u_i - U), red-black
-// sweeps for sigma tau ((L+1) I - Lap), flow steps and reflections of q_i and
-// p_i) and sums the new u_i per pixel (shared memory); phase 3 reflects p_s
-// with p_s = pbar_s - tau sum_i u_i.  Dynamic shared memory per warp:
-// (R + 2S + 1) rows of U and R rows of the new sum, one float2 per lane.
-template <typename S, bool ANISO, int SW>
-__global__ void __launch_bounds__(kStripWarps * 32)
-    k_potts_dr_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, DrCoef D, int R,
-                     int nstrips, int nitems) {
-    constexpr int NS = 1 + 2 * SW;
-    constexpr int HL = SW + 1;
-    constexpr int OUT = 2 * (32 - 2 * HL);
-    using PS = Pair<S>;
-    using PF = Pair<float>;
-    extern __shared__ float2 dyn_s[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int RU = R + 2 * NS + 1;
-    float2* Us = dyn_s + (size_t)wib * (RU + R) * 32;  // U of rows r0-NS .. r1+NS
-    float2* Ns = Us + (size_t)RU * 32;                  // sum of the new u_i, band rows
-    const Grid G = P.g;
-    const int L = P.L;
-    const float stL = D.sigma * D.tau * (float)L, st_ = D.sigma * D.tau;
-    const unsigned full = 0xffffffffu;
-
-    for (int item = blockIdx.x * kStripWarps + wib; item < nitems;
-         item += gridDim.x * kStripWarps) {
-        const int x0 = (item % nstrips) * OUT;
-        const int r0 = (item / nstrips) * R;
-        const int r1 = min(r0 + R, G.H);
-        const int c = x0 - 2 * HL + 2 * lane;
-        const bool colin = c >= 0 && c < G.W;
-        const bool own = colin && lane >= HL && lane <= 31 - HL;
-        const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;
-        const float ncx_e = (c > 0 ? 1.f : 0.f) + (c < G.W - 1 ? 1.f : 0.f);
-        const float ncx_o = 1.f + mxo;
-        auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
-        auto ld_s = [&](const S* base, int r) {
-            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
-        };
-        auto ld_f = [&](const float* base, int r) {
-            return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
-        };
-        auto ld_al = [&](int r) {
-            if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
-            return ld_f(P.alpha.plane, r);
-        };
-        const int m_first = r0 - NS, m_last = r1 + NS;
-
-        // phase 1: U = sum_j u_j^k on rows m_first .. m_last
-        for (int r = m_first; r <= m_last; ++r) {
-            float2 a = make_float2(0.f, 0.f);
-            if (ok_row(r)) {
-                const float* ub = s0.u + r * G.pitch + c;
-                for (int l = 0; l < L; ++l) {
-                    const float2 v = PF::ld(ub + (size_t)l * G.plane);
-                    a.x += v.x;
-                    a.y += v.y;
-                }
-            }
-            Us[(r - m_first) * 32 + lane] = a;
-        }
-
-        // phase 2: per label, the pipelined iteration
-        for (int l = 0; l < L; ++l) {
-            const size_t lo = (size_t)l * G.plane;
-            const float* u0 = s0.u + lo;
-            const S* qx0 = s0.qx + lo;
-            const S* qy0 = s0.qy + lo;
-            const S* p0 = s0.p + lo;
-            float2 V[NS + 2];
-            float2 Bh[NS + 1];
-#pragma unroll
-            for (int k = 0; k < NS + 2; ++k) V[k] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < NS + 1; ++k) Bh[k] = make_float2(0.f, 0.f);
-            float2 qby_up = ld_s(qy0, m_first - 1);
-            float2 in_u = ld_f(u0, m_first), in_qx = ld_s(qx0, m_first);
-            float2 in_qy = ld_s(qy0, m_first), in_p = ld_s(p0, m_first);
-            float2 in_ps = ld_f(s0.ps, m_first);
-            const int t_first = m_first - NS - 1;
-            float2 f_qx = ld_s(qx0, t_first), f_qy = ld_s(qy0, t_first);
-            // costs of label l: its plane, or (I - c_l)^2 from the image plane
-            const float* Cb = P.lev ? P.C : P.C + lo;
-            const float lev_l = P.lev ? __ldg(P.lev + l) : 0.f;
-            auto ld_cost = [&](int r) {
-                if (P.C16)
-                    return ok_row(r) ? Pair<__half>::f2(Pair<__half>::ld(P.C16 + lo + r * G.pitch + c))
-                                     : PF::zero();
-                float2 v = ld_f(Cb, r);
-                if (P.lev && ok_row(r)) {
-                    v.x = (v.x - lev_l) * (v.x - lev_l);
-                    v.y = (v.y - lev_l) * (v.y - lev_l);
-                }
-                return v;
-            };
-            float2 f_p = ld_s(p0, t_first), f_c = ld_cost(t_first), f_al = ld_al(t_first);
-#pragma unroll 1
-            for (int m = m_first; m <= m_last; ++m) {
-#pragma unroll
-                for (int k = NS + 1; k > 0; --k) V[k] = V[k - 1];
-#pragma unroll
-                for (int k = NS; k > 0; --k) Bh[k] = Bh[k - 1];
-                {
-                    const float qxl = __shfl_up_sync(full, in_qx.y, 1);
-                    const float wy = m < G.H - 1 ? 1.f : 0.f;
-                    const float2 U = Us[(m - m_first) * 32 + lane];
-                    float2 b;
-                    b.x = -D.sigma * (in_qx.x - qxl + wy * in_qy.x - qby_up.x + in_p.x - in_ps.x) +
-                          (stL * in_u.x - st_ * U.x);
-                    b.y = -D.sigma * (mxo * in_qx.y - in_qx.x + wy * in_qy.y - qby_up.y + in_p.y -
-                                      in_ps.y) +
-                          (stL * in_u.y - st_ * U.y);
-                    Bh[0] = ok_row(m) ? b : make_float2(0.f, 0.f);
-                    V[0] = in_u;
-                    qby_up = in_qy;
-                }
-                if (m < m_last) {
-                    const int r = m + 1;
-                    in_u = ld_f(u0, r);
-                    in_qx = ld_s(qx0, r);
-                    in_qy = ld_s(qy0, r);
-                    in_p = ld_s(p0, r);
-                    in_ps = ld_f(s0.ps, r);
-                }
-#pragma unroll
-                for (int st = 0; st < NS; ++st) {
-                    const int j = m - 1 - st;
-                    const bool red = (st & 1) == 0;
-                    const bool act_e = ((j & 1) == 0) == red;
-                    const float2 cur = V[st + 1], up = V[st + 2], dn = V[st];
-                    const float left = __shfl_up_sync(full, cur.y, 1);
-                    const float right = __shfl_down_sync(full, cur.x, 1);
-                    const float ncy = (j > 0 ? 1.f : 0.f) + (j < G.H - 1 ? 1.f : 0.f);
-                    const float2 bj = Bh[st + 1];
-                    if (ok_row(j)) {
-                        if (act_e) {
-                            const float sum = left + cur.y + up.x + dn.x;
-                            V[st + 1].x = (bj.x * D.inv_st + sum) / (D.kappa + ncx_e + ncy);
-                        } else {
-                            const float sum = cur.x + right + up.y + dn.y;
-                            V[st + 1].y = (bj.y * D.inv_st + sum) / (D.kappa + ncx_o + ncy);
-                        }
-                    }
-                }
-                const int t = m - NS - 1;
-                const float2 uc = V[NS + 1], ud = V[NS];
-                const float u_right = __shfl_down_sync(full, uc.x, 1);
-                if (t >= r0 && t < r1) {
-                    float2& ns = Ns[(t - r0) * 32 + lane];
-                    ns = l == 0 ? uc : make_float2(ns.x + uc.x, ns.y + uc.y);
-                    if (own) {
-                        const float wy = t < G.H - 1 ? 1.f : 0.f;
-                        const float gx[2] = {uc.y - uc.x, mxo * (u_right - uc.y)};
-                        const float gy[2] = {wy * (ud.x - uc.x), wy * (ud.y - uc.y)};
-                        const float qbx[2] = {f_qx.x, f_qx.y}, qby[2] = {f_qy.x, f_qy.y};
-                        const float pb[2] = {f_p.x, f_p.y}, cc[2] = {f_c.x, f_c.y};
-                        const float al[2] = {f_al.x, f_al.y}, u[2] = {uc.x, uc.y};
-                        float oqx[2], oqy[2], op[2];
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const float q1 = qbx[e] - D.tau * gx[e], q2 = qby[e] - D.tau * gy[e];
-                            float tx = 2.f * q1 - qbx[e], ty = 2.f * q2 - qby[e];
-                            project_sel<ANISO>(tx, ty, al[e]);
-                            oqx[e] = qbx[e] + D.rho * (tx - q1);
-                            oqy[e] = qby[e] + D.rho * (ty - q2);
-                            const float p1 = pb[e] + D.tau * u[e];
-                            op[e] = pb[e] + D.rho * (fminf(2.f * p1 - pb[e], cc[e]) - p1);
-                        }
-                        const int o = t * G.pitch + c;
-                        PF::st(s1.u + lo + o, uc.x, uc.y);
-                        PS::st(s1.qx + lo + o, oqx[0], oqx[1]);
-                        PS::st(s1.qy + lo + o, oqy[0], oqy[1]);
-                        PS::st(s1.p + lo + o, op[0], op[1]);
-                    }
-                }
-                if (m < m_last) {
-                    const int r = t + 1;
-                    f_qx = ld_s(qx0, r);
-                    f_qy = ld_s(qy0, r);
-                    f_p = ld_s(p0, r);
-                    f_c = ld_cost(r);
-                    f_al = ld_al(r);
-                }
-            }
-        }
-
-        // phase 3: p_s reflection on the band
-        if (own)
-            for (int t = r0; t < r1; ++t) {
-                const float2 pbs = ld_f(s0.ps, t);
-                const float2 us = Ns[(t - r0) * 32 + lane];
-                const float ps1x = pbs.x - D.tau * us.x, ps1y = pbs.y - D.tau * us.y;
-                PF::st(s1.ps + t * G.pitch + c,
-                       pbs.x + D.rho * ((2.f * ps1x - pbs.x + D.tau) - ps1x),
-                       pbs.y + D.rho * ((2.f * ps1y - pbs.y + D.tau) - ps1y));
-            }
-        __syncwarp();
-    }
-}
-
 // u_i = w_i + cu p_s on every label plane (turns the strip kernel's output
 // back into the multipliers themselves).
 __global__ void k_potts_strip_finalize(Grid G, int L, float* u, const float* ps, float cu) {
@@ -685,61 +482,6 @@ cudaError_t potts_strip_step(int storage, const PottsProblem& P, const PottsStat
         case CMF_F32: return strip_step_s<float>(P, a, b, aniso, K, cu_in, st);
         case CMF_F16: return strip_step_s<__half>(P, a, b, aniso, K, cu_in, st);
         default: return strip_step_s<__nv_bfloat16>(P, a, b, aniso, K, cu_in, st);
-    }
-}
-
-template <typename S, bool ANISO, int SW>
-static cudaError_t launch_potts_dr_strip(const PottsProblem& P, const PottsState<S>& a,
-                                         const PottsState<S>& b, const DrCoef& D,
-                                         cudaStream_t st) {
-    constexpr int NS = 1 + 2 * SW;
-    constexpr int RMAX = 16;
-    auto kern = k_potts_dr_strip<S, ANISO, SW>;
-    auto dyn_for = [](int r) { return (size_t)kStripWarps * (2 * r + 2 * NS + 1) * 32 * 8; };
-    static std::atomic<long long> memo[kMaxDevices];  // warps resident per device
-    long long resident = 0;
-    {
-        const cudaError_t e = strip::device_resident_warps(memo, kern, dyn_for(RMAX), resident);
-        if (e != cudaSuccess) return e;
-    }
-    const Grid& G = P.g;
-    constexpr int OUT = 2 * (32 - 2 * (SW + 1));
-    const int nstrips = (G.W + OUT - 1) / OUT;
-    const int R = strip::choose_rows(G.H, nstrips, resident, 4, RMAX, 2 * NS + 1);
-    const int nitems = nstrips * ((G.H + R - 1) / R);
-    const int blocks = (nitems + kStripWarps - 1) / kStripWarps;
-    const int grid = blocks < resident / kStripWarps ? blocks : resident / kStripWarps;
-    kern<<<grid, kStripWarps * 32, dyn_for(R), st>>>(P, a, b, D, R, nstrips, nitems);
-    return cudaGetLastError();
-}
-
-template <typename S, bool ANISO>
-static cudaError_t potts_dr_strip_sw(const PottsProblem& P, const PottsState<S>& A,
-                                     const PottsState<S>& B, const DrCoef& D, cudaStream_t st) {
-    switch (D.sweeps) {
-        case 1: return launch_potts_dr_strip<S, ANISO, 1>(P, A, B, D, st);
-        case 2: return launch_potts_dr_strip<S, ANISO, 2>(P, A, B, D, st);
-        case 3: return launch_potts_dr_strip<S, ANISO, 3>(P, A, B, D, st);
-        default: return launch_potts_dr_strip<S, ANISO, 4>(P, A, B, D, st);
-    }
-}
-
-template <typename S>
-static cudaError_t potts_dr_strip_s(const PottsProblem& P, const PottsStateV& a,
-                                    const PottsStateV& b, bool aniso, const DrCoef& D,
-                                    cudaStream_t st) {
-    const PottsState<S> A = a.as<S>(), B = b.as<S>();
-    return aniso ? potts_dr_strip_sw<S, true>(P, A, B, D, st)
-                 : potts_dr_strip_sw<S, false>(P, A, B, D, st);
-}
-
-cudaError_t potts_dr_strip_step(int storage, const PottsProblem& P, const PottsStateV& a,
-                                const PottsStateV& b, bool aniso, const DrCoef& D,
-                                cudaStream_t st) {
-    switch (storage) {
-        case CMF_F32: return potts_dr_strip_s<float>(P, a, b, aniso, D, st);
-        case CMF_F16: return potts_dr_strip_s<__half>(P, a, b, aniso, D, st);
-        default: return potts_dr_strip_s<__nv_bfloat16>(P, a, b, aniso, D, st);
     }
 }
 

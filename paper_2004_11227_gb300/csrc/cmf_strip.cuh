@@ -92,11 +92,11 @@ __device__ __forceinline__ void project_sel(float& x, float& y, float al) {
     }
 }
 
-// Warps of `kern` resident on the whole current device, for blocks of
-// kStripWarps warps with `dyn` bytes of dynamic shared memory (with dyn > 0
-// the kernel's dynamic shared-memory limit is raised to dyn first).  `memo`
-// is the caller's per-kernel table: the queries run once per device.
-template <typename Kern>
+// Warps of `kern` resident on the whole current device, for blocks of WPB
+// warps with `dyn` bytes of dynamic shared memory (with dyn > 0 the kernel's
+// dynamic shared-memory limit is raised to dyn first).  `memo` is the
+// caller's per-kernel table: the queries run once per device.
+template <int WPB = kStripWarps, typename Kern>
 inline cudaError_t device_resident_warps(std::atomic<long long> (&memo)[kMaxDevices], Kern kern,
                                          size_t dyn, long long& out) {
     return per_device(
@@ -110,11 +110,10 @@ inline cudaError_t device_resident_warps(std::atomic<long long> (&memo)[kMaxDevi
             if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
                 cudaSuccess)
                 return e;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern,
-                                                                    kStripWarps * 32, dyn)) !=
-                cudaSuccess)
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, WPB * 32,
+                                                                    dyn)) != cudaSuccess)
                 return e;
-            v = (long long)sms * (blocks > 0 ? blocks : 1) * kStripWarps;
+            v = (long long)sms * (blocks > 0 ? blocks : 1) * WPB;
             return cudaSuccess;
         },
         out);
