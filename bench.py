@@ -337,14 +337,17 @@ def binary_workload(cmf, synth, flush, peak) -> dict:
 
 def potts4_workload(cmf, synth, flush, peak) -> dict:
     """The 4-label 2048^2 Voronoi workload (alpha 0.3): per flow storage the
-    fused iteration's time and bandwidth and the time to the 1e-4 gap, and the
-    plain float32 form's time to the gap."""
+    fused iteration's time and bandwidth and the time to the 1e-4 gap, the
+    plain float32 form's time to the gap, and the same for rPDRQ (one
+    red-black sweep, fused: k_potts_dr_strip)."""
     inst = synth.config3()
     out = {"workload": "potts L=4 2048x2048 Voronoi (64 seeds), alpha 0.3, solve to gap 1e-4"}
-    for storage, name, impl, max_iter in ((0, "float32", 0, 20000), (1, "float16", 0, 4000),
-                                         (2, "bfloat16", 0, 4000),
-                                         (0, "float32_plain", 1, 20000)):
-        p = cmf.default_params(FLAGSHIP, inst.L, storage=storage, impl=impl, tol_gap=TOL,
+    for algo, storage, name, impl, max_iter in ((FLAGSHIP, 0, "float32", 0, 20000),
+                                                (FLAGSHIP, 1, "float16", 0, 4000),
+                                                (FLAGSHIP, 2, "bfloat16", 0, 4000),
+                                                (FLAGSHIP, 0, "float32_plain", 1, 20000),
+                                                (3, 0, "rPDRQ_float32", 0, 20000)):
+        p = cmf.default_params(algo, inst.L, storage=storage, impl=impl, tol_gap=TOL,
                                max_iter=max_iter, check_every=CHECK_SIDE)
         s = cmf.alloc_potts(inst, p)
         cmf.cmf_init_potts(s)
@@ -446,6 +449,27 @@ def batch_workload(cmf, synth, flush) -> dict:
            "label_pixels": sum(i.H * i.W * i.L for i in insts)}
     del batch, items
     torch.cuda.empty_cache()
+    # the same instances solved one after another by the single-instance
+    # solver (its automatic kernel choice, device-driven loop; allocation
+    # outside the timed calls, graph building inside them)
+    seq_ms, seq_units, seq_ok = 0.0, 0, 0
+    for inst in insts:
+        q = cmf.default_params(2, inst.L, tol_gap=1e-4, max_iter=5000, check_every=10)
+        one = cmf.alloc_binary(inst, q) if inst.kind == "binary" else cmf.alloc_potts(inst, q)
+        torch.cuda.synchronize()
+        e0.record()
+        st1, it1, _ = (cmf.cmf_solve_binary(one) if inst.kind == "binary"
+                       else cmf.cmf_solve_potts(one))
+        e1.record()
+        e1.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        seq_units += inst.H * inst.W * inst.L * it1
+        seq_ok += int(st1 == cmf.OK)
+        del one
+    torch.cuda.empty_cache()
+    out["sequential_single_solves"] = {
+        "time_ms": round(seq_ms, 2), "px_label_it_per_s": seq_units / seq_ms * 1e3,
+        "converged": seq_ok, "batch_rate_over_sequential": (units / ms) / (seq_units / seq_ms)}
     return out
 
 
