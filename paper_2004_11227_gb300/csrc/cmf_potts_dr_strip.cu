@@ -29,7 +29,7 @@ using strip::project_sel;
 namespace {
 
 constexpr int kDrMaxWarps = 8;  // warps per block at most (one per label group)
-constexpr int kDrRmax = 64;     // band rows at most: (64 + 19) x 256 B of U < 48 KB
+constexpr int kDrRmax = 128;    // band rows at most: (128 + 19) x 256 B of U < 48 KB
 
 template <typename S, bool ANISO, int SW>
 __global__ void __launch_bounds__(kDrMaxWarps * 32)
