@@ -447,6 +447,27 @@ def batch_workload(cmf, synth, flush) -> dict:
            "converged": sum(1 for r in res if r["status"] == cmf.OK),
            "iters_min": min(iters), "iters_median": int(np.median(iters)), "iters_max": max(iters),
            "label_pixels": sum(i.H * i.W * i.L for i in insts)}
+    # every instance's final state certified by the FP64 oracle: its relative
+    # gap recomputed from the state the batch left in the caller's buffers
+    import oracle as O
+
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    og = []
+    for inst, item in zip(insts, items):
+        op = O.default_params(O.RPADMM_EB, inst.L)
+        if inst.kind == "binary":
+            og.append(O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, item.state(), op)[2])
+        else:
+            op.a2 = max(op.a2, 2.0 * inst.L)
+            og.append(O.potts_eval(inst.costs, inst.alpha, item.state(), op)[2])
+    og = np.array(og)
+    gg = np.array([r["gap"] for r in res])
+    out["oracle_certified"] = {
+        "instances_at_or_below_1e-4": int(np.sum(og <= TOL * 1.01)),
+        "oracle_gap_max": float(og.max()), "max_abs_gap_diff_vs_gpu": float(np.abs(og - gg).max()),
+        "oracle_s": round(time.perf_counter() - t0, 1)}
     del batch, items
     torch.cuda.empty_cache()
     # the same instances solved one after another by the single-instance

@@ -31,8 +31,12 @@ namespace {
 constexpr int kDrMaxWarps = 8;  // warps per block at most (one per label group)
 constexpr int kDrRmax = 128;    // band rows at most: (128 + 19) x 256 B of U < 48 KB
 
+// The bound of three 8-warp blocks per SM holds a thread to 80 registers (a
+// few bytes of spill for one sweep): 24 resident warps for 4-warp blocks
+// where 96 registers gave 20 (measured 7% faster; a 64-register bound spilled
+// more and ran 20% slower).
 template <typename S, bool ANISO, int SW>
-__global__ void __launch_bounds__(kDrMaxWarps * 32)
+__global__ void __launch_bounds__(kDrMaxWarps * 32, 3)
     k_potts_dr_strip(PottsProblem P, PottsState<S> s0, PottsState<S> s1, DrCoef D,
                      const float* __restrict__ U_in, float* __restrict__ U_out, int R,
                      int nstrips, int nitems) {
@@ -247,9 +251,8 @@ __global__ void __launch_bounds__(kDrMaxWarps * 32)
 // Warps per block for L labels.  Every warp runs ceil(L / nw) pipelines and
 // the block waits for the slowest, so the score is the share of the warps'
 // label passes that do work, times the band's sharing (up to four warps);
-// ties go to fewer idle passes, then to the count nearest four (about 96
-// registers a thread: blocks of two to seven warps keep 18-21 warps resident
-// per SM, eight only 16).
+// ties go to fewer idle passes, then to the count nearest four (at 80
+// registers a thread, 21-25 warps stay resident per SM for any count).
 static int dr_warps(int L) {
     int best = 1;
     double best_score = 0.0, best_eff = 0.0;
