@@ -411,7 +411,9 @@ size_t cmf_batch_workspace_bytes(const cmf_instance *inst, int n, const cmf_para
 
 /* Solve all n instances (host array; device pointers inside) with the same
  * algorithm and parameters (rPDRQ: the same sigma and tau for every
- * instance; Potts instances use a2 = max(p->a2, 2L), the bound of Thm 2);
+ * instance; Potts instances use a2 = max(p->a2, 2L), the bound of Thm 2;
+ * ALG1 instances use tau = min(p->tau, 1 / ((L == 2 ? 10 : 9 + L) sigma)),
+ * the step bound cmf_default_params takes for their L);
  * cold start unless p->warm_start.  Fills the
  * result fields of every instance.  Returns CMF_OK when every instance
  * reached p->tol_gap, CMF_NOT_CONVERGED when some stopped at max_iter. */

@@ -270,9 +270,17 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
         D.ev_base = (int)(in.model == 0 ? eb.size() : B.n_bin_ev + ep.size());
         D.ev_count = ntx * ((in.H + 31) / 32);
         const Alpha A{in.d_alpha, in.alpha0};
-        // Thm 2 needs a2 >= 2L: each Potts instance uses max(p->a2, 2L)
+        // Thm 2 needs a2 >= 2L: each Potts instance uses max(p->a2, 2L).
+        // ALG1 needs sigma tau ||K*K|| <= 1: each instance uses
+        // min(p->tau, 1 / (bound x sigma)), the bound of cmf_default_params
+        // for its L (10 binary, 9 + L Potts)
         cmf_params pi = *p;
         if (in.model == 1 && pi.a2 < 2.0 * in.L) pi.a2 = 2.0 * in.L;
+        if (p->algo == CMF_CP) {
+            const double bound = in.model == 0 ? 10.0 : 9.0 + in.L;
+            const double tmax = 1.0 / (bound * pi.sigma);
+            if (pi.tau > tmax) pi.tau = tmax;
+        }
         D.ak = make_admm_coef(pi, in.model == 0 ? 2 : in.L);
         D.dk = make_dr_coef(pi, in.model == 0 ? 2 : in.L, in.model == 1);
         if (in.model == 0) {

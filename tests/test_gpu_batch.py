@@ -192,3 +192,30 @@ def test_batch_strip_odd_widths_ignore_the_padding_column(cmf, algo):
         got = item.state()
         for k in ("u", "qx", "qy", "p", "ps"):
             assert np.abs(got[k] - ref[k]).max() <= 1e-4, (inst.W, k)
+
+
+def test_batch_alg1_takes_each_instances_step_bound(cmf):
+    """ALG1 without a hand-set tau: every instance of the batch runs with
+    tau = min(p.tau, 1 / (bound(L) sigma)), the bound cmf_default_params takes
+    for its label count, so it matches a single solve with its own defaults."""
+    insts = _instances()
+    kw = dict(tol_gap=1e-4, max_iter=20000, check_every=10, variant=1)
+    p = cmf.default_params(5, 2, **kw)
+    items = [_alloc(cmf, i, p) for i in insts]
+    status, res = cmf.cmf_solve_batch(items, p)
+    assert status == cmf.OK, res
+    for inst, item, r in zip(insts, items, res):
+        q = cmf.default_params(5, inst.L, **kw)
+        q.a2 = max(p.a2, 2.0 * inst.L)
+        assert q.tau == min(p.tau, 1.0 / ((10 if inst.L == 2 else 9 + inst.L) * q.sigma))
+        if inst.kind == "potts" and inst.W % 2 == 0:
+            q.variant = 2  # the batch runs this instance by warp strips
+        single = _alloc(cmf, inst, q)
+        if inst.kind == "binary":
+            st, it, hist = cmf.cmf_solve_binary(single)
+        else:
+            st, it, hist = cmf.cmf_solve_potts(single)
+        assert st == cmf.OK and it == r["iters"], (inst.kind, it, r["iters"])
+        a, b = item.state(), single.state()
+        for k in a:
+            assert np.abs(a[k] - b[k]).max() <= 1e-5, k
