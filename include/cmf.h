@@ -172,16 +172,19 @@ typedef struct {
                           caller's buffers) and the solve starts cold.  Phase
                           one runs in phase_storage (flows q_i, p_i in 16 bits;
                           u, p_s float32) in state sets inside the workspace
-                          until the certified gap is <= phase_gap; the state
-                          is then written exactly into the caller's float32
-                          buffers and phase two continues in float32 to
-                          tol_gap.  Iteration counts and history rows run on
-                          across the switch; phase one alone may use up
-                          max_iter.  16-bit flows cannot certify arbitrarily
-                          small gaps (rounding of q_i and p_i holds the
+                          until the certified gap is <= phase_gap, or is
+                          below 10 phase_gap and above 0.7 times its value
+                          at the check ceil(200 / check_every) checks
+                          earlier (tested at every such check, from the
+                          first on; the 16-bit rounding floor of
+                          the instance: rounding of q_i and p_i holds the
                           16-label 4096^2 workload near 3e-4 in float16,
-                          near 3e-3 in bfloat16): phase_gap must lie above
-                          that floor and above tol_gap.                    */
+                          near 3e-3 in bfloat16, higher for larger c); the
+                          state is then written exactly into the caller's
+                          float32 buffers and phase two continues in float32
+                          to tol_gap.  Iteration counts and history rows run
+                          on across the switch; phase one alone may use up
+                          max_iter.  phase_gap must lie above tol_gap.    */
     double phase_gap;
     int tune_step;     /* cmf_autotune_*: 0 = launch configurations only; 1 =
                           also the ADMM step size c of pADMMI, rpADMMI,

@@ -722,6 +722,16 @@ void graph_drop(cudaGraphExec_t ge) {
         }
 }
 
+// The stall test of a two-phase solve's first phase (solve_decide): off when
+// iters == 0; the window is the checks that cover `iters` iterations.
+struct StallRule {
+    int iters = 0;
+    double factor = 0.0, near = 0.0;
+    int checks(int check_every) const {
+        return iters > 0 ? (iters + check_every - 1) / check_every : 0;
+    }
+};
+
 // `chunk(stream, from)` launches check_every iterations starting in buffer
 // set `from` (0 = the caller's, 1 = the workspace's) and returns the set they
 // end in through `to`; `certify(stream, set)` launches the certificate kernel
@@ -736,7 +746,8 @@ void graph_drop(cudaGraphExec_t ge) {
 template <typename Chunk, typename EndOf, typename Copy>
 cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
                        Chunk chunk, EndOf end_of, Copy copy_back, double* h_hist,
-                       int hist_cap, int* h_iters, cudaStream_t st, int it0 = 0, int nh0 = 0) {
+                       int hist_cap, int* h_iters, cudaStream_t st, int it0 = 0, int nh0 = 0,
+                       const StallRule& sr = StallRule()) {
     SolveCtl* ctl = (SolveCtl*)(wsbase + w.ctl);
     double* dhist = (double*)(wsbase + w.hist);
     const int rows = (int)hist_rows_for(*p);
@@ -749,6 +760,9 @@ cmf_status solve_graph(const cmf_params* p, const SolveSig& sig, char* wsbase, c
     T.K = p->check_every;
     T.max_iter = p->max_iter;
     T.tol = p->tol_gap;
+    T.stall = sr.checks(p->check_every);
+    T.stall_f = sr.factor;
+    T.stall_near = sr.near;
     k_solve_reset<<<1, 1, 0, st>>>(ctl, it0);
     CMF_CUDA_TRY(cudaGetLastError());
 
@@ -880,8 +894,11 @@ struct LoopState {
 // k0 of the solve and writes the certificates (E, D, gap, res) to out.
 template <typename RunCert>
 cmf_status loop_chunks(const cmf_params* p, int it_stop, RunCert run_cert, double* h_hist,
-                       int hist_cap, LoopState& ls) {
+                       int hist_cap, LoopState& ls, const StallRule& sr = StallRule()) {
     double out[4];
+    const int stall = sr.checks(p->check_every);
+    double gref = 0.0;  // the stall test, as solve_decide keeps it
+    int nchk = 0;
     while (ls.it < p->max_iter && ls.it < it_stop) {
         const int k =
             p->check_every < p->max_iter - ls.it ? p->check_every : p->max_iter - ls.it;
@@ -897,7 +914,13 @@ cmf_status loop_chunks(const cmf_params* p, int it_stop, RunCert run_cert, doubl
             row[4] = out[3];
         }
         ++ls.nh;
-        if (out[2] <= p->tol_gap) {
+        bool stalled = false;
+        if (stall > 0 && nchk % stall == 0) {
+            stalled = nchk > 0 && out[2] < sr.near && out[2] > sr.factor * gref;
+            gref = out[2];
+        }
+        ++nchk;
+        if (out[2] <= p->tol_gap || stalled) {
             ls.converged = true;
             break;
         }
@@ -924,12 +947,12 @@ template <typename RunCert, typename Copy, typename Chunk, typename EndOf>
 cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, const WsLayout& w,
                         RunCert run_cert, Copy copy_back, Chunk chunk, EndOf end_of,
                         double* h_hist, int hist_cap, int* h_iters, cudaStream_t st,
-                        int it0 = 0, int nh0 = 0) {
+                        int it0 = 0, int nh0 = 0, const StallRule& sr = StallRule()) {
     LoopState ls;
     ls.it = it0;
     ls.nh = nh0;
     if (!graph_eligible(*p)) {
-        cmf_status s = loop_chunks(p, p->max_iter, run_cert, h_hist, hist_cap, ls);
+        cmf_status s = loop_chunks(p, p->max_iter, run_cert, h_hist, hist_cap, ls, sr);
         if (s != CMF_OK) return s;
         return finish_loop(ls, copy_back, h_iters, st);
     }
@@ -941,7 +964,7 @@ cmf_status solve_driver(const cmf_params* p, const SolveSig& sig, char* wsbase, 
         if (ls.converged || ls.it >= p->max_iter) return finish_loop(ls, copy_back, h_iters, st);
     }
     return solve_graph(p, sig, wsbase, w, chunk, end_of, copy_back, h_hist, hist_cap,
-                       h_iters, st, ls.it, ls.nh);
+                       h_iters, st, ls.it, ls.nh, sr);
 }
 
 }  // namespace
@@ -1138,6 +1161,15 @@ cmf_status cmf_eval_potts(const float* d_C, int L, const float* d_alpha, float a
     return potts_eval_state(c, c.user, h_out, (cudaStream_t)stream);
 }
 
+// The first phase of a two-phase solve also ends when its certified gap,
+// below kPhaseStallNear x phase_gap, has not fallen to kPhaseStallFactor
+// times its value kPhaseStallIters iterations earlier (tested once per such
+// window): the 16-bit storage's rounding floor of this instance is near (it
+// rises with the step size c), and float32 storage continues from there.
+constexpr int kPhaseStallIters = 200;
+constexpr double kPhaseStallFactor = 0.7;
+constexpr double kPhaseStallNear = 10.0;
+
 cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float alpha0, int H,
                            int W, int pitch, const cmf_params* p, float* d_u, void* d_qx,
                            void* d_qy, void* d_p, void* d_ps, double* h_hist, int hist_cap,
@@ -1187,7 +1219,8 @@ cmf_status cmf_solve_potts(const float* d_C, int L, const float* d_alpha, float 
                 potts_run(c1, q.check_every, to, nullptr, 0, nullptr, true);
                 return to;
             },
-            h_hist, hist_cap, &it1, st);
+            h_hist, hist_cap, &it1, st, 0, 0, StallRule{kPhaseStallIters, kPhaseStallFactor,
+                                                        kPhaseStallNear * q.tol_gap});
         if (s != CMF_OK && s != CMF_NOT_CONVERGED) return s;
         // the switch: the 16-bit state written exactly into the caller's
         // float32 buffers; phase two continues from it

@@ -223,16 +223,23 @@ struct SolveCtl {
     int err;              // kErrWaitTimeout: a bounded device-side wait ran out
     int where;            // buffer set holding the state when the loop stopped (1 = workspace)
     unsigned int arrive;  // blocks of the current certificate launch done (0 between launches)
+    double gref;          // gap at the last stall-test check (first phase of a two-phase solve)
 };
+static_assert(sizeof(SolveCtl) <= 64, "the workspace reserves 64 bytes for SolveCtl");
 
 // One thread: turn the reduced (E, D, res^2) into a history row and decide
 // whether the loop goes on.  The state it certified is in buffer set `where`.
 // set_h: 1 = h is the loop's condition, 2 = h is the condition of the second
 // half of a two-chunk loop body, 0 = leave the conditions to a later kernel.
+// stall > 0 (the first phase of a two-phase solve): every `stall` checks
+// the gap is compared with its value `stall` checks earlier, and the loop
+// also stops, as converged, when it is below stall_near and above stall_f
+// times that value (the storage's rounding floor is reached).
 __device__ __forceinline__ void solve_decide(const double* scal, SolveCtl* ctl, double* hist,
                                              int hist_rows, int K, int max_iter, double tol,
                                              cudaGraphConditionalHandle h, int set_h,
-                                             int where) {
+                                             int where, int stall, double stall_f,
+                                             double stall_near) {
     const double E = scal[0], D = scal[1], R = scal[2];
     const double gap = (E - D) / (fabs(E) > 1e-30 ? fabs(E) : 1e-30);
     const int it = ctl->it + K;
@@ -247,7 +254,12 @@ __device__ __forceinline__ void solve_decide(const double* scal, SolveCtl* ctl, 
         row[4] = sqrt(R > 0.0 ? R : 0.0);
     }
     ctl->checks = n + 1;
-    const bool converged = gap <= tol;
+    bool stalled = false;
+    if (stall > 0 && n % stall == 0) {
+        stalled = n > 0 && gap < stall_near && gap > stall_f * ctl->gref;
+        ctl->gref = gap;
+    }
+    const bool converged = gap <= tol || stalled;
     const bool failed = ctl->err == kErrWaitTimeout;
     const bool go = !converged && !failed && it + K <= max_iter;
     ctl->stop = go ? 0 : (failed ? 3 : (converged ? 1 : 2));
@@ -270,6 +282,8 @@ struct EvalTail {
     double tol = 0.0;
     cudaGraphConditionalHandle h = 0;
     int set_h = 0, where = 0;
+    int stall = 0;  // see solve_decide
+    double stall_f = 0.0, stall_near = 0.0;
 };
 
 // Called by every thread of every block after the block's partial triple is
@@ -299,7 +313,7 @@ __device__ __forceinline__ void eval_tail(const EvalTail& T, const double* parti
         T.ctl->arrive = 0;
         if (T.decide)
             solve_decide(T.scal, T.ctl, T.hist, T.hist_rows, T.K, T.max_iter, T.tol, T.h,
-                         T.set_h, T.where);
+                         T.set_h, T.where, T.stall, T.stall_f, T.stall_near);
     }
 }
 

@@ -462,19 +462,53 @@ def test_half_cost_planes_match_oracle(cmf, algo, shape):
     assert abs(E - Eo) <= 1e-5 * abs(Eo) and abs(D - Do) <= 1e-5 * abs(Eo)
 
 
-@pytest.mark.parametrize("phase_storage,switch", [(1, 2e-3), (2, 1e-2)])
+def _phase_one_stop(h, switch, check_every):
+    """Row of a 16-bit solve's history at which the first phase of a
+    two-phase solve stops: the first gap <= switch, or, tested every
+    ceil(200 / check_every) checks from the first, a gap below 10 switch and
+    above 0.7 times the gap at the previous tested check."""
+    w = -(-200 // check_every)
+    ref = None
+    for n in range(len(h)):
+        g = h[n, 3]
+        if g <= switch:
+            return n
+        if n % w == 0:
+            if n > 0 and g < 10 * switch and g > 0.7 * ref:
+                return n
+            ref = g
+    return len(h) - 1
+
+
+@pytest.mark.parametrize("phase_storage,switch", [(1, 2e-3), (2, 1e-2), (1, 1.2e-4)])
 def test_two_phase_solve(cmf, phase_storage, switch):
-    """phase_storage: the solve runs in 16-bit flows to the switch gap, then
-    in float32 from exactly that state.  Phase one equals the 16-bit solve
-    to the switch gap row for row; phase two equals a float32 warm start from
-    its state row for row; the result is certified by the oracle."""
+    """phase_storage: the solve runs in 16-bit flows to the switch gap (or
+    to where that storage's gap stalls), then in float32 from exactly that
+    state.  Phase one equals the 16-bit solve row for row up to the row the
+    switch rule picks; phase two equals a float32 warm start from that state
+    row for row; the result is certified by the oracle.  A switch gap below
+    the float16 floor (1.2e-4) ends phase one by the stall rule."""
     inst = synth.config5(96, 128)
     tol = 1e-4
     kw = dict(max_iter=20000, check_every=10)
     p16 = cmf.default_params(2, 16, storage=phase_storage, tol_gap=switch, **kw)
     a = cmf.alloc_potts(inst, p16)
     st_a, it_a, h_a = cmf.cmf_solve_potts(a)
-    assert st_a == cmf.OK and h_a[-1, 3] <= switch
+    n_s = _phase_one_stop(h_a, switch, kw["check_every"])
+    if switch < 2e-4:
+        assert h_a[n_s, 3] > switch  # the stall rule, not the gap, ends phase one
+    if n_s < len(h_a) - 1 or h_a[n_s, 3] > switch:
+        # the state at the stalled check: the same 16-bit iterations, stopped there
+        it_a = int(h_a[n_s, 0])
+        q16 = cmf.default_params(2, 16, storage=phase_storage, tol_gap=0.0, max_iter=it_a,
+                                 check_every=kw["check_every"])
+        a = cmf.alloc_potts(inst, q16)
+        st_s, it_s, h_s = cmf.cmf_solve_potts(a)
+        assert it_s == it_a
+        np.testing.assert_array_equal(h_s, h_a[:n_s + 1])
+        h_a = h_s
+    else:
+        assert st_a == cmf.OK and h_a[-1, 3] <= switch
     p32 = cmf.default_params(2, 16, tol_gap=tol, warm_start=1, **kw)
     c = cmf.alloc_potts(inst, p32)
     c.load_state(a.state())  # 16-bit values are exact in float32
@@ -491,6 +525,13 @@ def test_two_phase_solve(cmf, phase_storage, switch):
         np.testing.assert_array_equal(got[k], c.state()[k])
     E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, got, O.default_params(2, 16))
     assert gap <= 1.001e-4
+    # the host-driven loop takes the same decisions
+    ph = cmf.default_params(2, 16, tol_gap=tol, phase_storage=phase_storage, phase_gap=switch,
+                            use_graph=0, **kw)
+    e = cmf.alloc_potts(inst, ph)
+    st_e, it_e, h_e = cmf.cmf_solve_potts(e)
+    assert st_e == cmf.OK and it_e == it_b
+    np.testing.assert_array_equal(h_e, h_b)
 
 
 def test_autotune_step_size(cmf, tmp_path):
@@ -513,3 +554,27 @@ def test_autotune_step_size(cmf, tmp_path):
     assert st == cmf.OK
     E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, t.state(), O.default_params(2, 16))
     assert gap <= 1.001e-4
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("L,shape", [(5, (301, 130)), (16, (140, 64)), (3, (9, 200))])
+def test_rpdrq_strip_label_sum_plane_is_exact(cmf, storage, L, shape):
+    """The rPDRQ strip kernel's later launches of a call read sum_i u_i from
+    the plane the previous launch wrote; the first launch sums the u_i
+    planes. Both sums are taken in label order, so seven iterations in one
+    call equal seven calls of one iteration bit for bit (bands of several
+    heights, label counts shared out over 3, 4 and 5 warps)."""
+    H, W = shape
+    inst = synth.random_potts(H, W, L, seed=90 + L, alpha=0.3, field_alpha=True)
+    p = cmf.default_params(3, L, storage=storage, variant=2)
+    a = cmf.alloc_potts(inst, p)
+    b = cmf.alloc_potts(inst, p)
+    cmf.cmf_init_potts(a)
+    cmf.cmf_init_potts(b)
+    cmf.cmf_iterate_potts(a, 7)
+    for _ in range(7):
+        cmf.cmf_iterate_potts(b, 1)
+    torch.cuda.synchronize()
+    sa, sb = a.state(), b.state()
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
