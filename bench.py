@@ -393,8 +393,9 @@ def potts16_other_forms(cmf, inst, flush) -> dict:
 
 def tuned_step(cmf, inst, flush) -> dict:
     """The step-size search: cmf_autotune_potts with tune_step = 1 (c, 2c, 4c,
-    8c beside the launch variants) on the 1024^2 instance of the recipe, then
-    one two-phase solve of the 4096^2 instance with the chosen c."""
+    8c beside the launch variants, each also with the switch left to the
+    stall test) on the 1024^2 instance of the recipe, then one two-phase
+    solve of the 4096^2 instance with the chosen c and switch gap."""
     small = rank_instance(0, 1024)
     p = cmf.default_params(FLAGSHIP, L, tol_gap=TOL, max_iter=MAX_ITER, check_every=CHECK_EVERY,
                            phase_storage=PHASE_STORAGE, phase_gap=PHASE_GAP, tune_step=1)
@@ -404,13 +405,14 @@ def tuned_step(cmf, inst, flush) -> dict:
     tune_s = time.perf_counter() - t0
     del s
     q = cmf.default_params(FLAGSHIP, L, tol_gap=TOL, max_iter=MAX_ITER, check_every=CHECK_EVERY,
-                           phase_storage=PHASE_STORAGE, phase_gap=PHASE_GAP, c=best.c,
+                           phase_storage=PHASE_STORAGE, phase_gap=best.phase_gap, c=best.c,
                            variant=best.variant)
     g = cmf.alloc_potts(inst, q)
     flush.zero_()
     ms, (st, iters, hist) = _timed(lambda: cmf.cmf_solve_potts(g))
     del g
-    return {"c": best.c, "variant": best.variant, "tuned_on": "1024x1024 instance of the recipe",
+    return {"c": best.c, "phase_gap": best.phase_gap, "variant": best.variant,
+            "tuned_on": "1024x1024 instance of the recipe",
             "tuning_s": round(tune_s, 1), "time_to_gap_ms": round(ms, 1), "iterations": iters,
             "converged": st == cmf.OK, "final_gap": float(hist[-1, 3])}
 

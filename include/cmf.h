@@ -191,7 +191,10 @@ typedef struct {
                           rpADMMII and pADMM-TY (candidates c, 2c, 4c, 8c
                           with the given kernel variant; Sec. 4 takes c = 0.3,
                           and any c > 0 keeps the convergence results of Thm 1
-                          and Thm 2).  Other algorithms ignore it.           */
+                          and Thm 2), and for a two-phase solve each of them
+                          also with phase_gap = 1.5 tol_gap (the switch left
+                          to the first phase's stall test).  Other algorithms
+                          ignore it.                                         */
 } cmf_params;
 
 /* Fill *p with the paper's defaults for `algo` and L labels (L = 2 for the

@@ -461,8 +461,8 @@ def cmf_autotune_potts(s: Potts, stream=None):
 
 def tuned_params(problem, cache_path: str | None = None) -> Params:
     """Autotuned parameters for a Binary / Potts container, cached in a JSON
-    file keyed by (model, H, W, L, storage, algo, impl, tune_step, c, SM
-    count, device)."""
+    file keyed by (model, H, W, L, storage, algo, impl, tune_step, c,
+    phase_storage, phase_gap, SM count, device)."""
     import json
 
     p = problem.params
@@ -470,7 +470,7 @@ def tuned_params(problem, cache_path: str | None = None) -> Params:
     key = "|".join(str(v) for v in (
         "binary" if isinstance(problem, Binary) else "potts", problem.H, problem.W,
         getattr(problem, "L", 2), p.storage, p.algo, p.impl, p.tune_step, p.c,
-        props.multi_processor_count, props.name))
+        p.phase_storage, p.phase_gap, props.multi_processor_count, props.name))
     path = cache_path or os.environ.get(
         "CMF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cmf_tune.json"))
     try:
@@ -484,14 +484,16 @@ def tuned_params(problem, cache_path: str | None = None) -> Params:
     if key in cache:
         q.variant, q.sweeps = cache[key]["variant"], cache[key]["sweeps"]
         q.c = cache[key].get("c", q.c)
+        q.phase_gap = cache[key].get("phase_gap", q.phase_gap)
         return q
     if isinstance(problem, Binary):
         best, ms = cmf_autotune_binary(problem)
     else:
         best, ms = cmf_autotune_potts(problem)
-    cache[key] = {"variant": best.variant, "sweeps": best.sweeps, "c": best.c, "ms_to_gap": ms}
+    cache[key] = {"variant": best.variant, "sweeps": best.sweeps, "c": best.c,
+                  "phase_gap": best.phase_gap, "ms_to_gap": ms}
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     with open(path, "w") as f:
         json.dump(cache, f, indent=1)
-    q.variant, q.sweeps, q.c = best.variant, best.sweeps, best.c
+    q.variant, q.sweeps, q.c, q.phase_gap = best.variant, best.sweeps, best.c, best.phase_gap
     return q

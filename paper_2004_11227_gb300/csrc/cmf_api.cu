@@ -1294,6 +1294,17 @@ std::vector<cmf_params> tune_candidates(const cmf_params& p, bool binary) {
             q.warm_start = 0;
             out.push_back(q);
         }
+    // two-phase solves (tune_step): each step size also with the switch left
+    // to the first phase's stall test alone (phase_gap 1.5 tol_gap)
+    const double stall_only = 1.5 * p.tol_gap;
+    if (p.tune_step == 1 && admm && p.phase_storage != 0 && stall_only < p.phase_gap)
+        for (double f : {1.0, 2.0, 4.0, 8.0}) {
+            cmf_params q = p;
+            q.c = p.c * f;
+            q.phase_gap = stall_only;
+            q.warm_start = 0;
+            out.push_back(q);
+        }
     return out;
 }
 

@@ -556,6 +556,28 @@ def test_autotune_step_size(cmf, tmp_path):
     assert gap <= 1.001e-4
 
 
+def test_autotune_two_phase_switch(cmf, tmp_path):
+    """tune_step = 1 on a two-phase solve also tries each step size with the
+    switch left to the stall test (phase_gap = 1.5 tol_gap); the binding's
+    cache carries the chosen switch gap, and the tuned solve is certified."""
+    inst = synth.config5(64, 96)
+    p = cmf.default_params(2, 16, tol_gap=1e-4, max_iter=8000, check_every=10, tune_step=1,
+                           phase_storage=1, phase_gap=2e-3)
+    s = cmf.alloc_potts(inst, p)
+    best, ms = cmf.cmf_autotune_potts(s)
+    assert ms > 0 and any(abs(best.c - 0.3 * f) < 1e-12 for f in (1, 2, 4, 8))
+    assert best.phase_gap in (2e-3, 1.5 * p.tol_gap) and best.phase_storage == 1
+    q = cmf.tuned_params(s, cache_path=str(tmp_path / "tune.json"))
+    assert q.phase_gap == best.phase_gap and abs(q.c - best.c) < 1e-12
+    q2 = cmf.tuned_params(s, cache_path=str(tmp_path / "tune.json"))  # from the cache
+    assert q2.phase_gap == best.phase_gap and abs(q2.c - best.c) < 1e-12
+    t = cmf.alloc_potts(inst, q)
+    st, it, hist = cmf.cmf_solve_potts(t)
+    assert st == cmf.OK
+    E, D, gap, res = O.potts_eval(inst.costs, inst.alpha, t.state(), O.default_params(2, 16))
+    assert gap <= 1.001e-4
+
+
 @pytest.mark.parametrize("storage", [0, 1])
 @pytest.mark.parametrize("L,shape", [(5, (301, 130)), (16, (140, 64)), (3, (9, 200))])
 def test_rpdrq_strip_label_sum_plane_is_exact(cmf, storage, L, shape):
