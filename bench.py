@@ -271,6 +271,7 @@ KERNEL_CASES = {
     "potts4-admm-2048": ("potts", 2, 2048, 2048, 4, 0, 0),
     "potts4-admm-2048-f16": ("potts", 2, 2048, 2048, 4, 1, 0),
     "potts4-dr-2048": ("potts", 3, 2048, 2048, 4, 0, 0),
+    "potts4-dr-2048-f16": ("potts", 3, 2048, 2048, 4, 1, 0),
     "potts16-admm-2048-f16": ("potts", 2, 2048, 2048, 16, 1, 0),
     "potts16-admm-4096-f16": ("potts", 2, 4096, 4096, 16, 1, 0),
     "potts16-admm-2048-f32": ("potts", 2, 2048, 2048, 16, 0, 0),

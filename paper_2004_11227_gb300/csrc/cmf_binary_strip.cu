@@ -187,8 +187,10 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         const float ncx_e = (c > 0 ? 1.f : 0.f) + (c < G.W - 1 ? 1.f : 0.f);
         const float ncx_o = 1.f + mxo;
         auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
+        // stored pairs stay in their storage type until used: a conversion at
+        // the load would wait for the prefetched row at once
         auto ld_s = [&](const S* base, int r) {
-            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
+            return ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero();
         };
         auto ld_f = [&](const float* base, int r) {
             return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             if (!P.alpha.plane) return make_float2(P.alpha.value, P.alpha.value);
             return ld_f(P.alpha.plane, r);
         };
+        using SP = typename PS::T;
 
         float2 V[NS + 2];   // V[k]: u of row m-k (stage k-1 applied; k >= NS: final)
         float2 Bh[NS + 1];  // Bh[k]: b of row m-k
@@ -204,16 +207,16 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         for (int k = 0; k < NS + 2; ++k) V[k] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < NS + 1; ++k) Bh[k] = make_float2(0.f, 0.f);
-        float2 qby_up = ld_s(s0.qy, r0 - NS - 1);  // qbar_y of the row above the ingested one
+        SP qby_up = ld_s(s0.qy, r0 - NS - 1);  // qbar_y of the row above the ingested one
 
         // prefetched inputs of the next ingested row and the next finished row
         const int m_first = r0 - NS, m_last = r1 + NS;
-        float2 in_u = ld_f(s0.u, m_first), in_qx = ld_s(s0.qx, m_first);
-        float2 in_qy = ld_s(s0.qy, m_first), in_ps = ld_s(s0.ps, m_first);
-        float2 in_pt = ld_s(s0.pt, m_first);
+        float2 in_u = ld_f(s0.u, m_first);
+        SP in_qx = ld_s(s0.qx, m_first), in_qy = ld_s(s0.qy, m_first);
+        SP in_ps = ld_s(s0.ps, m_first), in_pt = ld_s(s0.pt, m_first);
         const int t_first = m_first - NS - 1;
-        float2 f_qx = ld_s(s0.qx, t_first), f_qy = ld_s(s0.qy, t_first);
-        float2 f_ps = ld_s(s0.ps, t_first), f_pt = ld_s(s0.pt, t_first);
+        SP f_qx = ld_s(s0.qx, t_first), f_qy = ld_s(s0.qy, t_first);
+        SP f_ps = ld_s(s0.ps, t_first), f_pt = ld_s(s0.pt, t_first);
         float2 f_cs = ld_f(P.Cs, t_first), f_ct = ld_f(P.Ct, t_first), f_al = ld_al(t_first);
 
 #pragma unroll 1
@@ -225,12 +228,13 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             for (int k = NS; k > 0; --k) Bh[k] = Bh[k - 1];
             // b of row m (zero outside the grid)
             {
-                const float qxl = __shfl_up_sync(full, in_qx.y, 1);
+                const float2 qx = PS::f2(in_qx), qy = PS::f2(in_qy), qu = PS::f2(qby_up);
+                const float2 ps = PS::f2(in_ps), pt = PS::f2(in_pt);
+                const float qxl = __shfl_up_sync(full, qx.y, 1);
                 const float wy = m < G.H - 1 ? 1.f : 0.f;
                 float2 b;
-                b.x = -D.sigma * (in_qx.x - qxl + wy * in_qy.x - qby_up.x + in_pt.x - in_ps.x);
-                b.y = -D.sigma * (mxo * in_qx.y - in_qx.x + wy * in_qy.y - qby_up.y + in_pt.y -
-                                  in_ps.y);
+                b.x = -D.sigma * (qx.x - qxl + wy * qy.x - qu.x + pt.x - ps.x);
+                b.y = -D.sigma * (mxo * qx.y - qx.x + wy * qy.y - qu.y + pt.y - ps.y);
                 const bool ok = ok_row(m);
                 Bh[0] = ok ? b : make_float2(0.f, 0.f);
                 V[0] = in_u;  // zero outside the grid
@@ -277,9 +281,11 @@ __global__ void __launch_bounds__(kStripWarps * 32)
                 const float gx_e = uc.y - uc.x, gx_o = mxo * (u_right - uc.y);
                 const float gy_e = wy * (ud.x - uc.x), gy_o = wy * (ud.y - uc.y);
                 float qx_e, qy_e, ps_e, pt_e, qx_o, qy_o, ps_o, pt_o;
-                binary_dr_flows<S, ANISO>(D, uc.x, gx_e, gy_e, f_qx.x, f_qy.x, f_ps.x, f_pt.x,
+                const float2 fqx = PS::f2(f_qx), fqy = PS::f2(f_qy);
+                const float2 fps = PS::f2(f_ps), fpt = PS::f2(f_pt);
+                binary_dr_flows<S, ANISO>(D, uc.x, gx_e, gy_e, fqx.x, fqy.x, fps.x, fpt.x,
                                           f_al.x, f_cs.x, f_ct.x, qx_e, qy_e, ps_e, pt_e);
-                binary_dr_flows<S, ANISO>(D, uc.y, gx_o, gy_o, f_qx.y, f_qy.y, f_ps.y, f_pt.y,
+                binary_dr_flows<S, ANISO>(D, uc.y, gx_o, gy_o, fqx.y, fqy.y, fps.y, fpt.y,
                                           f_al.y, f_cs.y, f_ct.y, qx_o, qy_o, ps_o, pt_o);
                 const int o = t * G.pitch + c;
                 PF::st(s1.u + o, uc.x, uc.y);

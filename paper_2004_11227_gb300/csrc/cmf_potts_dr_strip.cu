@@ -63,8 +63,10 @@ __global__ void __launch_bounds__(kDrMaxWarps * 32, 3)
         const float ncx_e = (c > 0 ? 1.f : 0.f) + (c < G.W - 1 ? 1.f : 0.f);
         const float ncx_o = 1.f + mxo;
         auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
+        // stored pairs stay in their storage type until used: a conversion at
+        // the load would wait for the prefetched row at once
         auto ld_s = [&](const S* base, int r) {
-            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
+            return ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero();
         };
         auto ld_f = [&](const float* base, int r) {
             return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
@@ -108,12 +110,13 @@ __global__ void __launch_bounds__(kDrMaxWarps * 32, 3)
             for (int k = 0; k < NS + 2; ++k) V[k] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < NS + 1; ++k) Bh[k] = make_float2(0.f, 0.f);
-            float2 qby_up = ld_s(qy0, m_first - 1);
-            float2 in_u = ld_f(u0, m_first), in_qx = ld_s(qx0, m_first);
-            float2 in_qy = ld_s(qy0, m_first), in_p = ld_s(p0, m_first);
+            typename PS::T qby_up = ld_s(qy0, m_first - 1);
+            float2 in_u = ld_f(u0, m_first);
+            typename PS::T in_qx = ld_s(qx0, m_first), in_qy = ld_s(qy0, m_first),
+                           in_p = ld_s(p0, m_first);
             float2 in_ps = ld_f(s0.ps, m_first);
             const int t_first = m_first - NS - 1;
-            float2 f_qx = ld_s(qx0, t_first), f_qy = ld_s(qy0, t_first);
+            typename PS::T f_qx = ld_s(qx0, t_first), f_qy = ld_s(qy0, t_first);
             // costs of label l: its plane, or (I - c_l)^2 from the image plane
             const float* Cb = P.lev ? P.C : P.C + lo;
             const float lev_l = P.lev ? __ldg(P.lev + l) : 0.f;
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(kDrMaxWarps * 32, 3)
                 }
                 return v;
             };
-            float2 f_p = ld_s(p0, t_first), f_c = ld_cost(t_first), f_al = ld_al(t_first);
+            typename PS::T f_p = ld_s(p0, t_first);
+            float2 f_c = ld_cost(t_first), f_al = ld_al(t_first);
 #pragma unroll 1
             for (int m = m_first; m <= m_last; ++m) {
 #pragma unroll
@@ -136,14 +140,15 @@ __global__ void __launch_bounds__(kDrMaxWarps * 32, 3)
 #pragma unroll
                 for (int k = NS; k > 0; --k) Bh[k] = Bh[k - 1];
                 {  // row m enters: u^k and b
-                    const float qxl = __shfl_up_sync(full, in_qx.y, 1);
+                    const float2 qx = PS::f2(in_qx), qy = PS::f2(in_qy), pp = PS::f2(in_p);
+                    const float2 qu = PS::f2(qby_up);
+                    const float qxl = __shfl_up_sync(full, qx.y, 1);
                     const float wy = m < G.H - 1 ? 1.f : 0.f;
                     const float2 U = Us[(m - m_first) * 32 + lane];
                     float2 b;
-                    b.x = -D.sigma * (in_qx.x - qxl + wy * in_qy.x - qby_up.x + in_p.x - in_ps.x) +
+                    b.x = -D.sigma * (qx.x - qxl + wy * qy.x - qu.x + pp.x - in_ps.x) +
                           (stL * in_u.x - st_ * U.x);
-                    b.y = -D.sigma * (mxo * in_qx.y - in_qx.x + wy * in_qy.y - qby_up.y + in_p.y -
-                                      in_ps.y) +
+                    b.y = -D.sigma * (mxo * qx.y - qx.x + wy * qy.y - qu.y + pp.y - in_ps.y) +
                           (stL * in_u.y - st_ * U.y);
                     Bh[0] = ok_row(m) ? b : make_float2(0.f, 0.f);
                     V[0] = in_u;
@@ -189,8 +194,9 @@ __global__ void __launch_bounds__(kDrMaxWarps * 32, 3)
                     const float wy = t < G.H - 1 ? 1.f : 0.f;
                     const float gx[2] = {uc.y - uc.x, mxo * (u_right - uc.y)};
                     const float gy[2] = {wy * (ud.x - uc.x), wy * (ud.y - uc.y)};
-                    const float qbx[2] = {f_qx.x, f_qx.y}, qby[2] = {f_qy.x, f_qy.y};
-                    const float pb[2] = {f_p.x, f_p.y}, cc[2] = {f_c.x, f_c.y};
+                    const float2 fqx = PS::f2(f_qx), fqy = PS::f2(f_qy), fp = PS::f2(f_p);
+                    const float qbx[2] = {fqx.x, fqx.y}, qby[2] = {fqy.x, fqy.y};
+                    const float pb[2] = {fp.x, fp.y}, cc[2] = {f_c.x, f_c.y};
                     const float al[2] = {f_al.x, f_al.y}, u[2] = {uc.x, uc.y};
                     float oqx[2], oqy[2], op[2];
 #pragma unroll
