@@ -535,9 +535,6 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         const bool own = colin && lane >= 1 && lane <= 30;
         const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;
         auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
-        auto ld_s = [&](const S* base, int r) {
-            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
-        };
         auto ld_f = [&](const float* base, int r) {
             return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
         };
@@ -598,7 +595,15 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         }
         __syncwarp();
 
-        // phase 2: per label, stream down the band
+        // phase 2: per label, stream down the band; row t+1's inputs (and u of
+        // row t+2) are in flight while row t is summed, stored pairs kept in
+        // their storage type until used
+        using SP = typename PS::T;
+        struct RowIn {
+            SP qx, qy, p;
+            float2 c, ps, al;
+            __half2 ch;  // float16 cost planes
+        };
         for (int l = 0; l < L; ++l) {
             const size_t lo = (size_t)l * G.plane;
             const float* ul = s.u + lo;
@@ -606,10 +611,31 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             const S* qyl = s.qy + lo;
             const float* Cb = P.lev ? P.C : P.C + lo;
             const float lev_l = P.lev ? __ldg(P.lev + l) : 0.f;
+            auto ld_raw = [&](const S* base, int r) {
+                return ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero();
+            };
+            auto row_in = [&](int r) {
+                RowIn x;
+                x.qx = ld_raw(qxl, r);
+                x.qy = ld_raw(qyl, r);
+                x.p = ld_raw(s.p + lo, r);
+                x.ps = ld_f(s.ps, r);
+                x.al = ld_al(r);
+                if (P.C16) {
+                    x.ch = ok_row(r) ? Pair<__half>::ld(P.C16 + lo + r * G.pitch + c)
+                                     : Pair<__half>::zero();
+                    x.c = PF::zero();
+                } else {
+                    x.c = ld_f(Cb, r);
+                    x.ch = Pair<__half>::zero();
+                }
+                return x;
+            };
             // flows y of row r (zero outside the grid); every lane shuffles
-            auto flows = [&](int r, float2 u_r, float2 u_d, float2& f_x, float2& f_y) {
-                f_x = ld_s(qxl, r);
-                f_y = ld_s(qyl, r);
+            auto flows = [&](const RowIn& x, int r, float2 u_r, float2 u_d, float2& f_x,
+                             float2& f_y) {
+                f_x = PS::f2(x.qx);
+                f_y = PS::f2(x.qy);
                 const float u_right = __shfl_down_sync(full, u_r.x, 1);
                 if (DR) {
                     const float wy = row_w(r);
@@ -622,28 +648,30 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             };
             float2 u_t = ld_f(ul, r0 - 1), u_n = ld_f(ul, r0);
             float2 fx, fy;
-            flows(r0 - 1, u_t, u_n, fx, fy);
-            float2 al = ld_al(r0 - 1);
+            const RowIn x0 = row_in(r0 - 1);
+            flows(x0, r0 - 1, u_t, u_n, fx, fy);
             float2 fy_up = fy, py_up;
-            project_sel<ANISO>(fx.x, fy.x, al.x);
-            project_sel<ANISO>(fx.y, fy.y, al.y);
+            project_sel<ANISO>(fx.x, fy.x, x0.al.x);
+            project_sel<ANISO>(fx.y, fy.y, x0.al.y);
             py_up = fy;
             u_t = u_n;
+            RowIn nx = row_in(r0);
+            float2 u_nn = ld_f(ul, r0 + 1);
             float2 th_t = th_s[wib][0][lane];
             for (int t = r0; t < r1; ++t) {
-                u_n = ld_f(ul, t + 1);
+                const RowIn x = nx;
+                u_n = u_nn;  // row t+1
+                if (t + 1 < r1) nx = row_in(t + 1);
+                if (t + 2 <= r1) u_nn = ld_f(ul, t + 2);
                 const float2 th_n = th_s[wib][t + 1 - r0][lane];
-                float2 Cl = P.C16 ? (ok_row(t) ? Pair<__half>::f2(Pair<__half>::ld(
-                                                      P.C16 + lo + t * G.pitch + c))
-                                               : PF::zero())
-                                  : ld_f(Cb, t);
+                float2 Cl = P.C16 ? Pair<__half>::f2(x.ch) : x.c;
                 if (P.lev && ok_row(t)) {
                     Cl.x = (Cl.x - lev_l) * (Cl.x - lev_l);
                     Cl.y = (Cl.y - lev_l) * (Cl.y - lev_l);
                 }
-                float2 fp = ld_s(s.p + lo, t), fs = ld_f(s.ps, t);
-                al = ld_al(t);
-                flows(t, u_t, u_n, fx, fy);
+                float2 fp = PS::f2(x.p), fs = x.ps;
+                const float2 al = x.al;
+                flows(x, t, u_t, u_n, fx, fy);
                 const float wy = row_w(t);
                 // primal energy at ub_i = max(u_i - theta, 0)
                 const float ub_e = fmaxf(u_t.x - th_t.x, 0.f);
