@@ -446,8 +446,9 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         const bool own = colin && lane >= 1 && lane <= 30;
         const float mxo = c + 1 < G.W - 1 ? 1.f : 0.f;
         auto ok_row = [&](int r) { return colin && r >= 0 && r < G.H; };
-        auto ld_s = [&](const S* base, int r) {
-            return PS::f2(ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero());
+        // stored pairs stay in their storage type until used
+        auto ld_raw = [&](const S* base, int r) {
+            return ok_row(r) ? PS::ld(base + r * G.pitch + c) : PS::zero();
         };
         auto ld_f = [&](const float* base, int r) {
             return ok_row(r) ? PF::ld(base + r * G.pitch + c) : PF::zero();
@@ -457,10 +458,27 @@ __global__ void __launch_bounds__(kStripWarps * 32)
             return ld_f(P.alpha.plane, r);
         };
         auto row_w = [&](int r) { return r < G.H - 1 ? 1.f : 0.f; };
+        // the inputs of one row, loaded a row ahead of their use
+        struct RowIn {
+            typename PS::T qx, qy, ps, pt;
+            float2 cs, ct, al;
+        };
+        auto row_in = [&](int r) {
+            RowIn x;
+            x.qx = ld_raw(s.qx, r);
+            x.qy = ld_raw(s.qy, r);
+            x.ps = ld_raw(s.ps, r);
+            x.pt = ld_raw(s.pt, r);
+            x.cs = ld_f(P.Cs, r);
+            x.ct = ld_f(P.Ct, r);
+            x.al = ld_al(r);
+            return x;
+        };
         // flows y of row r (zero outside the grid) from q and, for rPDRQ, u of
         // rows r and r+1; every lane takes part in the shuffle
-        auto flows = [&](int r, float2 u_r, float2 u_d, float2& f_x, float2& f_y) {
-            const float2 qx = ld_s(s.qx, r), qy = ld_s(s.qy, r);
+        auto flows = [&](const RowIn& x, int r, float2 u_r, float2 u_d, float2& f_x,
+                         float2& f_y) {
+            const float2 qx = PS::f2(x.qx), qy = PS::f2(x.qy);
             const float u_right = __shfl_down_sync(full, u_r.x, 1);  // u(r, c+2)
             f_x = qx;
             f_y = qy;
@@ -477,20 +495,26 @@ __global__ void __launch_bounds__(kStripWarps * 32)
         // row r0-1: its y flows and their projections enter the divergence at r0
         float2 u_t = ld_f(s.u, r0 - 1), u_n = ld_f(s.u, r0);
         float2 fx, fy;
-        flows(r0 - 1, u_t, u_n, fx, fy);
-        float2 al = ld_al(r0 - 1);
+        const RowIn x0 = row_in(r0 - 1);
+        flows(x0, r0 - 1, u_t, u_n, fx, fy);
         float2 fy_up = fy, py_up;
-        project_sel<ANISO>(fx.x, fy.x, al.x);
-        project_sel<ANISO>(fx.y, fy.y, al.y);
+        project_sel<ANISO>(fx.x, fy.x, x0.al.x);
+        project_sel<ANISO>(fx.y, fy.y, x0.al.y);
         py_up = fy;
         u_t = u_n;
+        RowIn nx = row_in(r0);
+        float2 u_nn = ld_f(s.u, r0 + 1);
 #pragma unroll 1
         for (int t = r0; t < r1; ++t) {
-            u_n = ld_f(s.u, t + 1);
-            const float2 cs = ld_f(P.Cs, t), ct = ld_f(P.Ct, t);
-            float2 ps = ld_s(s.ps, t), pt = ld_s(s.pt, t);
-            al = ld_al(t);
-            flows(t, u_t, u_n, fx, fy);
+            // row t's inputs arrived during the previous step; row t+1's and
+            // u of row t+2 go in flight now
+            const RowIn x = nx;
+            u_n = u_nn;
+            if (t + 1 < r1) nx = row_in(t + 1);
+            if (t + 2 <= r1) u_nn = ld_f(s.u, t + 2);
+            const float2 cs = x.cs, ct = x.ct, al = x.al;
+            float2 ps = PS::f2(x.ps), pt = PS::f2(x.pt);
+            flows(x, t, u_t, u_n, fx, fy);
             const float wy = row_w(t);
             // primal energy at ub = clip(u, 0, 1)
             const float ub_e = fminf(fmaxf(u_t.x, 0.f), 1.f);
