@@ -51,6 +51,8 @@ PHASE_GAP = 2e-3      # switch to float32 storage at this certified gap
 COSTS = 0             # cost planes as given (float32)
 CHECK_EVERY = 50      # a 16-label certificate launch costs about 1.7 iterations
 CHECK_SIDE = 10       # the side workloads check every 10 iterations
+BATCH_CHECK = 20      # the batch (and its one-by-one comparison) every 20: its tile
+                      # certificates cost about an iteration of all instances
 MAX_ITER = 12000
 # Algorithmic bytes of one iteration of this workload counted with every
 # stored field in 16 bits: L (8 s + s_c) + 2 s + 4 with s = s_c = 2 (u, q_i,
@@ -427,7 +429,7 @@ def batch_workload(cmf, synth, flush) -> dict:
     import torch
 
     insts = synth.batch_instances()
-    p = cmf.default_params(2, 2, tol_gap=1e-4, max_iter=5000, check_every=10)
+    p = cmf.default_params(2, 2, tol_gap=1e-4, max_iter=5000, check_every=BATCH_CHECK)
     items = [cmf.alloc_binary(i, p) if i.kind == "binary" else cmf.alloc_potts(i, p)
              for i in insts]
     for it in items:  # the single-solve workspaces are not used by the batch
@@ -446,7 +448,8 @@ def batch_workload(cmf, synth, flush) -> dict:
     ms = e0.elapsed_time(e1)
     units = sum(i.H * i.W * i.L * r["iters"] for i, r in zip(insts, res))
     iters = [r["iters"] for r in res]
-    out = {"instances": len(insts), "time_ms": round(ms, 2), "px_label_it_per_s": units / ms * 1e3,
+    out = {"instances": len(insts), "check_every": BATCH_CHECK, "time_ms": round(ms, 2),
+           "px_label_it_per_s": units / ms * 1e3,
            "converged": sum(1 for r in res if r["status"] == cmf.OK),
            "iters_min": min(iters), "iters_median": int(np.median(iters)), "iters_max": max(iters),
            "label_pixels": sum(i.H * i.W * i.L for i in insts)}
@@ -478,7 +481,7 @@ def batch_workload(cmf, synth, flush) -> dict:
     # outside the timed calls, graph building inside them)
     seq_ms, seq_units, seq_ok = 0.0, 0, 0
     for inst in insts:
-        q = cmf.default_params(2, inst.L, tol_gap=1e-4, max_iter=5000, check_every=10)
+        q = cmf.default_params(2, inst.L, tol_gap=1e-4, max_iter=5000, check_every=BATCH_CHECK)
         one = cmf.alloc_binary(inst, q) if inst.kind == "binary" else cmf.alloc_potts(inst, q)
         torch.cuda.synchronize()
         e0.record()
