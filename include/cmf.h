@@ -207,9 +207,11 @@ const char *cmf_status_str(cmf_status s);
 /* Bytes of device workspace the calls below need for an H x W grid with L
  * labels (L = 2: binary) and row pitch `pitch`.  The workspace is caller-
  * owned device memory, at least 256-byte aligned, passed as d_ws/ws_bytes.
- * It holds one extra state set (two for the fused binary form), the plain
- * form's temporaries, the certificate partials, the solve loop's control
- * block and max_iter / check_every + 1 history rows, so it depends on *p:
+ * It holds one extra state set (two for the fused binary form; two 16-bit
+ * sets more for a two-phase Potts solve), the plain form's temporaries, two
+ * float32 planes of sum_i u_i for fused Potts rPDRQ, the certificate
+ * partials, the solve loop's control block and max_iter / check_every + 1
+ * history rows, so it depends on *p:
  * size it with the parameters the calls will use (a call whose parameters
  * need more returns CMF_ENOMEM before launching anything). */
 size_t cmf_workspace_bytes(int H, int W, int L, int pitch, const cmf_params *p);
