@@ -15,9 +15,9 @@
 // p_i, written to the output set.  Phase 3 (after a block barrier): the new
 // u_i of the band are read back (from L2, written moments before) and summed
 // in label order (the next launch's U, written to a plane), and pbar_s is
-// reflected.  One shared U per band, instead
-// of one per warp, lets the band be several times taller for the same shared
-// memory, so the 2 (1 + 2 SW) + 1 halo rows every band recomputes weigh less.
+// reflected.  One shared U per band, instead of one per warp, lets the band be
+// several times taller for the same shared memory, so the 2 (1 + 2 SW) + 1
+// halo rows every band recomputes weigh less.
 #include "cmf_kernels.cuh"
 #include "cmf_strip.cuh"
 
