@@ -75,6 +75,20 @@ def test_many_labels(cmf, L):
         assert np.abs(s.state()["u"] - ref["u"]).max() <= TOL_U
 
 
+@pytest.mark.parametrize("L", [31, 64])
+def test_many_labels_strips(cmf, L):
+    """Even width: the warp-strip kernels at large label counts (the rPDRQ
+    kernel shares 31 labels out over 4 warps of 8 and 7 passes, 64 over 4
+    warps of 16), against the oracle."""
+    inst = synth.random_potts(23, 38, L, seed=40 + L, alpha=0.2, field_alpha=True)
+    for algo in [2, 3]:
+        s = _gpu_run(cmf, inst, algo, 20, variant=2)
+        ref, _ = _oracle_run(inst, algo, 20)
+        got = s.state()
+        for k in ("u", "qx", "qy", "p", "ps"):
+            assert np.abs(got[k] - ref[k]).max() <= TOL_U, (algo, k)
+
+
 @pytest.mark.parametrize("algo", ALGOS)
 def test_anisotropic_and_multisweep(cmf, algo):
     inst = synth.random_potts(31, 26, 4, seed=40, alpha=0.3, field_alpha=True)
