@@ -195,6 +195,10 @@ typedef struct {
                           also with phase_gap = 1.5 tol_gap (the switch left
                           to the first phase's stall test).  Other algorithms
                           ignore it.                                         */
+    int batch_rows;    /* cmf_solve_batch: band height of the warp-strip items
+                          of its Potts instances, 8..24 (0 = 24); the items
+                          of a band share its halo rows, the warps of a batch
+                          share the work of small instances.               */
 } cmf_params;
 
 /* Fill *p with the paper's defaults for `algo` and L labels (L = 2 for the
@@ -427,6 +431,17 @@ size_t cmf_batch_workspace_bytes(const cmf_instance *inst, int n, const cmf_para
  * reached p->tol_gap, CMF_NOT_CONVERGED when some stopped at max_iter. */
 cmf_status cmf_solve_batch(cmf_instance *inst, int n, const cmf_params *p, void *d_ws,
                            size_t ws_bytes, void *stream);
+
+/* Time cmf_solve_batch (cold starts; the instances' state buffers are
+ * overwritten) over candidate launch and check settings and write the
+ * fastest whose every instance reaches p->tol_gap to *best: check_every in
+ * {k, 2k, 5k} (k = p->check_every; those that divide p->max_iter) and,
+ * when the batch has strip instances, batch_rows in {12, 16, 24}.  The
+ * workspace must hold cmf_batch_workspace_bytes for batch_rows = 12 (the
+ * largest item tables).  *h_best_ms: the fastest time.  Returns
+ * CMF_NOT_CONVERGED when no candidate converged. */
+cmf_status cmf_autotune_batch(cmf_instance *inst, int n, const cmf_params *p, cmf_params *best,
+                              double *h_best_ms, void *d_ws, size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

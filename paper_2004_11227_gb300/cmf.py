@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
         ("costs", ctypes.c_int),
         ("rho_schedule", ctypes.POINTER(ctypes.c_double)), ("rho_schedule_len", ctypes.c_int),
         ("phase_storage", ctypes.c_int), ("phase_gap", ctypes.c_double),
-        ("tune_step", ctypes.c_int),
+        ("tune_step", ctypes.c_int), ("batch_rows", ctypes.c_int),
     ]
 
     def set_rho_schedule(self, rhos) -> "Params":
@@ -109,6 +109,8 @@ _SIGS = {
     "cmf_batch_workspace_bytes": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
     "cmf_solve_batch": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_size_t, ctypes.c_void_p],
+    "cmf_autotune_batch": [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4 +
+                          [ctypes.c_size_t, ctypes.c_void_p],
 }
 EXPORTED = tuple(_SIGS)
 
@@ -429,6 +431,21 @@ class Batch:
         res = [dict(iters=d.iters, status=d.status, energy=d.energy, dual=d.dual, gap=d.gap,
                     res=d.res) for d in self.insts]
         return st, res
+
+
+def cmf_autotune_batch(items, params: Params, stream=None):
+    """cmf_autotune_batch over a list of Binary / Potts containers (their
+    state is overwritten).  Returns (best Params, milliseconds)."""
+    q = Params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(params), ctypes.sizeof(Params))
+    q.batch_rows = 12  # the workspace for the largest item tables
+    b = Batch(items, q)
+    best = Params()
+    ms = ctypes.c_double(0.0)
+    _check(lib().cmf_autotune_batch(b.insts, len(items), ctypes.byref(params), ctypes.byref(best),
+                                    ctypes.byref(ms), _ptr(b.ws), b.ws.numel(), _stream(stream)),
+           "cmf_autotune_batch")
+    return best, ms.value
 
 
 def cmf_solve_batch(items, params: Params, stream=None):

@@ -41,8 +41,12 @@ bool batch_strip(const cmf_instance& in, const cmf_params& p) {
     return potts_strip_eligible(G, p.storage, in.d_cost, in.d_alpha, s, s, true);
 }
 int strip_count(const cmf_instance& in) { return (in.W + 59) / 60; }
-int strip_items(const cmf_instance& in) {
-    const int R = potts_strip_max_rows();
+// band height of the strip items (params.batch_rows, 0: the kernels' maximum)
+int strip_rows(const cmf_params& p) {
+    return p.batch_rows > 0 ? p.batch_rows : potts_strip_max_rows();
+}
+int strip_items(const cmf_instance& in, const cmf_params& p) {
+    const int R = strip_rows(p);
     return strip_count(in) * ((in.H + R - 1) / R);
 }
 
@@ -74,7 +78,7 @@ BatchLayout batch_layout(const cmf_instance* inst, int n, const cmf_params& p) {
         } else {
             const int ty = 8 * b.potts_rows;
             if (batch_strip(in, p))
-                b.n_strip_items += strip_items(in);
+                b.n_strip_items += strip_items(in, p);
             else
                 b.n_potts_tiles += ntx * ((in.H + ty - 1) / ty);
             b.n_potts_ev += ev;
@@ -219,6 +223,8 @@ cmf_status check_batch_params(const cmf_params* p) {
         p->max_iter % p->check_every)
         return CMF_EINVAL;
     if (!(p->tol_gap >= 0)) return CMF_EINVAL;
+    if (p->batch_rows != 0 && (p->batch_rows < 8 || p->batch_rows > potts_strip_max_rows()))
+        return CMF_EINVAL;
     return CMF_OK;
 }
 
@@ -317,9 +323,9 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
             D.ev_tab = (int)ep.size();
             if (batch_strip(in, *p)) {
                 D.sp_nstrips = strip_count(in);
-                D.sp_rows = potts_strip_max_rows();
+                D.sp_rows = strip_rows(*p);
                 std::vector<int2>& dst = in.W % 2 ? oitems : sitems;
-                for (int t = 0; t < strip_items(in); ++t) dst.push_back(make_int2(i, t));
+                for (int t = 0; t < strip_items(in, *p); ++t) dst.push_back(make_int2(i, t));
             } else {
                 for (int t = 0; t < ntx * ((in.H + pty - 1) / pty); ++t) tp.push_back(i);
             }
@@ -472,4 +478,69 @@ extern "C" cmf_status cmf_solve_batch(cmf_instance* inst, int n, const cmf_param
     if (g) cudaGraphDestroy(g);
     if (cs) cudaStreamDestroy(cs);
     return status;
+}
+
+extern "C" cmf_status cmf_autotune_batch(cmf_instance* inst, int n, const cmf_params* p,
+                                         cmf_params* best, double* h_best_ms, void* d_ws,
+                                         size_t ws_bytes, void* stream) {
+    if (!inst || n < 1 || !p || !best) return CMF_EINVAL;
+    cmf_status s;
+    if ((s = check_batch_params(p)) != CMF_OK) return s;
+    bool strips = false;
+    for (int i = 0; i < n; ++i) {
+        if ((s = check_instance(inst[i], *p)) != CMF_OK) return s;
+        strips = strips || batch_strip(inst[i], *p);
+    }
+    std::vector<cmf_params> cand;
+    for (int f : {1, 2, 5}) {
+        const int k = p->check_every * f;
+        if (k > p->max_iter || p->max_iter % k) continue;
+        for (int rows : {12, 16, 24}) {
+            if (!strips && rows != 24) continue;
+            cmf_params q = *p;
+            q.check_every = k;
+            q.batch_rows = rows;
+            q.warm_start = 0;
+            cand.push_back(q);
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // one untimed solve first: module loading and first launches
+    if (!cand.empty() && batch_layout(inst, n, cand[0]).total <= ws_bytes) {
+        s = cmf_solve_batch(inst, n, &cand[0], d_ws, ws_bytes, stream);
+        if (s == CMF_ECUDA || s == CMF_ETIMEOUT || s == CMF_EINVAL) return s;
+    }
+    cudaEvent_t e0, e1;
+    CMF_CUDA_TRY(cudaEventCreate(&e0));
+    CMF_CUDA_TRY(cudaEventCreate(&e1));
+    double best_ms = 1e300;
+    bool found = false;
+    cmf_status last = CMF_NOT_CONVERGED;
+    for (const cmf_params& q : cand) {
+        if (batch_layout(inst, n, q).total > ws_bytes) {
+            last = CMF_ENOMEM;
+            continue;
+        }
+        cudaEventRecord(e0, st);
+        s = cmf_solve_batch(inst, n, &q, d_ws, ws_bytes, stream);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (s == CMF_ECUDA || s == CMF_ETIMEOUT) {
+            last = s;
+            break;
+        }
+        if (s != CMF_OK) continue;
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = q;
+            found = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!found) return last;
+    if (h_best_ms) *h_best_ms = best_ms;
+    return CMF_OK;
 }

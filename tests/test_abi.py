@@ -231,3 +231,32 @@ def test_two_phase_parameters_validated(cmf):
     p0 = cmf.default_params(cmf.RPADMM_EB, 4)
     p1 = cmf.default_params(cmf.RPADMM_EB, 4, phase_storage=1, phase_gap=2e-3)
     assert cmf.cmf_workspace_bytes(64, 64, 4, 64, p1) > cmf.cmf_workspace_bytes(64, 64, 4, 64, p0)
+
+
+def test_batch_rows_validated_and_sized(cmf):
+    """params.batch_rows (the strip band height of a batch): 0 or 8..24; the
+    workspace grows with the item table as the bands get shorter; the batch
+    autotuner validates before any launch."""
+    lib = cmf.lib()
+    ptr, keep = _fake(64 * 64)
+    inst = cmf.Instance()
+    inst.model, inst.L, inst.H, inst.W, inst.pitch = 1, 4, 1024, 64, 64
+    inst.d_cost = inst.d_u = inst.d_qx = inst.d_qy = inst.d_p = inst.d_ps = ptr
+    inst.alpha0 = 0.3
+
+    def nbytes(rows):
+        q = cmf.default_params(cmf.RPADMM_EB, 2)
+        q.batch_rows = rows
+        return lib.cmf_batch_workspace_bytes(ctypes.byref(inst), 1, ctypes.byref(q))
+
+    for bad in (7, 25, -1):
+        assert nbytes(bad) == 0, bad
+    assert nbytes(0) == nbytes(24) > 0
+    assert nbytes(8) > nbytes(12) >= nbytes(24)
+    q = cmf.default_params(cmf.RPADMM_EB, 2)
+    q.batch_rows = 30
+    best = cmf.Params()
+    ms = ctypes.c_double(0.0)
+    assert lib.cmf_autotune_batch(ctypes.byref(inst), 1, ctypes.byref(q), ctypes.byref(best),
+                                  ctypes.byref(ms), ptr, 1 << 20, None) == cmf.EINVAL
+    del keep

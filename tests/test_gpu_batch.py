@@ -219,3 +219,44 @@ def test_batch_alg1_takes_each_instances_step_bound(cmf):
         a, b = item.state(), single.state()
         for k in a:
             assert np.abs(a[k] - b[k]).max() <= 1e-5, k
+
+
+def test_batch_rows_give_the_same_solution(cmf):
+    """params.batch_rows changes only how the strip instances are cut into
+    work items: the same iterations and states bit for bit."""
+    insts = [synth.potts_shapes(120, 88, 8, seed=104), synth.potts_shapes(67, 71, 3, seed=102),
+             synth.binary_shapes(40, 50, seed=106)]
+    out = []
+    for rows in (24, 12, 8):
+        p = cmf.default_params(2, 2, tol_gap=1e-4, max_iter=20000, check_every=10,
+                               batch_rows=rows)
+        items = [_alloc(cmf, i, p) for i in insts]
+        status, res = cmf.cmf_solve_batch(items, p)
+        assert status == cmf.OK, res
+        out.append(([r["iters"] for r in res], [it.state() for it in items]))
+    for iters, states in out[1:]:
+        assert iters == out[0][0]
+        for a, b in zip(states, out[0][1]):
+            for k in a:
+                assert np.array_equal(a[k], b[k]), k
+
+
+def test_batch_autotune(cmf):
+    """cmf_autotune_batch times the batch over check intervals and strip band
+    heights and returns one whose instances all converge; solved with it,
+    every instance is certified by the oracle."""
+    insts = _instances()
+    p = cmf.default_params(2, 2, tol_gap=1e-4, max_iter=20000, check_every=10)
+    items = [_alloc(cmf, i, p) for i in insts]
+    best, ms = cmf.cmf_autotune_batch(items, p)
+    assert ms > 0 and best.check_every in (10, 20, 50) and best.batch_rows in (12, 16, 24)
+    items = [_alloc(cmf, i, best) for i in insts]
+    status, res = cmf.cmf_solve_batch(items, best)
+    assert status == cmf.OK, res
+    for inst, item in zip(insts, items):
+        po = O.default_params(2, inst.L, a2=max(best.a2, 2.0 * inst.L))
+        if inst.kind == "binary":
+            gap = O.binary_eval(inst.costs[0], inst.costs[1], inst.alpha, item.state(), po)[2]
+        else:
+            gap = O.potts_eval(inst.costs, inst.alpha, item.state(), po)[2]
+        assert gap <= 1.01e-4
