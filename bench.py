@@ -289,6 +289,10 @@ KERNEL_CASES = {
     "potts4-plain-2048": ("potts", 2, 2048, 2048, 4, 0, 1),
     # a host-driven solve to gap 1e-4 (use_graph = 0), so a profiler sees every launch
     "binary-solve-host-1024": ("binary-solve", 2, 1024, 1024, 2, 0, 0),
+    # 16 painted-shapes instances (seeds 100..115) as one host-driven batch, `iters`
+    # iterations: even and odd widths
+    "potts4-batch-16x512": ("potts-batch", 2, 512, 512, 4, 0, 0),
+    "potts4-batch-16x511": ("potts-batch", 2, 511, 511, 4, 0, 0),
 }
 
 
@@ -679,6 +683,15 @@ def run_kernel_case(name: str, iters: int, time_it: bool = False, variant: int =
                                phase_gap=PHASE_GAP, use_graph=int(model == "potts-solve"))
         st = cmf.alloc_potts(rank_instance(0, h), q)
         print(name, cmf.cmf_solve_potts(st)[:2])
+        torch.cuda.synchronize()
+        return
+    if model == "potts-batch":
+        ins = [synth.potts_shapes(h, w, nl, seed=100 + k) for k in range(16)]
+        q = cmf.default_params(algo, 2, tol_gap=1e-12, max_iter=max(10, (iters + 9) // 10 * 10),
+                               check_every=10, use_graph=0)
+        items = [cmf.alloc_potts(i, q) for i in ins]
+        st_b, res = cmf.cmf_solve_batch(items, q)
+        print(name, st_b, [r["iters"] for r in res][:4])
         torch.cuda.synchronize()
         return
     if model == "binary-solve":
