@@ -614,3 +614,25 @@ def test_rpdrq_strip_label_sum_plane_is_exact(cmf, storage, L, shape):
     sa, sb = a.state(), b.state()
     for k in sa:
         assert np.array_equal(sa[k], sb[k]), k
+
+
+@pytest.mark.parametrize("algo,shape", [(3, (64, 96)), (5, (64, 96)), (0, (64, 96)),
+                                        (2, (63, 91))])
+def test_two_phase_other_algorithms_and_tiles(cmf, algo, shape):
+    """Two-phase solves of rPDRQ (its strip kernel's label-sum planes serve
+    both phases), ALG1 and pADMMI, and of an odd width (tile kernels): the
+    result is certified by the oracle, and the host-driven loop takes the
+    same decisions as the device-driven one."""
+    inst = synth.config5(*shape)
+    kw = dict(tol_gap=1e-4, max_iter=30000, check_every=10, phase_storage=1, phase_gap=2e-3)
+    p = cmf.default_params(algo, 16, **kw)
+    s = cmf.alloc_potts(inst, p)
+    st, it, hist = cmf.cmf_solve_potts(s)
+    assert st == cmf.OK, (it, hist[-1])
+    po = O.default_params(algo, 16, sigma=p.sigma, tau=p.tau)
+    assert O.potts_eval(inst.costs, inst.alpha, s.state(), po)[2] <= 1.001e-4
+    ph = cmf.default_params(algo, 16, use_graph=0, **kw)
+    e = cmf.alloc_potts(inst, ph)
+    st_e, it_e, h_e = cmf.cmf_solve_potts(e)
+    assert st_e == cmf.OK and it_e == it
+    np.testing.assert_array_equal(h_e, hist)
