@@ -636,3 +636,23 @@ def test_two_phase_other_algorithms_and_tiles(cmf, algo, shape):
     st_e, it_e, h_e = cmf.cmf_solve_potts(e)
     assert st_e == cmf.OK and it_e == it
     np.testing.assert_array_equal(h_e, hist)
+
+
+def test_two_phase_first_phase_uses_up_max_iter(cmf):
+    """A first phase that reaches neither the switch gap nor a stall within
+    max_iter: NOT_CONVERGED after max_iter iterations, the 16-bit state
+    widened into the caller's buffers (equal to a 16-bit solve stopped there)."""
+    inst = synth.config5(32, 64)
+    kw = dict(max_iter=40, check_every=10)
+    p = cmf.default_params(2, 16, tol_gap=1e-4, phase_storage=1, phase_gap=2e-3, **kw)
+    s = cmf.alloc_potts(inst, p)
+    st, it, hist = cmf.cmf_solve_potts(s)
+    assert st == cmf.NOT_CONVERGED and it == 40 and len(hist) == 4
+    q = cmf.default_params(2, 16, storage=1, tol_gap=2e-3, **kw)
+    a = cmf.alloc_potts(inst, q)
+    st_a, it_a, h_a = cmf.cmf_solve_potts(a)
+    assert it_a == 40
+    np.testing.assert_array_equal(hist, h_a)
+    got, ref = s.state(), a.state()
+    for k in got:
+        np.testing.assert_array_equal(got[k], ref[k])
