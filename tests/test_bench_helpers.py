@@ -42,3 +42,30 @@ def test_traffic_table_matches_the_sources():
         assert sha == e["src_sha256"], name
         assert bench._traffic(e["source"], name) == float(e["dram_bytes_per_launch_full_size"])
     assert bench._traffic("paper_2004_11227_gb300/csrc/cmf_potts_strip.cu", "no-such") is None
+
+
+def test_phase_one_end_follows_the_switch_rule():
+    """The bench recovers where a two-phase solve switched storage from its
+    history: the first gap <= the switch gap, or a stall (tested every
+    ceil(200 / check_every) checks, below 10x the switch gap, above 0.7x the
+    previous tested gap)."""
+    import numpy as np
+
+    def hist(gaps):
+        h = np.zeros((len(gaps), 5))
+        h[:, 0] = 50 * (np.arange(len(gaps)) + 1)
+        h[:, 3] = gaps
+        return h
+
+    # reaches the switch gap at row 3
+    assert bench.phase_one_end(hist([1e-1, 1e-2, 5e-3, 1e-3, 5e-4]), 2e-3, 50) == 3
+    # window of 4 checks at check_every 50: rows 0, 4, 8 tested; row 4 (6e-4 <
+    # 1.5e-3, 6e-4 > 0.7 x 8e-4) stalls
+    g = [8e-4, 7.5e-4, 7e-4, 6.5e-4, 6e-4, 5e-4]
+    assert bench.phase_one_end(hist(g), 1.5e-4, 50) == 4
+    # falling fast enough: no stall; the last row is returned
+    g = [1e-2, 5e-3, 3e-3, 2e-3, 1e-3, 8e-4, 6e-4, 5e-4, 3e-4]
+    assert bench.phase_one_end(hist(g), 1.5e-4, 50) == len(g) - 1
+    # a stall far above 10x the switch gap does not count
+    g = [1e-1] * 9 + [1e-3]
+    assert bench.phase_one_end(hist(g), 1.5e-4, 50) == len(g) - 1
